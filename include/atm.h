@@ -1,0 +1,195 @@
+/*
+ * atm.h -- C ABI of libatm, a GB300 (sm_103a) implementation of the
+ * space-time relaxation and coarse-correction sweep of AT-MGRIT
+ * (Hahne, Southworth, Friedhoff, "Asynchronous Truncated
+ * Multigrid-reduction-in-time", arXiv 2107.09596).
+ *
+ * The problem (Sec. 2, Eq. 1-2): an initial value problem discretised on the
+ * time grid t_i = t_0 + i dt, i = 0..nt_points-1, as the one-step system
+ *     u_0 = g_0,   u_i = Phi(u_{i-1}) + g_i,
+ * i.e. the block lower-bidiagonal space-time system A(u) = g.  The library
+ * solves it by sequential time stepping, by MGRIT, or by AT-MGRIT: every m-th
+ * point is a C-point (Sec. 2.1), relaxation is F or FCF (Algorithm 2,
+ * F(CF)^nu), residuals are restricted by injection into an FAS coarse problem
+ * re-discretised with the coarse step m*dt (Sec. 2.1, last paragraph), and on
+ * the coarsest level the global coarse grid is replaced by the local grids
+ * T^(p) = {i dT : i in [max(0, p-k+1), p]} (Sec. 2.1), each solved as an
+ * independent chain and injected back (Algorithm 2).
+ *
+ * Conventions for every call below
+ *   - Status: every call returns an atm_status; nothing throws across the ABI.
+ *     atm_last_error() returns a message for the calling thread's last error.
+ *   - Memory: the caller owns all device memory, including the workspace given
+ *     to atm_create (query its size with atm_workspace_size).  The library
+ *     never allocates or frees device memory.  A handle is owned by the
+ *     library until atm_destroy.
+ *   - Streams: all GPU work is issued on the CUDA stream given to atm_create.
+ *     Calls return after issuing their work, except where noted.
+ *   - Threads: one thread at a time per handle.
+ *   - Layout: a state (one time point) is row-major: heat1d holds nx values;
+ *     the 2D problems hold ny rows of nx values (x fastest).  Space-time arrays
+ *     are time-major: state i starts at offset i * state_size.
+ */
+#ifndef ATM_H
+#define ATM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ATM_OK = 0,
+    ATM_ERR_INVALID_ARG = 1,   /* a size, pointer or option is out of range */
+    ATM_ERR_CUDA = 2,          /* a CUDA call failed; see atm_last_error() */
+    ATM_ERR_OOM = 3,           /* the workspace is smaller than atm_workspace_size */
+    ATM_ERR_NOT_CONVERGED = 4, /* max_iter cycles ran without reaching tol; result is filled */
+    ATM_ERR_DIVERGED = 5,      /* a non-finite residual or a residual growth above 1e3 */
+    ATM_ERR_TIMEOUT = 6,       /* reserved: a bounded device wait ran out */
+    ATM_ERR_UNSUPPORTED = 7    /* a valid but unimplemented combination of options */
+} atm_status;
+
+/* Problem families (Phi on the fine grid). */
+enum {
+    ATM_HEAT1D = 0,      /* u_t = u_xx on [0, lx], Dirichlet 0, nx interior points, dx = lx/(nx+1) */
+    ATM_HEAT2D = 1,      /* u_t = u_xx + u_yy, periodic [0,lx) x [0,ly), dx = lx/nx, dy = ly/ny */
+    ATM_ALLEN_CAHN = 2   /* u_t = Lap u + (u - u^3)/eps^2, periodic as ATM_HEAT2D */
+};
+
+/* One-step propagators of the 2D families on a level with step D (heat1d is
+ * always backward Euler).  For Allen-Cahn the reaction is first advanced by s
+ * explicit Euler substeps of size D/s (Lie splitting), then the diffusion: */
+enum {
+    ATM_PROP_SPLIT_BE = 0, /* (I - D Lx) y = w, (I - D Ly) u' = y */
+    ATM_PROP_PR_ADI = 1    /* (I - D/2 Lx) u* = (I + D/2 Ly) w, (I - D/2 Ly) u' = (I + D/2 Lx) u* */
+};
+
+enum { ATM_SEQUENTIAL = 0, ATM_MGRIT = 1, ATM_AT_MGRIT = 2 };
+
+/* Arithmetic of the sweep: FP64 throughout; FP32 throughout (residual norm
+ * accumulated in FP64); FP32 propagation inside an FP64 defect-correction
+ * loop (FP64 residual, correction and norm). */
+enum { ATM_FP64 = 0, ATM_FP32 = 1, ATM_FP32_REFINED = 2 };
+
+#define ATM_MAX_LEVELS 8
+
+typedef struct {
+    int kind;          /* ATM_HEAT1D | ATM_HEAT2D | ATM_ALLEN_CAHN */
+    int nx, ny;        /* grid; ny ignored for heat1d.  2D: nx, ny multiples of 32 */
+    double lx, ly;     /* domain lengths */
+    double dt;         /* fine time step */
+    int nt_points;     /* number of time points including t_0 (>= 2) */
+    double eps;        /* Allen-Cahn interface parameter */
+} atm_problem;
+
+typedef struct {
+    int algorithm;                    /* ATM_SEQUENTIAL | ATM_MGRIT | ATM_AT_MGRIT */
+    int levels;                       /* number of time levels L >= 2 (MGRIT / AT-MGRIT) */
+    int m[ATM_MAX_LEVELS];            /* coarsening factor from level l to l+1 (>= 2) */
+    int k;                            /* AT-MGRIT local grid size in points (>= 1) */
+    int nu;                           /* 0: F-relaxation, 1: FCF-relaxation */
+    int fine_prop;                    /* propagator on level 0 (2D) */
+    int coarse_prop;                  /* propagator on levels >= 1 (2D) */
+    int reaction_substeps[ATM_MAX_LEVELS]; /* Allen-Cahn substeps per level; 0 = product of m below */
+    double tol;                       /* stop when the residual 2-norm <= tol */
+    int max_iter;                     /* maximum V-cycles */
+    int precision;                    /* ATM_FP64 | ATM_FP32 | ATM_FP32_REFINED */
+    int use_graph;                    /* 1: replay the cycle as a captured CUDA graph */
+} atm_solver;
+
+typedef struct {
+    int iterations;            /* V-cycles run (0 for sequential stepping) */
+    int converged;             /* 1 if the last residual <= tol */
+    double initial_residual;   /* ||r||_2 of the initial guess after F-relaxation */
+    double final_residual;     /* ||r||_2 after the last cycle */
+    double time_ms;            /* device time of the solve (CUDA events) */
+} atm_result;
+
+typedef struct atm_handle atm_handle;
+
+/* Bytes of device workspace atm_create needs for this problem and solver.
+ * Errors: ATM_ERR_INVALID_ARG for inconsistent sizes or options. */
+atm_status atm_workspace_size(const atm_problem *prob, const atm_solver *solver, size_t *bytes);
+
+/* Build a solver in the caller's workspace (device memory of at least
+ * atm_workspace_size bytes, 256-byte aligned) on `cuda_stream` (a
+ * cudaStream_t; NULL = legacy default stream).  Precomputes the propagator
+ * coefficients and the launch tables of the cycle; synchronises the stream
+ * once.  The state starts as u_0 = 0 and a zero initial guess. */
+atm_status atm_create(const atm_problem *prob, const atm_solver *solver, void *d_workspace,
+                      size_t bytes, void *cuda_stream, atm_handle **out);
+
+/* Set u_0 = g_0 (the initial condition, FP64, one state).  `u0` may be a host
+ * or a device pointer (unified addressing); a host copy completes before the
+ * call returns. */
+atm_status atm_set_initial_condition(atm_handle *h, const double *u0);
+
+/* Set the iterate at time points 1..nt_points-1 from `u` (FP64, nt_points
+ * states, host or device; state 0 is ignored).  Default: zero. */
+atm_status atm_set_initial_guess(atm_handle *h, const double *u);
+
+/* Run the solver (Algorithm 2 V-cycles, or sequential stepping) until the
+ * residual 2-norm over the space-time points is <= tol or max_iter cycles
+ * ran.  Blocks until the result is known.  Returns ATM_ERR_NOT_CONVERGED
+ * (result filled) when max_iter is reached first, ATM_ERR_DIVERGED on a
+ * non-finite residual. */
+atm_status atm_solve(atm_handle *h, atm_result *out);
+
+/* Copy states t0..t0+count-1 of the level-0 iterate to `dst` (FP64, host or
+ * device pointer).  Blocks for host destinations. */
+atm_status atm_get_solution(atm_handle *h, int t0, int count, double *dst);
+
+/* Residual norms of the last solve: hist[0] for the initial guess, hist[i]
+ * after cycle i.  Writes min(cap, iterations+1) values, the count to *n. */
+atm_status atm_get_residual_history(atm_handle *h, double *hist, int cap, int *n);
+
+/* out[s] = Phi_level(in[s]) for s < nstates: the level's one-step propagator
+ * (Sec. 2.1: Phi on level 0, re-discretisation with step dt*m_0*..*m_{l-1} on
+ * level l), in the handle's working precision.  in/out: FP64 device arrays of
+ * nstates states; they may alias.  nstates <= the handle's largest batch
+ * (nt_points - 1 bounded by the scratch size; ATM_ERR_INVALID_ARG beyond). */
+atm_status atm_apply_propagator(atm_handle *h, int level, const double *in, double *out,
+                                int nstates);
+
+/* Building blocks of one V-cycle (Algorithm 2), on the handle's level arrays:
+ *   ATM_STAGE_F_RELAX    F-relaxation of level l (Sec. 2.1)
+ *   ATM_STAGE_C_RELAX    C-relaxation of level l (u_0 = g_0, u_im = Phi(u_im-1) + g_im)
+ *   ATM_STAGE_RESTRICT   residual at the C-points of level l, injection v^{l+1},
+ *                        FAS right-hand side g^{l+1} and u^{l+1} = v^{l+1}
+ *   ATM_STAGE_COARSEST   local chains (AT-MGRIT) or sequential solve (MGRIT)
+ *                        on the coarsest level
+ *   ATM_STAGE_CORRECT    u^l_C += u^{l+1} - v^{l+1}
+ * `level` is ignored for ATM_STAGE_COARSEST. */
+enum { ATM_STAGE_F_RELAX = 0, ATM_STAGE_C_RELAX = 1, ATM_STAGE_RESTRICT = 2,
+       ATM_STAGE_COARSEST = 3, ATM_STAGE_CORRECT = 4 };
+atm_status atm_run_stage(atm_handle *h, int stage, int level);
+
+/* Level arrays: U iterate, V injected approximation, R injected residual,
+ * G right-hand side (levels >= 1; level 0 has g_0 = u_0 and g_i = 0). */
+enum { ATM_ARRAY_U = 0, ATM_ARRAY_V = 1, ATM_ARRAY_R = 2, ATM_ARRAY_G = 3 };
+
+/* Copy `count` states starting at t0 of a level array to / from an FP64
+ * device buffer (converted to or from the working precision). */
+atm_status atm_level_read(atm_handle *h, int level, int array, int t0, int count, double *d_dst);
+atm_status atm_level_write(atm_handle *h, int level, int array, int t0, int count,
+                           const double *d_src);
+
+/* Number of time points on `level`, or -1 for an invalid level. */
+int atm_level_points(const atm_handle *h, int level);
+
+/* Kernel launches issued by the last atm_solve (graph replays count the
+ * kernels inside the graph). */
+long long atm_last_launch_count(const atm_handle *h);
+
+/* Message of the calling thread's last error ("" if none). */
+const char *atm_last_error(void);
+
+void atm_destroy(atm_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ATM_H */

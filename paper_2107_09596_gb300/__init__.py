@@ -1,0 +1,271 @@
+"""GB300 (sm_103a) AT-MGRIT space-time sweep (arXiv 2107.09596).
+
+Thin ctypes binding over ``libatm.so`` (``include/atm.h``): argument
+marshalling only.  Every step of the sweep runs in the library's CUDA kernels;
+there is no CPU fallback -- importing the binding without the built library on
+a machine raises.  PyTorch provides device memory (the workspace and state
+buffers) and the CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+HEAT1D, HEAT2D, ALLEN_CAHN = 0, 1, 2
+PROP_SPLIT_BE, PROP_PR_ADI = 0, 1
+SEQUENTIAL, MGRIT, AT_MGRIT = 0, 1, 2
+FP64, FP32, FP32_REFINED = 0, 1, 2
+STAGE_F_RELAX, STAGE_C_RELAX, STAGE_RESTRICT, STAGE_COARSEST, STAGE_CORRECT = range(5)
+ARRAY_U, ARRAY_V, ARRAY_R, ARRAY_G = range(4)
+MAX_LEVELS = 8
+
+STATUS = {0: "ATM_OK", 1: "ATM_ERR_INVALID_ARG", 2: "ATM_ERR_CUDA", 3: "ATM_ERR_OOM",
+          4: "ATM_ERR_NOT_CONVERGED", 5: "ATM_ERR_DIVERGED", 6: "ATM_ERR_TIMEOUT",
+          7: "ATM_ERR_UNSUPPORTED"}
+
+
+class AtmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("lx", ctypes.c_double), ("ly", ctypes.c_double), ("dt", ctypes.c_double),
+                ("nt_points", ctypes.c_int), ("eps", ctypes.c_double)]
+
+
+class SolverDesc(ctypes.Structure):
+    _fields_ = [("algorithm", ctypes.c_int), ("levels", ctypes.c_int),
+                ("m", ctypes.c_int * MAX_LEVELS), ("k", ctypes.c_int), ("nu", ctypes.c_int),
+                ("fine_prop", ctypes.c_int), ("coarse_prop", ctypes.c_int),
+                ("reaction_substeps", ctypes.c_int * MAX_LEVELS),
+                ("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
+                ("precision", ctypes.c_int), ("use_graph", ctypes.c_int)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int),
+                ("initial_residual", ctypes.c_double), ("final_residual", ctypes.c_double),
+                ("time_ms", ctypes.c_double)]
+
+
+EXPORTS = ["atm_workspace_size", "atm_create", "atm_set_initial_condition",
+           "atm_set_initial_guess", "atm_solve", "atm_get_solution",
+           "atm_get_residual_history", "atm_apply_propagator", "atm_run_stage",
+           "atm_level_read", "atm_level_write", "atm_level_points",
+           "atm_last_launch_count", "atm_last_error", "atm_destroy"]
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libatm.so (building it with nvcc if absent and allowed)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise OSError(f"{path} is missing: run paper_2107_09596_gb300.build.build()")
+        _build.build()
+    L = ctypes.CDLL(path)
+    vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    L.atm_workspace_size.argtypes = [ctypes.POINTER(Problem), ctypes.POINTER(SolverDesc), ctypes.POINTER(ctypes.c_size_t)]
+    L.atm_create.argtypes = [ctypes.POINTER(Problem), ctypes.POINTER(SolverDesc), vp, ctypes.c_size_t, vp, ctypes.POINTER(vp)]
+    L.atm_set_initial_condition.argtypes = [vp, vp]
+    L.atm_set_initial_guess.argtypes = [vp, vp]
+    L.atm_solve.argtypes = [vp, ctypes.POINTER(Result)]
+    L.atm_get_solution.argtypes = [vp, i, i, vp]
+    L.atm_get_residual_history.argtypes = [vp, vp, i, ctypes.POINTER(i)]
+    L.atm_apply_propagator.argtypes = [vp, i, vp, vp, i]
+    L.atm_run_stage.argtypes = [vp, i, i]
+    L.atm_level_read.argtypes = [vp, i, i, i, i, vp]
+    L.atm_level_write.argtypes = [vp, i, i, i, i, vp]
+    L.atm_level_points.argtypes = [vp, i]
+    L.atm_level_points.restype = i
+    L.atm_last_launch_count.argtypes = [vp]
+    L.atm_last_launch_count.restype = ctypes.c_longlong
+    L.atm_last_error.restype = ctypes.c_char_p
+    L.atm_destroy.argtypes = [vp]
+    for name in EXPORTS:
+        if name not in ("atm_level_points", "atm_last_launch_count", "atm_last_error", "atm_destroy"):
+            getattr(L, name).restype = i
+    _lib = L
+    return L
+
+
+def _check(st: int, ok=(0,)):
+    if st not in ok:
+        raise AtmError(st, load().atm_last_error().decode())
+    return st
+
+
+def make_problem(kind, nx, ny=1, lx=1.0, ly=1.0, dt=1e-3, nt_points=65, eps=0.02) -> Problem:
+    p = Problem()
+    p.kind, p.nx, p.ny = kind, nx, ny
+    p.lx, p.ly, p.dt, p.nt_points, p.eps = lx, ly, dt, nt_points, eps
+    return p
+
+
+def make_solver(algorithm=AT_MGRIT, m=(8,), k=4, nu=1, fine_prop=PROP_PR_ADI,
+                coarse_prop=PROP_SPLIT_BE, reaction_substeps=None, tol=1e-10, max_iter=50,
+                precision=FP64, use_graph=True) -> SolverDesc:
+    s = SolverDesc()
+    s.algorithm = algorithm
+    s.levels = len(m) + 1
+    for j, mj in enumerate(m):
+        s.m[j] = mj
+    s.k, s.nu = k, nu
+    s.fine_prop, s.coarse_prop = fine_prop, coarse_prop
+    if reaction_substeps:
+        for j, v in enumerate(reaction_substeps):
+            s.reaction_substeps[j] = v
+    s.tol, s.max_iter, s.precision, s.use_graph = tol, max_iter, precision, int(use_graph)
+    return s
+
+
+def workspace_size(problem: Problem, solver: SolverDesc) -> int:
+    n = ctypes.c_size_t()
+    _check(load().atm_workspace_size(ctypes.byref(problem), ctypes.byref(solver), ctypes.byref(n)))
+    return n.value
+
+
+def _ptr(x) -> int:
+    """Data pointer of a torch tensor or a numpy array (no copy)."""
+    if hasattr(x, "data_ptr"):
+        assert x.is_contiguous()
+        return x.data_ptr()
+    assert isinstance(x, np.ndarray) and x.flags["C_CONTIGUOUS"]
+    return x.ctypes.data
+
+
+class Solver:
+    """One space-time problem and its solver, living in a torch-allocated workspace."""
+
+    def __init__(self, problem: Problem, solver: SolverDesc, device="cuda:0", stream=None):
+        import torch
+        self.torch = torch
+        self.problem, self.desc = problem, solver
+        self.device = torch.device(device)
+        # the library issues all work on its own (non-default) stream, which
+        # also allows CUDA-graph capture; calls are ordered against torch's
+        # current stream on entry and exit
+        self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
+        nbytes = workspace_size(problem, solver)
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        base = self.workspace.data_ptr()
+        aligned = (base + 255) // 256 * 256
+        self.handle = ctypes.c_void_p()
+        self._enter()
+        _check(load().atm_create(ctypes.byref(problem), ctypes.byref(solver), ctypes.c_void_p(aligned),
+                                 nbytes, ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(self.handle)))
+        self._leave()
+        self.state_shape = (problem.nx,) if problem.kind == HEAT1D else (problem.ny, problem.nx)
+
+    def _enter(self):
+        self.stream.wait_stream(self.torch.cuda.current_stream(self.device))
+
+    def _leave(self):
+        self.torch.cuda.current_stream(self.device).wait_stream(self.stream)
+
+    def close(self):
+        if getattr(self, "handle", None) and self.handle.value:
+            self.stream.synchronize()
+            load().atm_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _f64(self, x):
+        """Keep host numpy arrays as they are; make torch tensors contiguous float64."""
+        if hasattr(x, "data_ptr"):
+            return x.to(dtype=self.torch.float64).contiguous()
+        return np.ascontiguousarray(x, dtype=np.float64)
+
+    def set_initial_condition(self, u0):
+        u0 = self._f64(u0)
+        self._enter()
+        _check(load().atm_set_initial_condition(self.handle, ctypes.c_void_p(_ptr(u0))))
+        self._leave()
+        return u0
+
+    def set_initial_guess(self, u):
+        u = self._f64(u)
+        self._enter()
+        _check(load().atm_set_initial_guess(self.handle, ctypes.c_void_p(_ptr(u))))
+        self._leave()
+        return u
+
+    def solve(self, allow_not_converged=True) -> dict:
+        r = Result()
+        ok = (0, 4) if allow_not_converged else (0,)
+        self._enter()
+        st = _check(load().atm_solve(self.handle, ctypes.byref(r)), ok)
+        self._leave()
+        return {"status": STATUS[st], "iterations": r.iterations, "converged": bool(r.converged),
+                "initial_residual": r.initial_residual, "final_residual": r.final_residual,
+                "time_ms": r.time_ms, "launches": load().atm_last_launch_count(self.handle)}
+
+    def residual_history(self, cap=4096) -> np.ndarray:
+        buf = np.zeros(cap)
+        n = ctypes.c_int()
+        _check(load().atm_get_residual_history(self.handle, ctypes.c_void_p(buf.ctypes.data), cap, ctypes.byref(n)))
+        return buf[: n.value].copy()
+
+    def solution(self, t0=0, count=None, out=None):
+        """States t0..t0+count-1 as a float64 tensor on the device (or into `out`,
+        a device tensor or host numpy array)."""
+        if count is None:
+            count = self.level_points(0) - t0
+        if out is None:
+            out = self.torch.empty((count,) + self.state_shape, dtype=self.torch.float64, device=self.device)
+        self._enter()
+        _check(load().atm_get_solution(self.handle, t0, count, ctypes.c_void_p(_ptr(out))))
+        self._leave()
+        return out
+
+    def apply_propagator(self, level, x):
+        x = x.to(device=self.device, dtype=self.torch.float64).contiguous()
+        out = self.torch.empty_like(x)
+        self._enter()
+        _check(load().atm_apply_propagator(self.handle, level, ctypes.c_void_p(x.data_ptr()),
+                                           ctypes.c_void_p(out.data_ptr()), x.shape[0]))
+        self._leave()
+        return out
+
+    def run_stage(self, stage, level=0):
+        self._enter()
+        _check(load().atm_run_stage(self.handle, stage, level))
+        self._leave()
+
+    def level_read(self, level, array, t0=0, count=None):
+        if count is None:
+            count = self.level_points(level) - t0
+        out = self.torch.empty((count,) + self.state_shape, dtype=self.torch.float64, device=self.device)
+        self._enter()
+        _check(load().atm_level_read(self.handle, level, array, t0, count, ctypes.c_void_p(out.data_ptr())))
+        self._leave()
+        return out
+
+    def level_write(self, level, array, x, t0=0):
+        x = x.to(device=self.device, dtype=self.torch.float64).contiguous()
+        self._enter()
+        _check(load().atm_level_write(self.handle, level, array, t0, x.shape[0], ctypes.c_void_p(x.data_ptr())))
+        self._leave()
+
+    def level_points(self, level) -> int:
+        return load().atm_level_points(self.handle, level)

@@ -1,0 +1,170 @@
+// atm_api.cu -- the extern "C" entry points declared in include/atm.h.
+// Argument marshalling and validation only; every step of the sweep runs in
+// the kernels of atm_kernels.cuh, driven by the plan in atm_host.cuh.
+#include "atm_host.cuh"
+
+struct atm_handle {
+    atm::PlanBase *p;
+};
+
+namespace {
+
+template <typename T>
+atm_status plan_size(const atm_problem *pb, const atm_solver *sv, size_t *bytes)
+{
+    atm::Plan<T> p;
+    p.pb = *pb;
+    p.sv = *sv;
+    atm_status s;
+    size_t need = p.measure(&s);
+    if (s != ATM_OK) return s;
+    *bytes = need;
+    return ATM_OK;
+}
+
+template <typename T>
+atm_status plan_create(const atm_problem *pb, const atm_solver *sv, void *ws, size_t bytes, void *stream,
+                       atm_handle **out)
+{
+    atm::Plan<T> *p = new atm::Plan<T>();
+    p->pb = *pb;
+    p->sv = *sv;
+    p->st = reinterpret_cast<cudaStream_t>(stream);
+    atm_status s;
+    size_t need = p->measure(&s);
+    if (s == ATM_OK && bytes < need)
+        s = atm::fail(ATM_ERR_OOM, "workspace of %zu bytes is smaller than the %zu bytes needed", bytes, need);
+    if (s == ATM_OK) {
+        const int b = p->maxbatch, np = p->npartials_max;
+        s = p->layout(reinterpret_cast<uintptr_t>(ws), b, np);
+        if (s == ATM_OK && p->off != need) s = atm::fail(ATM_ERR_INVALID_ARG, "internal layout mismatch");
+    }
+    if (s == ATM_OK) s = p->finish_create();
+    if (s != ATM_OK) {
+        delete p;
+        return s;
+    }
+    *out = new atm_handle{p};
+    return ATM_OK;
+}
+
+atm_status check_args(const atm_problem *pb, const atm_solver *sv)
+{
+    if (!pb || !sv) return atm::fail(ATM_ERR_INVALID_ARG, "null problem or solver");
+    if (sv->precision == ATM_FP32_REFINED)
+        return atm::fail(ATM_ERR_UNSUPPORTED, "FP32 propagation with FP64 refinement is not built in this library");
+    if (sv->precision != ATM_FP64 && sv->precision != ATM_FP32)
+        return atm::fail(ATM_ERR_INVALID_ARG, "unknown precision %d", sv->precision);
+    return ATM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+atm_status atm_workspace_size(const atm_problem *prob, const atm_solver *solver, size_t *bytes)
+{
+    atm::last_error().clear();
+    ATM_TRY(check_args(prob, solver));
+    if (!bytes) return atm::fail(ATM_ERR_INVALID_ARG, "null bytes");
+    return solver->precision == ATM_FP64 ? plan_size<double>(prob, solver, bytes) : plan_size<float>(prob, solver, bytes);
+}
+
+atm_status atm_create(const atm_problem *prob, const atm_solver *solver, void *d_workspace, size_t bytes,
+                      void *cuda_stream, atm_handle **out)
+{
+    atm::last_error().clear();
+    ATM_TRY(check_args(prob, solver));
+    if (!out) return atm::fail(ATM_ERR_INVALID_ARG, "null out");
+    *out = nullptr;
+    if (!d_workspace) return atm::fail(ATM_ERR_INVALID_ARG, "null workspace");
+    if (reinterpret_cast<uintptr_t>(d_workspace) % 256 != 0)
+        return atm::fail(ATM_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    return solver->precision == ATM_FP64
+               ? plan_create<double>(prob, solver, d_workspace, bytes, cuda_stream, out)
+               : plan_create<float>(prob, solver, d_workspace, bytes, cuda_stream, out);
+}
+
+atm_status atm_set_initial_condition(atm_handle *h, const double *u0)
+{
+    if (!h) return atm::fail(ATM_ERR_INVALID_ARG, "null handle");
+    return h->p->set_state(0, 1, u0);
+}
+
+atm_status atm_set_initial_guess(atm_handle *h, const double *u)
+{
+    if (!h || !u) return atm::fail(ATM_ERR_INVALID_ARG, "null argument");
+    const int n = h->p->level_points(0);
+    const size_t nsp = h->p->pb.kind == ATM_HEAT1D ? (size_t)h->p->pb.nx : (size_t)h->p->pb.nx * h->p->pb.ny;
+    return h->p->set_state(1, n - 1, u + nsp);
+}
+
+atm_status atm_solve(atm_handle *h, atm_result *out)
+{
+    if (!h) return atm::fail(ATM_ERR_INVALID_ARG, "null handle");
+    atm::last_error().clear();
+    return h->p->solve(out);
+}
+
+atm_status atm_get_solution(atm_handle *h, int t0, int count, double *dst)
+{
+    if (!h) return atm::fail(ATM_ERR_INVALID_ARG, "null handle");
+    return h->p->get_state(t0, count, dst);
+}
+
+atm_status atm_get_residual_history(atm_handle *h, double *hist, int cap, int *n)
+{
+    if (!h || !n || (cap > 0 && !hist)) return atm::fail(ATM_ERR_INVALID_ARG, "null argument");
+    const int m = (int)h->p->hist.size() < cap ? (int)h->p->hist.size() : cap;
+    for (int i = 0; i < m; ++i) hist[i] = h->p->hist[i];
+    *n = m;
+    return ATM_OK;
+}
+
+atm_status atm_apply_propagator(atm_handle *h, int level, const double *in, double *out, int nstates)
+{
+    if (!h) return atm::fail(ATM_ERR_INVALID_ARG, "null handle");
+    return h->p->apply_prop(level, in, out, nstates);
+}
+
+atm_status atm_run_stage(atm_handle *h, int stage, int level)
+{
+    if (!h) return atm::fail(ATM_ERR_INVALID_ARG, "null handle");
+    return h->p->run_stage(stage, level);
+}
+
+atm_status atm_level_read(atm_handle *h, int level, int array, int t0, int count, double *d_dst)
+{
+    if (!h) return atm::fail(ATM_ERR_INVALID_ARG, "null handle");
+    return h->p->level_io(level, array, t0, count, d_dst, false);
+}
+
+atm_status atm_level_write(atm_handle *h, int level, int array, int t0, int count, const double *d_src)
+{
+    if (!h) return atm::fail(ATM_ERR_INVALID_ARG, "null handle");
+    return h->p->level_io(level, array, t0, count, const_cast<double *>(d_src), true);
+}
+
+int atm_level_points(const atm_handle *h, int level)
+{
+    return h ? h->p->level_points(level) : -1;
+}
+
+long long atm_last_launch_count(const atm_handle *h)
+{
+    return h ? h->p->launches : 0;
+}
+
+const char *atm_last_error(void)
+{
+    return atm::last_error().c_str();
+}
+
+void atm_destroy(atm_handle *h)
+{
+    if (!h) return;
+    delete h->p;
+    delete h;
+}
+
+}  // extern "C"

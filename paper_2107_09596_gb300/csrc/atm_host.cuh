@@ -1,0 +1,933 @@
+// atm_host.cuh -- host-side plan of the AT-MGRIT sweep: propagator
+// coefficients, launch tables (the V-cycle of Algorithm 2 unrolled into
+// batched launches), kernel dispatch and CUDA-graph replay.  Included by the
+// C-ABI translation unit only.
+#pragma once
+
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "../../include/atm.h"
+#include "atm_kernels.cuh"
+
+namespace atm {
+
+// ---------------------------------------------------------------------------
+// Errors
+// ---------------------------------------------------------------------------
+inline std::string &last_error()
+{
+    static thread_local std::string s;
+    return s;
+}
+
+inline atm_status fail(atm_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    last_error() = buf;
+    return st;
+}
+
+#define ATM_CK(call)                                                                        \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return ::atm::fail(ATM_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+#define ATM_TRY(expr)                         \
+    do {                                      \
+        atm_status s_ = (expr);               \
+        if (s_ != ATM_OK) return s_;          \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// Line-operator coefficients (host, FP64), converted to the working type.
+// d x_i - a (x_{i-1} + x_{i+1}) = f_i  ==  kappa (1 - rho S)(1 - rho S^-1) x = f
+// ---------------------------------------------------------------------------
+struct LineCoef {
+    double a = 0, rho = 0, kappa = 1;
+    int n = 0, chunk = 1;
+    bool periodic = true;
+    std::vector<double> w;   // Dirichlet rank-one vector
+    double sigma = 0;
+};
+
+inline LineCoef make_line(double a, int n, bool periodic, int chunk)
+{
+    LineCoef L;
+    L.a = a;
+    L.n = n;
+    L.periodic = periodic;
+    L.chunk = chunk;
+    const double s = std::sqrt(1.0 + 4.0 * a);
+    L.rho = 2.0 * a / (1.0 + 2.0 * a + s);
+    L.kappa = 0.5 * (1.0 + 2.0 * a + s);
+    if (!periodic) {
+        // w = (kappa L U)^-1 e_0 by the two recurrences; sigma = a rho / (1 + a rho w_0)
+        std::vector<double> z(n);
+        z[0] = 1.0 / L.kappa;
+        for (int i = 1; i < n; ++i) z[i] = L.rho * z[i - 1];
+        L.w.assign(n, 0.0);
+        L.w[n - 1] = z[n - 1];
+        for (int i = n - 2; i >= 0; --i) L.w[i] = L.rho * L.w[i + 1] + z[i];
+        L.sigma = a * L.rho / (1.0 + a * L.rho * L.w[0]);
+    }
+    return L;
+}
+
+template <typename T>
+inline TriCoef<T> to_coef(const LineCoef &L, const T *d_w)
+{
+    TriCoef<T> c;
+    std::memset(&c, 0, sizeof(c));
+    c.rho = (T)L.rho;
+    for (int i = 0; i <= kMaxChunk; ++i) c.pw[i] = (T)std::pow(L.rho, (double)i);
+    for (int j = 0; j < 6; ++j) c.scan[j] = (T)std::pow(L.rho, (double)L.chunk * (double)(1 << j));
+    for (int j = 0; j <= 32; ++j) c.chunk_pw[j] = (T)std::pow(L.rho, (double)L.chunk * (double)j);
+    c.inv1m = L.periodic ? (T)(1.0 / (1.0 - std::pow(L.rho, (double)L.n))) : (T)0;
+    c.sigma = (T)L.sigma;
+    c.w = d_w;
+    return c;
+}
+
+// ---------------------------------------------------------------------------
+// Kernel dispatch tables
+// ---------------------------------------------------------------------------
+template <typename T>
+using SweepFn = void (*)(SweepArgs<T>);
+
+template <typename T, bool DIR, bool PR, bool RE, bool FIN>
+inline SweepFn<T> pick_row(int C)
+{
+    switch (C) {
+    case 1: return row_sweep_kernel<T, 1, DIR, PR, RE, FIN>;
+    case 2: return row_sweep_kernel<T, 2, DIR, PR, RE, FIN>;
+    case 4: return row_sweep_kernel<T, 4, DIR, PR, RE, FIN>;
+    case 8: return row_sweep_kernel<T, 8, DIR, PR, RE, FIN>;
+    case 16: return row_sweep_kernel<T, 16, DIR, PR, RE, FIN>;
+    case 32: return row_sweep_kernel<T, 32, DIR, PR, RE, FIN>;
+    default: return nullptr;
+    }
+}
+
+template <typename T>
+inline SweepFn<T> row_kernel(int C, bool dirichlet, bool pr, bool react)
+{
+    if (dirichlet) return pick_row<T, true, false, false, true>(C);
+    if (pr) return react ? pick_row<T, false, true, true, false>(C) : pick_row<T, false, true, false, false>(C);
+    return react ? pick_row<T, false, false, true, false>(C) : pick_row<T, false, false, false, false>(C);
+}
+
+template <typename T>
+inline SweepFn<T> col_kernel(int CY, bool pr)
+{
+    if (CY == 16) return pr ? col_sweep_kernel<T, 16, true> : col_sweep_kernel<T, 16, false>;
+    if (CY == 32) return pr ? col_sweep_kernel<T, 32, true> : col_sweep_kernel<T, 32, false>;
+    if constexpr (sizeof(T) == 4) {
+        if (CY == 64) return pr ? col_sweep_kernel<T, 64, true> : col_sweep_kernel<T, 64, false>;
+    }
+    return nullptr;
+}
+
+}  // namespace atm
+
+namespace atm {
+
+enum { L_SWEEP = 0, L_AXPY = 1, L_NORM = 2 };
+
+// One kernel launch (a sweep is one launch in 1D, two in 2D) of a phase.
+struct LaunchRec {
+    int type = L_SWEEP;
+    int level = 0;
+    size_t job_index = 0;
+    int njobs = 0;
+    int neg = 0;
+    double *partials = nullptr;
+    int npartials = 0;
+    double *norm_out = nullptr;
+};
+
+using Phase = std::vector<LaunchRec>;
+
+// Virtual interface so the C ABI can hold plans of either working precision.
+struct PlanBase {
+    atm_problem pb{};
+    atm_solver sv{};
+    cudaStream_t st = nullptr;
+    std::vector<double> hist;
+    long long launches = 0;
+    virtual ~PlanBase() {}
+    virtual atm_status finish_create() = 0;
+    virtual atm_status set_state(int t0, int count, const double *src) = 0;
+    virtual atm_status get_state(int t0, int count, double *dst) = 0;
+    virtual atm_status solve(atm_result *res) = 0;
+    virtual atm_status apply_prop(int level, const double *in, double *out, int n) = 0;
+    virtual atm_status run_stage(int stage, int level) = 0;
+    virtual atm_status level_io(int level, int array, int t0, int count, double *buf, bool write) = 0;
+    virtual int level_points(int level) const = 0;
+};
+
+template <typename T>
+struct Level {
+    int N = 0, m = 0, NC = 0;
+    T *u = nullptr, *v = nullptr, *r = nullptr, *g = nullptr;
+    SweepArgs<T> args{};
+    SweepFn<T> row = nullptr, col = nullptr;
+    int rows_per_cta = 8, col_warps = 1, col_chunk = 16;
+    size_t row_smem = 0;
+    T *dir_w = nullptr;
+    std::vector<double> dir_w_host;
+};
+
+inline bool pow2_in(int v, int lo, int hi)
+{
+    if (v < lo || v > hi) return false;
+    return (v & (v - 1)) == 0;
+}
+
+template <typename T>
+struct Plan : PlanBase {
+    int L = 1;
+    int nsp = 0;
+    bool is1d = false;
+    int maxbatch = 16;
+    // workspace layout
+    uintptr_t base = 0;
+    size_t off = 0;
+    std::vector<Level<T>> lv;
+    T *yC = nullptr;        // level-0 C-relaxation values (FCF)
+    T *mid = nullptr;       // row-sweep results, maxbatch states
+    T *sin = nullptr, *sout = nullptr;   // FP64 <-> T staging for atm_apply_propagator
+    double *stage64 = nullptr;           // one FP64 state for host transfers
+    double *partials = nullptr;
+    int npartials_max = 0;
+    double *norm_cur = nullptr;
+    std::vector<Job<T>> jobs;
+    std::vector<AxpyJob<T>> ajobs;
+    Job<T> *d_jobs = nullptr;
+    AxpyJob<T> *d_ajobs = nullptr;
+    Job<T> *d_dyn = nullptr;             // jobs of atm_apply_propagator
+    Phase passA, rest, seq;
+    std::vector<Phase> st_f, st_c, st_r, st_corr;
+    Phase st_coarse;
+    cudaGraphExec_t gA = nullptr, gIter = nullptr, gSeq = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+
+    ~Plan() override
+    {
+        if (gA) cudaGraphExecDestroy(gA);
+        if (gIter) cudaGraphExecDestroy(gIter);
+        if (gSeq) cudaGraphExecDestroy(gSeq);
+        if (ev0) cudaEventDestroy(ev0);
+        if (ev1) cudaEventDestroy(ev1);
+    }
+
+    template <typename U>
+    U *take(size_t count)
+    {
+        off = (off + 255) & ~(size_t)255;
+        U *p = reinterpret_cast<U *>(base + off);
+        off += count * sizeof(U);
+        return p;
+    }
+
+    T *st_ptr(T *arr, int t) const { return arr + (size_t)t * nsp; }
+    T *gl(int l, int t) const { return l == 0 ? nullptr : st_ptr(lv[l].g, t); }
+
+    // ---------------- validation and layout ----------------
+    atm_status validate() const
+    {
+        if (pb.kind < ATM_HEAT1D || pb.kind > ATM_ALLEN_CAHN) return fail(ATM_ERR_INVALID_ARG, "unknown problem kind %d", pb.kind);
+        if (pb.nt_points < 2) return fail(ATM_ERR_INVALID_ARG, "nt_points must be >= 2");
+        if (!(pb.dt > 0) || !(pb.lx > 0) || (!is1d && !(pb.ly > 0))) return fail(ATM_ERR_INVALID_ARG, "dt, lx, ly must be > 0");
+        if (pb.kind == ATM_ALLEN_CAHN && !(pb.eps > 0)) return fail(ATM_ERR_INVALID_ARG, "eps must be > 0");
+        if (is1d) {
+            if (pb.nx < 2 || pb.nx > 1024) return fail(ATM_ERR_INVALID_ARG, "heat1d needs 2 <= nx <= 1024");
+        } else {
+            const int nmax = sizeof(T) == 4 ? 1024 : 512;
+            if (!pow2_in(pb.nx, 32, nmax) || !pow2_in(pb.ny, 32, nmax))
+                return fail(ATM_ERR_INVALID_ARG, "2D grids need nx, ny powers of two in [32, %d] for this precision", nmax);
+        }
+        if (sv.algorithm < ATM_SEQUENTIAL || sv.algorithm > ATM_AT_MGRIT) return fail(ATM_ERR_INVALID_ARG, "unknown algorithm");
+        if (sv.algorithm != ATM_SEQUENTIAL) {
+            if (sv.levels < 2 || sv.levels > ATM_MAX_LEVELS) return fail(ATM_ERR_INVALID_ARG, "levels must be in [2, %d]", ATM_MAX_LEVELS);
+            int N = pb.nt_points;
+            for (int l = 0; l + 1 < sv.levels; ++l) {
+                if (sv.m[l] < 2) return fail(ATM_ERR_INVALID_ARG, "m[%d] must be >= 2", l);
+                if (N < sv.m[l] + 1) return fail(ATM_ERR_INVALID_ARG, "level %d has %d points, fewer than m+1", l, N);
+                N = (N - 1) / sv.m[l] + 1;
+            }
+            if (sv.nu < 0 || sv.nu > 1) return fail(ATM_ERR_INVALID_ARG, "nu must be 0 (F) or 1 (FCF)");
+            if (sv.algorithm == ATM_AT_MGRIT && sv.k < 1) return fail(ATM_ERR_INVALID_ARG, "k must be >= 1");
+            if (sv.max_iter < 0) return fail(ATM_ERR_INVALID_ARG, "max_iter must be >= 0");
+        }
+        for (int l = 0; l < ATM_MAX_LEVELS; ++l)
+            if (sv.reaction_substeps[l] < 0) return fail(ATM_ERR_INVALID_ARG, "reaction_substeps must be >= 0");
+        if (!is1d) {
+            if (sv.fine_prop < 0 || sv.fine_prop > 1 || sv.coarse_prop < 0 || sv.coarse_prop > 1)
+                return fail(ATM_ERR_INVALID_ARG, "unknown propagator");
+        }
+        return ATM_OK;
+    }
+
+    void setup_level_op(int l)
+    {
+        Level<T> &Lv = lv[l];
+        double D = pb.dt;
+        int prod = 1;
+        for (int j = 0; j < l; ++j) { D *= (double)sv.m[j]; prod *= sv.m[j]; }
+        const int nsub = sv.reaction_substeps[l] > 0 ? sv.reaction_substeps[l] : prod;
+        SweepArgs<T> a;
+        std::memset(&a, 0, sizeof(a));
+        a.nx = pb.nx;
+        a.ny = is1d ? 1 : pb.ny;
+        if (is1d) {
+            const double dx = pb.lx / (pb.nx + 1);
+            int C = 1;
+            while (32 * C < pb.nx) C *= 2;
+            LineCoef cx = make_line(D / (dx * dx), pb.nx, false, C);
+            a.cx = to_coef<T>(cx, Lv.dir_w);
+            a.rx0 = (T)(1.0 / cx.kappa);
+            Lv.dir_w_host = cx.w;
+            Lv.row = row_kernel<T>(C, true, false, false);
+            Lv.rows_per_cta = 1;
+        } else {
+            const double dx = pb.lx / pb.nx, dy = pb.ly / pb.ny;
+            const int prop = (l == 0) ? sv.fine_prop : sv.coarse_prop;
+            const bool pr = (prop == ATM_PROP_PR_ADI);
+            const double f = pr ? 0.5 * D : D;
+            const double ax = f / (dx * dx), ay = f / (dy * dy);
+            const int C = pb.nx / 32;
+            const int CY = pb.ny <= 256 ? 16 : pb.ny / 16;
+            LineCoef cx = make_line(ax, pb.nx, true, C);
+            LineCoef cy = make_line(ay, pb.ny, true, CY);
+            a.cx = to_coef<T>(cx, nullptr);
+            a.cy = to_coef<T>(cy, nullptr);
+            if (pr) {
+                a.rx0 = (T)((1.0 - 2.0 * ay) / cx.kappa);
+                a.rx1 = (T)(ay / cx.kappa);
+                a.cy0 = (T)((1.0 - 2.0 * ax) / cy.kappa);
+                a.cy1 = (T)(ax / cy.kappa);
+            } else {
+                a.rx0 = (T)(1.0 / cx.kappa);
+                a.cy0 = (T)(1.0 / cy.kappa);
+            }
+            const bool react = (pb.kind == ATM_ALLEN_CAHN);
+            if (react) {
+                a.react = (T)((D / nsub) / (pb.eps * pb.eps));
+                a.nsub = nsub;
+            }
+            Lv.row = row_kernel<T>(C, false, pr, react);
+            Lv.col = col_kernel<T>(CY, pr);
+            Lv.rows_per_cta = 8;
+            Lv.col_chunk = CY;
+            Lv.col_warps = pb.ny / CY;
+            Lv.row_smem = pr ? (size_t)(Lv.rows_per_cta + 2) * pb.nx * sizeof(T) : 0;
+        }
+        Lv.args = a;
+    }
+
+    // ---------------- phase builders ----------------
+    int blocks_per_job(int l) const { return is1d ? 1 : pb.nx / 32; }
+
+    void add_sweep(Phase &ph, int l, std::vector<Job<T>> &&js, int neg, bool norm)
+    {
+        if (js.empty()) return;
+        LaunchRec r;
+        r.type = L_SWEEP;
+        r.level = l;
+        r.job_index = jobs.size();
+        r.njobs = (int)js.size();
+        r.neg = neg;
+        if (norm) {
+            r.partials = partials;
+            r.npartials = r.njobs * blocks_per_job(l);
+            if (r.npartials > npartials_max) npartials_max = r.npartials;
+        }
+        if (r.njobs > maxbatch) maxbatch = r.njobs;
+        jobs.insert(jobs.end(), js.begin(), js.end());
+        ph.push_back(r);
+    }
+
+    void add_axpy(Phase &ph, std::vector<AxpyJob<T>> &&js)
+    {
+        if (js.empty()) return;
+        LaunchRec r;
+        r.type = L_AXPY;
+        r.job_index = ajobs.size();
+        r.njobs = (int)js.size();
+        ajobs.insert(ajobs.end(), js.begin(), js.end());
+        ph.push_back(r);
+    }
+
+    void add_norm(Phase &ph, int count)
+    {
+        LaunchRec r;
+        r.type = L_NORM;
+        r.partials = partials;
+        r.npartials = count;
+        r.norm_out = norm_cur;
+        ph.push_back(r);
+    }
+
+    static Job<T> job(const T *in, T *out, const T *g = nullptr, const T *h = nullptr,
+                      const T *sub = nullptr, T *out2 = nullptr)
+    {
+        Job<T> j;
+        j.in = in; j.out = out; j.g = g; j.h = h; j.sub = sub; j.out2 = out2;
+        return j;
+    }
+
+    static AxpyJob<T> ajob(T *out, const T *a, const T *b = nullptr, const T *c = nullptr)
+    {
+        AxpyJob<T> j;
+        j.out = out; j.a = a; j.b = b; j.c = c;
+        return j;
+    }
+
+    // F-relaxation of level l: u_{im+j} = Phi(u_{im+j-1}) + g_{im+j}, j = 1..m-1,
+    // all intervals i in one launch per j.  resid: 0 none; 1 residual at C-points
+    // i >= 1 with the C-relaxation value stored in yC (level 0); 2 residual
+    // stored in lv[l+1].r.  norm: accumulate ||r||^2.
+    void add_frelax(Phase &ph, int l, int resid, bool norm)
+    {
+        Level<T> &Lv = lv[l];
+        const int N = Lv.N, m = Lv.m, NC = Lv.NC;
+        for (int j = 1; j < m; ++j) {
+            std::vector<Job<T>> js;
+            for (int i = 0; i < NC; ++i) {
+                const int t = i * m + j;
+                if (t < N) js.push_back(job(st_ptr(Lv.u, t - 1), st_ptr(Lv.u, t), gl(l, t)));
+            }
+            add_sweep(ph, l, std::move(js), 0, false);
+        }
+        if (resid) {
+            std::vector<Job<T>> js;
+            for (int i = 1; i < NC; ++i) {
+                const int t = i * m;
+                js.push_back(job(st_ptr(Lv.u, t - 1), resid == 1 ? st_ptr(yC, i) : nullptr, gl(l, t), nullptr,
+                                 st_ptr(Lv.u, t), resid == 2 ? st_ptr(lv[l + 1].r, i) : nullptr));
+            }
+            const int n = (int)js.size();
+            add_sweep(ph, l, std::move(js), 0, norm);
+            if (norm) add_norm(ph, n * blocks_per_job(l));
+        }
+    }
+
+    // C-relaxation of level l: u_0 = g_0 (levels >= 1), u_im = Phi(u_im-1) + g_im.
+    void add_crelax(Phase &ph, int l)
+    {
+        Level<T> &Lv = lv[l];
+        if (l > 0) add_axpy(ph, {ajob(Lv.u, Lv.g)});
+        std::vector<Job<T>> js;
+        for (int i = 1; i < Lv.NC; ++i)
+            js.push_back(job(st_ptr(Lv.u, i * Lv.m - 1), st_ptr(Lv.u, i * Lv.m), gl(l, i * Lv.m)));
+        add_sweep(ph, l, std::move(js), 0, false);
+    }
+
+    // Residual at the C-points i >= 1 of level l into lv[l+1].r.
+    void add_residual(Phase &ph, int l)
+    {
+        Level<T> &Lv = lv[l];
+        std::vector<Job<T>> js;
+        for (int i = 1; i < Lv.NC; ++i) {
+            const int t = i * Lv.m;
+            js.push_back(job(st_ptr(Lv.u, t - 1), nullptr, gl(l, t), nullptr, st_ptr(Lv.u, t), st_ptr(lv[l + 1].r, i)));
+        }
+        add_sweep(ph, l, std::move(js), 0, false);
+    }
+
+    // Injection and FAS right-hand side of level l+1 (residual r_i, i >= 1, given):
+    // r_0 = g_0 - u_0, v = u^{l+1} = R_I u, g^{l+1}_i = v_i - Phi_{l+1}(v_{i-1}) + r_i,
+    // g^{l+1}_0 = v_0 + r_0.
+    void add_restrict(Phase &ph, int l)
+    {
+        Level<T> &F = lv[l];
+        Level<T> &C = lv[l + 1];
+        add_axpy(ph, {l == 0 ? ajob(C.r, nullptr) : ajob(C.r, nullptr, F.g, F.u)});
+        std::vector<AxpyJob<T>> cp;
+        for (int i = 0; i < C.N; ++i) {
+            cp.push_back(ajob(st_ptr(C.v, i), st_ptr(F.u, i * F.m)));
+            cp.push_back(ajob(st_ptr(C.u, i), st_ptr(F.u, i * F.m)));
+        }
+        add_axpy(ph, std::move(cp));
+        std::vector<Job<T>> js;
+        for (int i = 1; i < C.N; ++i)
+            js.push_back(job(st_ptr(C.v, i - 1), st_ptr(C.g, i), st_ptr(C.v, i), st_ptr(C.r, i)));
+        add_sweep(ph, l + 1, std::move(js), 1, false);
+        add_axpy(ph, {ajob(C.g, C.v, C.r)});
+    }
+
+    // Coarsest level: AT-MGRIT local chains, or MGRIT's sequential solve.
+    void add_coarsest(Phase &ph)
+    {
+        const int l = L - 1;
+        Level<T> &C = lv[l];
+        if (sv.algorithm == ATM_AT_MGRIT) {
+            const int k = sv.k;
+            std::vector<AxpyJob<T>> init;
+            for (int p = 0; p < C.N; ++p) {
+                const int j0 = p - k + 1 > 0 ? p - k + 1 : 0;
+                init.push_back(ajob(st_ptr(C.u, p), st_ptr(C.v, j0), st_ptr(C.r, j0)));
+            }
+            add_axpy(ph, std::move(init));
+            for (int s = 1; s < k; ++s) {
+                std::vector<Job<T>> js;
+                for (int p = 0; p < C.N; ++p) {
+                    const int j0 = p - k + 1 > 0 ? p - k + 1 : 0;
+                    if (p - j0 >= s) js.push_back(job(st_ptr(C.u, p), st_ptr(C.u, p), st_ptr(C.g, j0 + s)));
+                }
+                add_sweep(ph, l, std::move(js), 0, false);
+            }
+        } else {
+            add_axpy(ph, {ajob(C.u, C.g)});
+            for (int j = 1; j < C.N; ++j)
+                add_sweep(ph, l, {job(st_ptr(C.u, j - 1), st_ptr(C.u, j), st_ptr(C.g, j))}, 0, false);
+        }
+    }
+
+    // u^l_C += u^{l+1} - v^{l+1}
+    void add_correct(Phase &ph, int l)
+    {
+        std::vector<AxpyJob<T>> js;
+        for (int i = 0; i < lv[l + 1].N; ++i)
+            js.push_back(ajob(st_ptr(lv[l].u, i * lv[l].m), st_ptr(lv[l].u, i * lv[l].m), st_ptr(lv[l + 1].u, i),
+                              st_ptr(lv[l + 1].v, i)));
+        add_axpy(ph, std::move(js));
+    }
+
+    // Algorithm 2 on level l >= 1 (one V-cycle visit).
+    void add_level_cycle(Phase &ph, int l)
+    {
+        if (l == L - 1) {
+            add_coarsest(ph);
+            return;
+        }
+        if (sv.nu == 1) {
+            add_frelax(ph, l, 0, false);
+            add_crelax(ph, l);
+        }
+        add_frelax(ph, l, 2, false);
+        add_restrict(ph, l);
+        add_level_cycle(ph, l + 1);
+        add_correct(ph, l);
+        add_frelax(ph, l, 0, false);
+    }
+
+    void build_phases()
+    {
+        jobs.clear();
+        ajobs.clear();
+        passA.clear(); rest.clear(); seq.clear(); st_coarse.clear();
+        st_f.assign(L, Phase()); st_c.assign(L, Phase()); st_r.assign(L, Phase()); st_corr.assign(L, Phase());
+        if (sv.algorithm == ATM_SEQUENTIAL) {
+            for (int j = 1; j < pb.nt_points; ++j)
+                add_sweep(seq, 0, {job(st_ptr(lv[0].u, j - 1), st_ptr(lv[0].u, j))}, 0, false);
+            return;
+        }
+        // level 0: pass A = F-relaxation + residual (norm); the rest of the cycle
+        add_frelax(passA, 0, sv.nu == 1 ? 1 : 2, true);
+        if (sv.nu == 1) {
+            std::vector<AxpyJob<T>> cp;
+            for (int i = 1; i < lv[0].NC; ++i) cp.push_back(ajob(st_ptr(lv[0].u, i * lv[0].m), st_ptr(yC, i)));
+            add_axpy(rest, std::move(cp));
+            add_frelax(rest, 0, 2, false);
+        }
+        add_restrict(rest, 0);
+        add_level_cycle(rest, 1);
+        add_correct(rest, 0);
+        // building blocks for atm_run_stage
+        for (int l = 0; l < L; ++l) {
+            if (l + 1 < L) {
+                add_frelax(st_f[l], l, 0, false);
+                add_crelax(st_c[l], l);
+                add_residual(st_r[l], l);
+                add_restrict(st_r[l], l);
+                add_correct(st_corr[l], l);
+            }
+        }
+        add_coarsest(st_coarse);
+    }
+
+    // ---------------- layout (two passes: sizes, then real pointers) ----------------
+    // With ws == 0 the pass only measures; the second pass reuses the maxima.
+    atm_status layout(uintptr_t ws, int batch_hint, int npart_hint)
+    {
+        base = ws;
+        off = 0;
+        is1d = (pb.kind == ATM_HEAT1D);
+        nsp = is1d ? pb.nx : pb.nx * pb.ny;
+        ATM_TRY(validate());
+        L = (sv.algorithm == ATM_SEQUENTIAL) ? 1 : sv.levels;
+        lv.assign(L, Level<T>());
+        lv[0].N = pb.nt_points;
+        for (int l = 0; l + 1 < L; ++l) {
+            lv[l].m = sv.m[l];
+            lv[l].NC = (lv[l].N - 1) / sv.m[l] + 1;
+            lv[l + 1].N = lv[l].NC;
+        }
+        lv[0].u = take<T>((size_t)lv[0].N * nsp);
+        if (L > 1 && sv.nu == 1) yC = take<T>((size_t)lv[0].NC * nsp);
+        for (int l = 1; l < L; ++l) {
+            const size_t b = (size_t)lv[l].N * nsp;
+            lv[l].u = take<T>(b);
+            lv[l].v = take<T>(b);
+            lv[l].r = take<T>(b);
+            lv[l].g = take<T>(b);
+        }
+        maxbatch = batch_hint;
+        npartials_max = npart_hint;
+        if (!is1d) mid = take<T>((size_t)maxbatch * nsp);
+        if (sizeof(T) != sizeof(double)) {
+            sin = take<T>((size_t)maxbatch * nsp);
+            sout = take<T>((size_t)maxbatch * nsp);
+        }
+        stage64 = take<double>((size_t)nsp);
+        partials = take<double>((size_t)(npartials_max > 0 ? npartials_max : 1));
+        norm_cur = take<double>(1);
+        for (int l = 0; l < L; ++l) {
+            if (is1d) lv[l].dir_w = take<T>((size_t)pb.nx);
+            setup_level_op(l);
+            if (!lv[l].row || (!is1d && !lv[l].col))
+                return fail(ATM_ERR_UNSUPPORTED, "no kernel instantiation for this grid size and precision");
+        }
+        build_phases();
+        d_jobs = take<Job<T>>(jobs.size() + 1);
+        d_ajobs = take<AxpyJob<T>>(ajobs.size() + 1);
+        d_dyn = take<Job<T>>((size_t)maxbatch);
+        off = (off + 255) & ~(size_t)255;
+        return ATM_OK;
+    }
+
+    size_t measure(atm_status *st_out)
+    {
+        // maxbatch and the partial count only grow while phases are built
+        int b = 16, np = 1;
+        for (int pass = 0; pass < 3; ++pass) {
+            atm_status s = layout(0, b, np);
+            if (s != ATM_OK) { *st_out = s; return 0; }
+            if (maxbatch == b && npartials_max == np) break;
+            b = maxbatch;
+            np = npartials_max;
+        }
+        *st_out = ATM_OK;
+        return off;
+    }
+
+    // ---------------- execution ----------------
+    long long kernels_in(const Phase &ph) const
+    {
+        long long n = 0;
+        for (const LaunchRec &r : ph) n += (r.type == L_SWEEP && !is1d) ? 2 : 1;
+        return n;
+    }
+
+    void launch_sweep(int l, const Job<T> *djobs, int njobs, int neg, double *part)
+    {
+        const Level<T> &Lv = lv[l];
+        SweepArgs<T> a = Lv.args;
+        a.jobs = djobs;
+        a.neg = neg;
+        a.partials = part;
+        a.mid = mid;
+        if (is1d) {
+            Lv.row<<<dim3(1, njobs), 32, 0, st>>>(a);
+        } else {
+            Lv.row<<<dim3(pb.ny / Lv.rows_per_cta, njobs), 32 * Lv.rows_per_cta, Lv.row_smem, st>>>(a);
+            Lv.col<<<dim3(pb.nx / 32, njobs), 32 * Lv.col_warps, 0, st>>>(a);
+        }
+    }
+
+    void launch_axpy(const AxpyJob<T> *dj, int njobs)
+    {
+        int blocks = (int)((nsp + 255) / 256);
+        if (blocks > 64) blocks = 64;
+        axpy_kernel<T><<<dim3(blocks, njobs), 256, 0, st>>>(dj, (size_t)nsp);
+    }
+
+    atm_status run(const Phase &ph)
+    {
+        for (const LaunchRec &r : ph) {
+            if (r.type == L_SWEEP)
+                launch_sweep(r.level, d_jobs + r.job_index, r.njobs, r.neg, r.partials);
+            else if (r.type == L_AXPY)
+                launch_axpy(d_ajobs + r.job_index, r.njobs);
+            else
+                norm_finalize_kernel<<<1, 1024, 0, st>>>(r.partials, r.npartials, r.norm_out, nullptr);
+        }
+        ATM_CK(cudaGetLastError());
+        launches += kernels_in(ph);
+        return ATM_OK;
+    }
+
+    atm_status capture(const std::vector<const Phase *> &phs, cudaGraphExec_t *out)
+    {
+        cudaGraph_t g = nullptr;
+        ATM_CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        for (const Phase *p : phs) {
+            for (const LaunchRec &r : *p) {
+                if (r.type == L_SWEEP)
+                    launch_sweep(r.level, d_jobs + r.job_index, r.njobs, r.neg, r.partials);
+                else if (r.type == L_AXPY)
+                    launch_axpy(d_ajobs + r.job_index, r.njobs);
+                else
+                    norm_finalize_kernel<<<1, 1024, 0, st>>>(r.partials, r.npartials, r.norm_out, nullptr);
+            }
+        }
+        cudaError_t e = cudaStreamEndCapture(st, &g);
+        if (e != cudaSuccess) return fail(ATM_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
+        e = cudaGraphInstantiate(out, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return fail(ATM_ERR_CUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
+        return ATM_OK;
+    }
+
+    atm_status finish_create() override
+    {
+        for (int l = 0; l < L; ++l) {
+            if (lv[l].row_smem > 48 * 1024)
+                ATM_CK(cudaFuncSetAttribute((const void *)lv[l].row, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)lv[l].row_smem));
+            if (is1d) {
+                std::vector<T> w(lv[l].dir_w_host.begin(), lv[l].dir_w_host.end());
+                ATM_CK(cudaMemcpyAsync(lv[l].dir_w, w.data(), w.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+                ATM_CK(cudaStreamSynchronize(st));
+            }
+        }
+        if (!jobs.empty())
+            ATM_CK(cudaMemcpyAsync(d_jobs, jobs.data(), jobs.size() * sizeof(Job<T>), cudaMemcpyHostToDevice, st));
+        if (!ajobs.empty())
+            ATM_CK(cudaMemcpyAsync(d_ajobs, ajobs.data(), ajobs.size() * sizeof(AxpyJob<T>), cudaMemcpyHostToDevice, st));
+        ATM_CK(cudaMemsetAsync(lv[0].u, 0, (size_t)lv[0].N * nsp * sizeof(T), st));
+        ATM_CK(cudaEventCreate(&ev0));
+        ATM_CK(cudaEventCreate(&ev1));
+        ATM_CK(cudaStreamSynchronize(st));
+        if (sv.use_graph && st != nullptr) {
+            if (sv.algorithm == ATM_SEQUENTIAL) {
+                ATM_TRY(capture({&seq}, &gSeq));
+            } else {
+                ATM_TRY(capture({&passA}, &gA));
+                ATM_TRY(capture({&rest, &passA}, &gIter));
+            }
+        }
+        return ATM_OK;
+    }
+
+    atm_status read_norm(double *v)
+    {
+        ATM_CK(cudaMemcpyAsync(v, norm_cur, sizeof(double), cudaMemcpyDeviceToHost, st));
+        ATM_CK(cudaStreamSynchronize(st));
+        return ATM_OK;
+    }
+
+    atm_status solve(atm_result *res) override
+    {
+        atm_result R;
+        std::memset(&R, 0, sizeof(R));
+        launches = 0;
+        hist.clear();
+        ATM_CK(cudaEventRecord(ev0, st));
+        atm_status status = ATM_OK;
+        if (sv.algorithm == ATM_SEQUENTIAL) {
+            if (gSeq) {
+                ATM_CK(cudaGraphLaunch(gSeq, st));
+                launches += kernels_in(seq);
+            } else {
+                ATM_TRY(run(seq));
+            }
+            R.converged = 1;
+        } else {
+            if (gA) { ATM_CK(cudaGraphLaunch(gA, st)); launches += kernels_in(passA); }
+            else ATM_TRY(run(passA));
+            double r0 = 0;
+            ATM_TRY(read_norm(&r0));
+            hist.push_back(r0);
+            double rmin = r0;
+            int growth = 0;
+            int it = 0;
+            while (std::isfinite(hist[it]) && hist[it] > sv.tol && it < sv.max_iter) {
+                if (gIter) {
+                    ATM_CK(cudaGraphLaunch(gIter, st));
+                    launches += kernels_in(rest) + kernels_in(passA);
+                } else {
+                    ATM_TRY(run(rest));
+                    ATM_TRY(run(passA));
+                }
+                double r = 0;
+                ATM_TRY(read_norm(&r));
+                hist.push_back(r);
+                ++it;
+                if (r < rmin) rmin = r;
+                growth = (r > 1e3 * rmin) ? growth + 1 : 0;
+                if (growth >= 3) break;
+            }
+            R.iterations = it;
+            R.initial_residual = hist.front();
+            R.final_residual = hist.back();
+            R.converged = hist.back() <= sv.tol;
+            if (!std::isfinite(hist.back()) || growth >= 3)
+                status = fail(ATM_ERR_DIVERGED, "residual diverged (%g after %d cycles)", hist.back(), it);
+            else if (!R.converged)
+                status = fail(ATM_ERR_NOT_CONVERGED, "residual %g > tol %g after %d cycles", hist.back(), sv.tol, it);
+        }
+        ATM_CK(cudaEventRecord(ev1, st));
+        ATM_CK(cudaEventSynchronize(ev1));
+        float ms = 0;
+        ATM_CK(cudaEventElapsedTime(&ms, ev0, ev1));
+        R.time_ms = ms;
+        if (res) *res = R;
+        return status;
+    }
+
+    static bool is_device_ptr(const void *p)
+    {
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    }
+
+    void convert_to_T(const double *src, T *dst, size_t n)
+    {
+        int blocks = (int)((n + 255) / 256);
+        if (blocks > 1024) blocks = 1024;
+        convert_kernel<double, T><<<blocks, 256, 0, st>>>(src, dst, n);
+    }
+
+    void convert_from_T(const T *src, double *dst, size_t n)
+    {
+        int blocks = (int)((n + 255) / 256);
+        if (blocks > 1024) blocks = 1024;
+        convert_kernel<T, double><<<blocks, 256, 0, st>>>(src, dst, n);
+    }
+
+    // Copy FP64 states (host or device) into an array of T.
+    atm_status write_states(T *dst, const double *src, int count)
+    {
+        const size_t n = (size_t)count * nsp;
+        if (is_device_ptr(src)) {
+            if (sizeof(T) == sizeof(double))
+                ATM_CK(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+            else
+                convert_to_T(src, dst, n);
+        } else if (sizeof(T) == sizeof(double)) {
+            ATM_CK(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyHostToDevice, st));
+            ATM_CK(cudaStreamSynchronize(st));
+        } else {
+            for (int s = 0; s < count; ++s) {
+                ATM_CK(cudaMemcpyAsync(stage64, src + (size_t)s * nsp, nsp * sizeof(double), cudaMemcpyHostToDevice, st));
+                convert_to_T(stage64, dst + (size_t)s * nsp, nsp);
+            }
+            ATM_CK(cudaStreamSynchronize(st));
+        }
+        ATM_CK(cudaGetLastError());
+        return ATM_OK;
+    }
+
+    atm_status read_states(const T *src, double *dst, int count)
+    {
+        const size_t n = (size_t)count * nsp;
+        if (is_device_ptr(dst)) {
+            if (sizeof(T) == sizeof(double))
+                ATM_CK(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+            else
+                convert_from_T(src, dst, n);
+        } else if (sizeof(T) == sizeof(double)) {
+            ATM_CK(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+            ATM_CK(cudaStreamSynchronize(st));
+        } else {
+            for (int s = 0; s < count; ++s) {
+                convert_from_T(src + (size_t)s * nsp, stage64, nsp);
+                ATM_CK(cudaMemcpyAsync(dst + (size_t)s * nsp, stage64, nsp * sizeof(double), cudaMemcpyDeviceToHost, st));
+            }
+            ATM_CK(cudaStreamSynchronize(st));
+        }
+        ATM_CK(cudaGetLastError());
+        return ATM_OK;
+    }
+
+    atm_status set_state(int t0, int count, const double *src) override
+    {
+        if (!src || t0 < 0 || count < 0 || t0 + count > lv[0].N) return fail(ATM_ERR_INVALID_ARG, "state range out of bounds");
+        if (count == 0) return ATM_OK;
+        return write_states(st_ptr(lv[0].u, t0), src, count);
+    }
+
+    atm_status get_state(int t0, int count, double *dst) override
+    {
+        if (!dst || t0 < 0 || count < 0 || t0 + count > lv[0].N) return fail(ATM_ERR_INVALID_ARG, "state range out of bounds");
+        if (count == 0) return ATM_OK;
+        return read_states(st_ptr(lv[0].u, t0), dst, count);
+    }
+
+    atm_status apply_prop(int level, const double *in, double *out, int n) override
+    {
+        if (level < 0 || level >= L) return fail(ATM_ERR_INVALID_ARG, "level %d out of range", level);
+        if (n < 0 || n > maxbatch) return fail(ATM_ERR_INVALID_ARG, "nstates %d exceeds the batch limit %d", n, maxbatch);
+        if (n == 0) return ATM_OK;
+        if (!in || !out || !is_device_ptr(in) || !is_device_ptr(out))
+            return fail(ATM_ERR_INVALID_ARG, "in/out must be device pointers");
+        std::vector<Job<T>> js;
+        const bool f64 = sizeof(T) == sizeof(double);
+        if (!f64) convert_to_T(in, sin, (size_t)n * nsp);
+        for (int s = 0; s < n; ++s) {
+            const T *pi = f64 ? reinterpret_cast<const T *>(in) + (size_t)s * nsp : sin + (size_t)s * nsp;
+            T *po = f64 ? reinterpret_cast<T *>(out) + (size_t)s * nsp : sout + (size_t)s * nsp;
+            js.push_back(job(pi, po));
+        }
+        ATM_CK(cudaMemcpyAsync(d_dyn, js.data(), js.size() * sizeof(Job<T>), cudaMemcpyHostToDevice, st));
+        launch_sweep(level, d_dyn, n, 0, nullptr);
+        if (!f64) convert_from_T(sout, out, (size_t)n * nsp);
+        ATM_CK(cudaGetLastError());
+        ATM_CK(cudaStreamSynchronize(st));
+        return ATM_OK;
+    }
+
+    atm_status run_stage(int stage, int level) override
+    {
+        if (sv.algorithm == ATM_SEQUENTIAL) return fail(ATM_ERR_INVALID_ARG, "no cycle stages for sequential stepping");
+        if (stage == ATM_STAGE_COARSEST) return run(st_coarse);
+        if (level < 0 || level + 1 >= L) return fail(ATM_ERR_INVALID_ARG, "stage level %d out of range", level);
+        switch (stage) {
+        case ATM_STAGE_F_RELAX: return run(st_f[level]);
+        case ATM_STAGE_C_RELAX: return run(st_c[level]);
+        case ATM_STAGE_RESTRICT: return run(st_r[level]);
+        case ATM_STAGE_CORRECT: return run(st_corr[level]);
+        default: return fail(ATM_ERR_INVALID_ARG, "unknown stage %d", stage);
+        }
+    }
+
+    atm_status level_io(int level, int array, int t0, int count, double *buf, bool write) override
+    {
+        if (level < 0 || level >= L) return fail(ATM_ERR_INVALID_ARG, "level %d out of range", level);
+        T *arr = nullptr;
+        switch (array) {
+        case ATM_ARRAY_U: arr = lv[level].u; break;
+        case ATM_ARRAY_V: arr = lv[level].v; break;
+        case ATM_ARRAY_R: arr = lv[level].r; break;
+        case ATM_ARRAY_G: arr = lv[level].g; break;
+        default: return fail(ATM_ERR_INVALID_ARG, "unknown array %d", array);
+        }
+        if (!arr) return fail(ATM_ERR_INVALID_ARG, "array %d does not exist on level %d", array, level);
+        if (!buf || t0 < 0 || count < 0 || t0 + count > lv[level].N) return fail(ATM_ERR_INVALID_ARG, "state range out of bounds");
+        if (count == 0) return ATM_OK;
+        ATM_TRY(write ? write_states(st_ptr(arr, t0), buf, count) : read_states(st_ptr(arr, t0), buf, count));
+        ATM_CK(cudaStreamSynchronize(st));
+        return ATM_OK;
+    }
+
+    int level_points(int level) const override { return (level >= 0 && level < L) ? lv[level].N : -1; }
+};
+
+}  // namespace atm

@@ -1,0 +1,255 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+FP64 bar: relative L2 <= 1e-12 (the target for the FP64 sweep); the
+propagators themselves agree to ~1e-15 (different rounding order of the same
+exact solve).  FP32 bar: relative L2 <= 3e-6 for one propagator application
+(FP32 rounding of ~20 operations per value), looser where errors accumulate
+over many steps, as stated per test."""
+import numpy as np
+import pytest
+
+import atm_inputs as I
+import oracle
+import paper_2107_09596_gb300 as atm
+from helpers import pair, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch
+    assert torch.cuda.is_available()
+    atm._build.build()
+    atm.load()
+    return torch
+
+
+def dev(torch, x):
+    return torch.as_tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda:0")
+
+
+PROP_CASES = {
+    # name: pair() keyword arguments
+    "heat1d_127": dict(kind="heat1d", nx=127, dt=1 / 1024, nt=1025, m=(8,)),
+    "heat1d_1024": dict(kind="heat1d", nx=1024, dt=1e-4, nt=65, m=(4,)),
+    "heat1d_2": dict(kind="heat1d", nx=2, dt=1e-2, nt=65, m=(4,)),
+    "heat2d_pr_64x128": dict(kind="heat2d", nx=128, ny=64, lx=1.0, ly=0.7, dt=2e-4, nt=65, m=(4,)),
+    "heat2d_split_32": dict(kind="heat2d", nx=32, ny=32, dt=1e-3, nt=65, m=(4,),
+                            fine_prop=atm.PROP_SPLIT_BE),
+    "ac_pr_256": dict(kind="ac", nx=256, ny=256, dt=1e-4, nt=4097, m=(16, 16), k=8),
+    "ac_pr_512x32": dict(kind="ac", nx=512, ny=32, dt=1e-4, nt=65, m=(4, 4), k=3),
+    "ac_pr_32x512": dict(kind="ac", nx=32, ny=512, dt=1e-4, nt=65, m=(4, 4), k=3),
+}
+
+
+@pytest.mark.parametrize("prec", [atm.FP64, atm.FP32])
+@pytest.mark.parametrize("case", sorted(PROP_CASES))
+def test_propagator_matches_oracle(torch, case, prec):
+    kw = dict(PROP_CASES[case])
+    oc, gp, gs = pair(precision=prec, **kw)
+    s = atm.Solver(gp, gs)
+    shape = s.state_shape
+    nstates = 5
+    x = I.uniform_field((nstates,) + shape, 3, -1.0, 1.0)
+    for level in range(len(kw["m"]) + 1):
+        want = oracle.apply_prop(oc, level, x)
+        got = s.apply_propagator(level, dev(torch, x)).cpu().numpy()
+        tol = 1e-13 if prec == atm.FP64 else 3e-6
+        for j in range(nstates):
+            assert rel_l2(got[j], want[j]) <= tol, (level, j, rel_l2(got[j], want[j]))
+
+
+def test_stages_match_oracle_three_level(torch):
+    """Each building block of Algorithm 2 on its own: F- and C-relaxation,
+    residual + injection + FAS right-hand side, coarsest local chains,
+    correction; three levels, Allen-Cahn, ragged last intervals."""
+    oc, gp, gs = pair(kind="ac", nx=64, ny=64, dt=1e-4, nt=137, m=(4, 3), k=3, nu=1)
+    s = atm.Solver(gp, gs)
+    u = I.random_guess(137, (64, 64), 5, -0.5, 0.5)
+    u[0] = I.uniform_field((64, 64), 6)
+    s.level_write(0, atm.ARRAY_U, dev(torch, u))
+    tol = 1e-12
+
+    def chk(level, array, want):
+        got = s.level_read(level, array).cpu().numpy()
+        assert got.shape == want.shape
+        assert rel_l2(got, want) <= tol, (level, array, rel_l2(got, want))
+
+    uo = u.copy()
+    s.run_stage(atm.STAGE_F_RELAX, 0)
+    oracle.frelax_level(oc, 0, uo)
+    chk(0, atm.ARRAY_U, uo)
+    s.run_stage(atm.STAGE_C_RELAX, 0)
+    oracle.crelax_level(oc, 0, uo)
+    chk(0, atm.ARRAY_U, uo)
+    s.run_stage(atm.STAGE_F_RELAX, 0)
+    oracle.frelax_level(oc, 0, uo)
+    s.run_stage(atm.STAGE_RESTRICT, 0)
+    v1, r1, g1 = oracle.restrict_level(oc, 0, uo)
+    chk(1, atm.ARRAY_V, v1)
+    chk(1, atm.ARRAY_R, r1)
+    chk(1, atm.ARRAY_G, g1)
+    chk(1, atm.ARRAY_U, v1)
+    u1 = v1.copy()
+    s.run_stage(atm.STAGE_F_RELAX, 1)
+    oracle.frelax_level(oc, 1, u1, g1)
+    chk(1, atm.ARRAY_U, u1)
+    s.run_stage(atm.STAGE_C_RELAX, 1)
+    oracle.crelax_level(oc, 1, u1, g1)
+    chk(1, atm.ARRAY_U, u1)
+    s.run_stage(atm.STAGE_F_RELAX, 1)
+    oracle.frelax_level(oc, 1, u1, g1)
+    s.run_stage(atm.STAGE_RESTRICT, 1)
+    v2, r2, g2 = oracle.restrict_level(oc, 1, u1, g1)
+    chk(2, atm.ARRAY_V, v2)
+    chk(2, atm.ARRAY_R, r2)
+    chk(2, atm.ARRAY_G, g2)
+    s.run_stage(atm.STAGE_COARSEST)
+    u2 = oracle.coarsest_level(oc, 2, v2, r2, g2)
+    chk(2, atm.ARRAY_U, u2)
+    s.run_stage(atm.STAGE_CORRECT, 1)
+    u1[::3] = u1[::3] + (u2 - v2)
+    chk(1, atm.ARRAY_U, u1)
+
+
+SOLVE_CASES = {
+    "cfg1_at_fcf": dict(kind="heat1d", nx=127, dt=1 / 1024, nt=1025, m=(8,), k=4, nu=1),
+    "cfg1_at_k5": dict(kind="heat1d", nx=127, dt=1 / 1024, nt=1025, m=(8,), k=5, nu=1),
+    "cfg1_mgrit": dict(kind="heat1d", nx=127, dt=1 / 1024, nt=1025, m=(8,), k=4, nu=1, algorithm="mgrit"),
+    "heat1d_f_ragged": dict(kind="heat1d", nx=63, dt=1 / 512, nt=1000, m=(8,), k=3, nu=0),
+    "heat1d_k1": dict(kind="heat1d", nx=31, dt=1 / 256, nt=257, m=(4,), k=1, nu=1),
+    "heat1d_3lvl_m2": dict(kind="heat1d", nx=31, dt=1 / 256, nt=257, m=(2, 4), k=4, nu=1),
+    "ac_3lvl_ragged": dict(kind="ac", nx=64, ny=64, dt=1e-4, nt=300, m=(4, 4), k=3, nu=1),
+    "ac_4lvl_f": dict(kind="ac", nx=32, ny=32, dt=1e-4, nt=257, m=(4, 2, 2), k=4, nu=0),
+    "heat2d_2lvl_pr": dict(kind="heat2d", nx=64, ny=32, dt=1e-3, nt=129, m=(8,), k=3, nu=1),
+}
+
+
+@pytest.mark.parametrize("case", sorted(SOLVE_CASES))
+def test_solve_iterates_match_oracle(torch, case):
+    """Residual history and the iterate after j cycles (j = 1, 2, 5) match the
+    oracle's literal Algorithm 2 from the same initial guess."""
+    kw = dict(SOLVE_CASES[case])
+    nt = kw["nt"]
+    for j in (1, 2, 5):
+        oc, gp, gs = pair(max_iter=j, tol=0.0, **kw)
+        s = atm.Solver(gp, gs)
+        shape = s.state_shape
+        if kw["kind"] == "heat1d":
+            u0 = I.heat1d_initial_condition(kw["nx"], 0)
+        else:
+            u0 = I.uniform_field(shape, 1)
+        guess = I.random_guess(nt, shape, 2, -0.3, 0.3)
+        guess[0] = u0
+        s.set_initial_condition(dev(torch, u0))
+        s.set_initial_guess(dev(torch, guess))
+        res = s.solve()
+        assert res["iterations"] == j
+        got = s.solution().cpu().numpy()
+        uo = guess.copy()
+        it, hist = oracle.solve(oc, uo, j, 0.0)
+        assert it == j
+        assert rel_l2(got, uo) <= 1e-12, (j, rel_l2(got, uo))
+        gh = s.residual_history()
+        assert len(gh) == j + 1
+        np.testing.assert_allclose(gh, hist, rtol=1e-9, atol=1e-13 * hist[0])
+
+
+def test_converged_solution_is_sequential_and_graph_is_bitwise(torch):
+    oc, gp, gs = pair(kind="ac", nx=64, ny=64, dt=1e-4, nt=257, m=(4, 4), k=4, nu=1, tol=1e-10,
+                      max_iter=60, use_graph=True)
+    u0 = I.uniform_field((64, 64), 7)
+    a = atm.Solver(gp, gs)
+    a.set_initial_condition(dev(torch, u0))
+    ra = a.solve(allow_not_converged=False)
+    sol_a = a.solution().cpu().numpy()
+    _, gp2, gs2 = pair(kind="ac", nx=64, ny=64, dt=1e-4, nt=257, m=(4, 4), k=4, nu=1, tol=1e-10,
+                       max_iter=60, use_graph=False)
+    b = atm.Solver(gp2, gs2)
+    b.set_initial_condition(dev(torch, u0))
+    rb = b.solve(allow_not_converged=False)
+    np.testing.assert_array_equal(sol_a, b.solution().cpu().numpy())
+    np.testing.assert_array_equal(a.residual_history(), b.residual_history())
+    assert ra["iterations"] == rb["iterations"]
+    seq = oracle.sequential(oc, u0)
+    assert rel_l2(sol_a, seq) <= 1e-9
+
+
+def test_at_with_k_covering_all_points_equals_mgrit(torch):
+    kw = dict(kind="ac", nx=32, ny=32, dt=1e-4, nt=129, m=(4, 4), nu=1, tol=0.0, max_iter=4)
+    sols = []
+    for alg, k in (("mgrit", 1), ("at", 9)):
+        _, gp, gs = pair(algorithm=alg, k=k, **kw)
+        s = atm.Solver(gp, gs)
+        s.set_initial_condition(dev(torch, I.uniform_field((32, 32), 3)))
+        s.solve()
+        sols.append((s.solution().cpu().numpy(), s.residual_history()))
+    np.testing.assert_array_equal(sols[0][0], sols[1][0])
+    np.testing.assert_array_equal(sols[0][1], sols[1][1])
+
+
+def test_sequential_stepping_matches_oracle(torch):
+    for prec, tol in ((atm.FP64, 1e-12), (atm.FP32, 2e-4)):
+        oc, gp, gs = pair(kind="ac", nx=128, ny=128, dt=1e-4, nt=257, m=(4,), algorithm="seq",
+                          precision=prec)
+        s = atm.Solver(gp, gs)
+        u0 = I.uniform_field((128, 128), 9)
+        s.set_initial_condition(u0)          # host pointer path
+        s.solve()
+        got = s.solution(0, 257, out=np.zeros((257, 128, 128)))   # host destination
+        want = oracle.sequential(oc, u0)
+        assert rel_l2(got, want) <= tol, (prec, rel_l2(got, want))
+
+
+def test_fp32_solve_reaches_fp32_accuracy(torch):
+    oc, gp, gs = pair(kind="ac", nx=64, ny=64, dt=1e-4, nt=257, m=(4, 4), k=4, nu=1, tol=1e-4,
+                      max_iter=60, precision=atm.FP32)
+    s = atm.Solver(gp, gs)
+    u0 = I.uniform_field((64, 64), 7)
+    s.set_initial_condition(dev(torch, u0))
+    r = s.solve()
+    assert r["converged"], r
+    seq = oracle.sequential(oc, u0)
+    assert rel_l2(s.solution().cpu().numpy(), seq) <= 1e-4
+
+
+def test_invalid_calls_report_status(torch):
+    oc, gp, gs = pair(kind="heat1d", nx=31, dt=1 / 256, nt=65, m=(4,), k=2)
+    s = atm.Solver(gp, gs)
+    x = torch.zeros((1000, 31), dtype=torch.float64, device="cuda:0")
+    with pytest.raises(atm.AtmError, match="INVALID_ARG"):
+        s.apply_propagator(0, x)        # beyond the batch limit
+    with pytest.raises(atm.AtmError, match="INVALID_ARG"):
+        s.apply_propagator(7, x[:2])    # no such level
+    with pytest.raises(atm.AtmError, match="INVALID_ARG"):
+        s.run_stage(atm.STAGE_F_RELAX, 1)   # coarsest level has no C-points
+    ws = torch.empty(1024, dtype=torch.uint8, device="cuda:0")
+    h = atm.ctypes.c_void_p()
+    st = atm.load().atm_create(atm.ctypes.byref(gp), atm.ctypes.byref(gs),
+                               atm.ctypes.c_void_p(ws.data_ptr()), 1024, None, atm.ctypes.byref(h))
+    assert atm.STATUS[st] == "ATM_ERR_OOM"
+
+
+def test_full_size_cfg2_one_cycle_sampled(torch):
+    """Allen-Cahn 256^2, 4097 points, m = (16, 16), k = 8, FCF, FP64, in the
+    configuration the benchmark times: after one cycle every sampled fine step
+    is Phi of its predecessor (oracle applied to the GPU's own states), and the
+    initial residual equals ||Phi^16 u0|| (zero guess)."""
+    oc, gp, gs = pair(kind="ac", nx=256, ny=256, dt=1e-4, nt=4097, m=(16, 16), k=8, nu=1,
+                      tol=0.0, max_iter=1)
+    s = atm.Solver(gp, gs)
+    u0 = I.uniform_field((256, 256), 0)
+    s.set_initial_condition(dev(torch, u0))
+    r = s.solve()
+    x = u0[None].copy()
+    for _ in range(16):
+        x = oracle.apply_prop(oc, 0, x)
+    assert abs(r["initial_residual"] - np.linalg.norm(x)) <= 1e-12 * np.linalg.norm(x)
+    rng = np.random.default_rng(0)
+    for t in sorted(rng.choice(np.arange(1, 4097), 12, replace=False)):
+        if t % 16 == 0:
+            continue    # C-points carry the coarse correction
+        prev = s.solution(t - 1, 1).cpu().numpy()
+        cur = s.solution(t, 1).cpu().numpy()
+        assert rel_l2(cur, oracle.apply_prop(oc, 0, prev)) <= 1e-13, t
