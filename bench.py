@@ -1,0 +1,384 @@
+"""Benchmark: AT-MGRIT time-to-solution on one GB300 (or N, one independent
+problem per rank), printed as one JSON line.
+
+Workload (default): 2D Allen-Cahn, 256^2 periodic grid, eps = 0.02, PR-ADI
+fine step with explicit reaction, 4097 time points, dt = 1e-4, three-level
+AT-MGRIT, m = (16, 16), local grids of k = 8 points, FCF relaxation, residual
+tolerance 1e-8, u0 ~ U(-0.05, 0.05) (seed = rank), zero initial guess.
+A step is one full solve to ||r||_2 <= 1e-8 from the zero guess: every row of
+the sweep (relaxation, residual, restriction, local chains, correction, norm,
+cycle control).  value = fine time steps resolved per second
+= ranks * (nt - 1) / time-to-solution.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl atm|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import atm_inputs as I  # noqa: E402
+
+METRIC = "time-to-solution at residual 1e-8 and fine steps/s; HBM GB/s vs peak; AT-MGRIT vs plain"
+UNIT = "fine steps/s"
+
+WORKLOADS = {
+    "allen_cahn_256": dict(kind="ac", n=256, nt=4097, dt=1e-4, eps=0.02, m=(16, 16), k=8, nu=1,
+                           tol=1e-8, max_iter=60),
+    "heat1d_127": dict(kind="heat1d", n=127, nt=1025, dt=1 / 1024, eps=0.0, m=(8,), k=4, nu=1,
+                       tol=1e-10, max_iter=60),
+}
+
+# Textbook flops per grid value of one sweep kernel:
+# PR explicit term 5, periodic tridiagonal solve 7 (Thomas 5 + rank-one
+# periodic correction 2), split-BE right-hand side 0, reaction substep 5,
+# Dirichlet tridiagonal solve 5 (+2 for the first-row correction).
+FLOPS_PER_VALUE = {("row", "pr_react"): 17, ("row", "pr"): 12, ("col", "pr"): 12,
+                   ("row", "split"): 7, ("col", "split"): 7, ("row", "heat1d"): 7}
+
+
+def load_json(path, default=None):
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return default
+
+
+def peaks():
+    mp = load_json(os.path.join(ROOT, "MEASURED_PEAKS.json"), {}) or {}
+    return {
+        "hbm_gbs": mp.get("hbm_gbs", 6800.0),
+        "hbm_src": "measured" if "hbm_gbs" in mp else "fallback",
+        # FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (derivation in the design doc)
+        "fp64_tflops": 152 * 2 * 2 * 2.07e9 / 1e12,
+    }
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.idx)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=5)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def kernel_source_hash():
+    h = hashlib.md5()
+    for f in ("atm_kernels.cuh", "atm_host.cuh"):
+        with open(os.path.join(ROOT, "paper_2107_09596_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "atm" else "gloo"
+        dist.init_process_group(backend=backend)
+    return world, rank, local, dist
+
+
+def barrier(dist, device=None):
+    if dist is not None:
+        if device is not None:
+            dist.barrier(device_ids=[device.index])
+        else:
+            dist.barrier()
+
+
+def max_over_ranks(dist, value, device=None):
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def make_desc(atm, w, algorithm, precision, profile):
+    kind = {"ac": atm.ALLEN_CAHN, "heat1d": atm.HEAT1D}[w["kind"]]
+    ny = w["n"] if w["kind"] != "heat1d" else 1
+    prob = atm.make_problem(kind, w["n"], ny, dt=w["dt"], nt_points=w["nt"], eps=w["eps"])
+    alg = {"at": atm.AT_MGRIT, "mgrit": atm.MGRIT, "seq": atm.SEQUENTIAL}[algorithm]
+    desc = atm.make_solver(alg, m=w["m"], k=w["k"], nu=w["nu"], tol=w["tol"],
+                           max_iter=w["max_iter"], precision=precision, use_graph=True,
+                           profile=profile)
+    return prob, desc
+
+
+def initial_condition(w, seed):
+    if w["kind"] == "heat1d":
+        return I.heat1d_initial_condition(w["n"], seed)
+    return I.uniform_field((w["n"], w["n"]), seed)
+
+
+def oracle_cycle_sample(w, iterations):
+    """CPU baseline: the oracle (as it stands) runs the initial F-relaxation and
+    one V-cycle of the same workload; time-to-solution is scaled to the cycles
+    the solve needs (equal to the GPU's by parity)."""
+    import oracle
+    kind = {"ac": oracle.ALLEN_CAHN, "heat1d": oracle.HEAT1D}[w["kind"]]
+    ny = w["n"] if w["kind"] != "heat1d" else 1
+    c = oracle.make_cfg(kind, w["n"], ny, dt=w["dt"], nt=w["nt"], eps=w["eps"], m=w["m"],
+                        k=w["k"], nu=w["nu"])
+    u = np.zeros((w["nt"],) + oracle.state_shape(c))
+    u[0] = initial_condition(w, 0)
+    t = time.perf_counter()
+    oracle.solve(c, u, 1, 0.0)
+    sec = time.perf_counter() - t
+    est = sec * max(iterations, 1)
+    return {"value": (w["nt"] - 1) / est, "unit": UNIT, "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": f"initial F-relaxation + 1 V-cycle of the oracle on this workload "
+                      f"({sec:.1f} s), scaled to {iterations} cycles"}
+
+
+def run_reference(args, w, world, rank, dist):
+    """--impl reference: the oracle on the host cores, rank 0 only."""
+    if rank != 0:
+        return
+    import oracle
+    gold = load_json(os.path.join(ROOT, "tests", "golden", "oracle_histories.json"), {}) or {}
+    key = {"allen_cahn_256": "cfg2_at_k8", "heat1d_127": "cfg1_at_k4"}[args.workload]
+    iters = gold.get(key, {}).get("iterations", 13)
+    kind = {"ac": oracle.ALLEN_CAHN, "heat1d": oracle.HEAT1D}[w["kind"]]
+    ny = w["n"] if w["kind"] != "heat1d" else 1
+    c = oracle.make_cfg(kind, w["n"], ny, dt=w["dt"], nt=w["nt"], eps=w["eps"], m=w["m"],
+                        k=w["k"], nu=w["nu"])
+    u0 = initial_condition(w, 0)
+    times = []
+    for s in range(args.warmup + args.steps):
+        u = np.zeros((w["nt"],) + oracle.state_shape(c))
+        u[0] = u0
+        t = time.perf_counter()
+        oracle.solve(c, u, 1, 0.0)
+        if s >= args.warmup:
+            times.append(time.perf_counter() - t)
+    sec = float(np.mean(times))
+    ms_solve = sec * iters * 1e3
+    value = (w["nt"] - 1) / (ms_solve / 1e3)
+    sample = (f"each step: initial F-relaxation + 1 V-cycle of the oracle ({sec:.2f} s); "
+              f"time-to-solution = step time x {iters} cycles (the oracle's own count, "
+              f"tests/golden/oracle_histories.json)")
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_solve,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": args.workload, **{k: (list(v) if isinstance(v, tuple) else v)
+                                                     for k, v in w.items()},
+                       "algorithm": "at-mgrit", "l2": "inputs larger than L2 (host run)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["atm", "reference"], default="atm")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="allen_cahn_256")
+    ap.add_argument("--algorithm", choices=["at", "mgrit", "seq"], default="at")
+    ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    w = WORKLOADS[args.workload]
+    world, rank, local, dist = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, w, world, rank, dist)
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    import torch
+    import paper_2107_09596_gb300 as atm
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    atm._build.build()
+    prec = {"fp64": atm.FP64, "fp32": atm.FP32}[args.precision]
+    prob, desc = make_desc(atm, w, args.algorithm, prec, profile=True)
+    solver = atm.Solver(prob, desc, device=device)
+    shape = solver.state_shape
+    u0 = torch.as_tensor(initial_condition(w, rank), dtype=torch.float64, device=device)
+    zeros = torch.zeros((w["nt"],) + shape, dtype=torch.float64, device=device)
+
+    def step():
+        solver.set_initial_guess(zeros)
+        solver.set_initial_condition(u0)
+        return solver.solve()
+
+    for _ in range(args.warmup):
+        res = step()
+    torch.cuda.synchronize(device)
+    prof0 = [solver.kernel_profile(0), solver.kernel_profile(1)]
+    clocks = ClockSampler(device.index if device.index is not None else 0)
+    barrier(dist, device)
+    torch.cuda.synchronize(device)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    launches = 0
+    iters = []
+    e0.record(solver.stream)
+    for _ in range(args.steps):
+        res = step()
+        launches += res["launches"]
+        iters.append(res["iterations"])
+    e1.record(solver.stream)
+    torch.cuda.synchronize(device)
+    clk = clocks.stop()
+    barrier(dist, device)
+    ms = e0.elapsed_time(e1) / args.steps
+    ms = max_over_ranks(dist, ms, device)
+    value = world * (w["nt"] - 1) / (ms / 1e3)
+    prof1 = [solver.kernel_profile(0), solver.kernel_profile(1)]
+
+    # end to end through host buffers: u0 from pinned host memory in, the final
+    # state and the residual history out, copies inside the timed region
+    h_u0 = torch.as_tensor(initial_condition(w, rank), dtype=torch.float64).pin_memory()
+    h_out = torch.empty(shape, dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize(device)
+    barrier(dist, device)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        solver.set_initial_guess(zeros)
+        solver.set_initial_condition(h_u0)
+        solver.solve()
+        solver.solution(w["nt"] - 1, 1, out=h_out)
+        hist = solver.residual_history()
+    torch.cuda.synchronize(device)
+    e2e_ms = (time.perf_counter() - t) * 1e3 / args.steps
+    e2e_ms = max_over_ranks(dist, e2e_ms, device)
+    state_bytes = int(np.prod(shape)) * 8
+
+    # roofline of the dominant level-0 sweep kernel (event-timed during the timed steps)
+    pk = peaks()
+    n_val = int(np.prod(shape))
+    jobs = {"allen_cahn_256": 256, "heat1d_127": 128}[args.workload]
+    tot = [prof1[i][0] - prof0[i][0] for i in range(2)]
+    cnt = [prof1[i][1] - prof0[i][1] for i in range(2)]
+    which = 0 if tot[0] >= tot[1] else 1
+    avg_ms = tot[which] / max(cnt[which], 1)
+    if not avg_ms > 0:
+        raise RuntimeError("kernel profile recorded no launches")
+    name = ["row_sweep", "col_sweep"][which]
+    if w["kind"] == "heat1d":
+        fkey = ("row", "heat1d")
+    else:
+        fkey = ("row", "pr_react") if which == 0 else ("col", "pr")
+    traffic_db = load_json(os.path.join(ROOT, "profiles", "traffic.json"), {}) or {}
+    tkey = f"{args.workload}:{args.precision}:{name}"
+    tr = traffic_db.get(tkey)
+    traffic = tr["bytes_per_launch"] if tr and tr.get("source_hash") == kernel_source_hash() else None
+    if args.precision == "fp64":
+        flops = FLOPS_PER_VALUE[fkey] * n_val * jobs
+        achieved = flops / (avg_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": pk["fp64_tflops"], "unit": "TFLOP/s",
+                "frac": achieved / pk["fp64_tflops"], "traffic": traffic, "kernel": name,
+                "avg_launch_ms": avg_ms, "launches_timed": cnt[which],
+                "peak_source": "derived FP64 FMA rate (152 SMs x 2 DFMA/clk x 2.07 GHz)",
+                "algorithmic": f"{FLOPS_PER_VALUE[fkey]} flop/value x {n_val} values x {jobs} states"}
+    else:
+        nbytes = 2 * n_val * 4 * jobs
+        achieved = nbytes / (avg_ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / pk["hbm_gbs"], "traffic": traffic, "kernel": name,
+                "avg_launch_ms": avg_ms, "launches_timed": cnt[which],
+                "peak_source": f"{pk['hbm_src']} STREAM copy (MEASURED_PEAKS.json)",
+                "algorithmic": f"read + write of {jobs} states of {n_val} fp32 values"}
+
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            cpu = oracle_cycle_sample(w, int(np.median(iters)))
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": {"fp64": "f64", "fp32": "f32"}[args.precision], "data": "synthetic",
+                "config": {"workload": args.workload,
+                           **{k: (list(v) if isinstance(v, tuple) else v) for k, v in w.items()},
+                           "algorithm": args.algorithm, "parallelism": f"{world} independent problems",
+                           "l2": "inputs larger than L2 (space-time array %.2f GB)" % (
+                               w["nt"] * n_val * (8 if args.precision == "fp64" else 4) / 1e9)},
+                "iterations": int(np.median(iters)), "time_to_solution_ms": ms,
+                "final_residual": float(res["final_residual"]),
+                "e2e": {"value": world * (w["nt"] - 1) / (e2e_ms / 1e3), "unit": UNIT,
+                        "h2d_bytes_per_step": state_bytes,
+                        "d2h_bytes_per_step": state_bytes + 8 * len(hist)},
+                "gpu_launches": int(launches),
+                "roofline": roof, "cpu_baseline": cpu, "clocks": clk}
+        print(json.dumps(line), flush=True)
+    solver.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -97,6 +97,7 @@ typedef struct {
     int max_iter;                     /* maximum V-cycles */
     int precision;                    /* ATM_FP64 | ATM_FP32 | ATM_FP32_REFINED */
     int use_graph;                    /* 1: replay the cycle as a captured CUDA graph */
+    int profile;                      /* 1: time the level-0 relaxation sweeps with CUDA events */
 } atm_solver;
 
 typedef struct {
@@ -182,6 +183,12 @@ int atm_level_points(const atm_handle *h, int level);
 /* Kernel launches issued by the last atm_solve (graph replays count the
  * kernels inside the graph). */
 long long atm_last_launch_count(const atm_handle *h);
+
+/* Kernel time of the level-0 relaxation sweeps of all solves since
+ * atm_create (needs solver.profile = 1): `which` = 0 row sweeps (implicit in
+ * x; the whole propagator for heat1d), 1 column sweeps (implicit in y).
+ * *total_ms = summed CUDA-event durations, *launches = launches timed. */
+atm_status atm_get_kernel_profile(const atm_handle *h, int which, double *total_ms, long long *launches);
 
 /* Message of the calling thread's last error ("" if none). */
 const char *atm_last_error(void);

@@ -46,7 +46,8 @@ class SolverDesc(ctypes.Structure):
                 ("fine_prop", ctypes.c_int), ("coarse_prop", ctypes.c_int),
                 ("reaction_substeps", ctypes.c_int * MAX_LEVELS),
                 ("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
-                ("precision", ctypes.c_int), ("use_graph", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("use_graph", ctypes.c_int),
+                ("profile", ctypes.c_int)]
 
 
 class Result(ctypes.Structure):
@@ -59,7 +60,7 @@ EXPORTS = ["atm_workspace_size", "atm_create", "atm_set_initial_condition",
            "atm_set_initial_guess", "atm_solve", "atm_get_solution",
            "atm_get_residual_history", "atm_apply_propagator", "atm_run_stage",
            "atm_level_read", "atm_level_write", "atm_level_points",
-           "atm_last_launch_count", "atm_last_error", "atm_destroy"]
+           "atm_last_launch_count", "atm_get_kernel_profile", "atm_last_error", "atm_destroy"]
 
 _lib = None
 
@@ -95,6 +96,7 @@ def load(build_if_missing: bool = True):
     L.atm_level_points.restype = i
     L.atm_last_launch_count.argtypes = [vp]
     L.atm_last_launch_count.restype = ctypes.c_longlong
+    L.atm_get_kernel_profile.argtypes = [vp, i, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_longlong)]
     L.atm_last_error.restype = ctypes.c_char_p
     L.atm_destroy.argtypes = [vp]
     for name in EXPORTS:
@@ -119,7 +121,7 @@ def make_problem(kind, nx, ny=1, lx=1.0, ly=1.0, dt=1e-3, nt_points=65, eps=0.02
 
 def make_solver(algorithm=AT_MGRIT, m=(8,), k=4, nu=1, fine_prop=PROP_PR_ADI,
                 coarse_prop=PROP_SPLIT_BE, reaction_substeps=None, tol=1e-10, max_iter=50,
-                precision=FP64, use_graph=True) -> SolverDesc:
+                precision=FP64, use_graph=True, profile=False) -> SolverDesc:
     s = SolverDesc()
     s.algorithm = algorithm
     s.levels = len(m) + 1
@@ -131,6 +133,7 @@ def make_solver(algorithm=AT_MGRIT, m=(8,), k=4, nu=1, fine_prop=PROP_PR_ADI,
         for j, v in enumerate(reaction_substeps):
             s.reaction_substeps[j] = v
     s.tol, s.max_iter, s.precision, s.use_graph = tol, max_iter, precision, int(use_graph)
+    s.profile = int(profile)
     return s
 
 
@@ -266,6 +269,12 @@ class Solver:
         self._enter()
         _check(load().atm_level_write(self.handle, level, array, t0, x.shape[0], ctypes.c_void_p(x.data_ptr())))
         self._leave()
+
+    def kernel_profile(self, which):
+        """(total ms, launches) of the timed level-0 row (0) or column (1) sweeps."""
+        ms, n = ctypes.c_double(), ctypes.c_longlong()
+        _check(load().atm_get_kernel_profile(self.handle, which, ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value
 
     def level_points(self, level) -> int:
         return load().atm_level_points(self.handle, level)

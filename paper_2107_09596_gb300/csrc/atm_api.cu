@@ -155,6 +155,15 @@ long long atm_last_launch_count(const atm_handle *h)
     return h ? h->p->launches : 0;
 }
 
+atm_status atm_get_kernel_profile(const atm_handle *h, int which, double *total_ms, long long *launches)
+{
+    if (!h || !total_ms || !launches || which < 0 || which > 1)
+        return atm::fail(ATM_ERR_INVALID_ARG, "invalid argument");
+    *total_ms = h->p->prof_ms[which];
+    *launches = h->p->prof_n[which];
+    return ATM_OK;
+}
+
 const char *atm_last_error(void)
 {
     return atm::last_error().c_str();

@@ -154,6 +154,7 @@ struct LaunchRec {
     double *partials = nullptr;
     int npartials = 0;
     double *norm_out = nullptr;
+    int prof_slot = -1;   // >= 0: time this sweep's kernels with event slot prof_slot
 };
 
 using Phase = std::vector<LaunchRec>;
@@ -165,6 +166,8 @@ struct PlanBase {
     cudaStream_t st = nullptr;
     std::vector<double> hist;
     long long launches = 0;
+    double prof_ms[2] = {0, 0};
+    long long prof_n[2] = {0, 0};
     virtual ~PlanBase() {}
     virtual atm_status finish_create() = 0;
     virtual atm_status set_state(int t0, int count, const double *src) = 0;
@@ -221,9 +224,12 @@ struct Plan : PlanBase {
     Phase st_coarse;
     cudaGraphExec_t gA = nullptr, gIter = nullptr, gSeq = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    std::vector<cudaEvent_t> pev;   // 4 per profiled sweep: row start/end, column start/end
+    int nprof = 0;
 
     ~Plan() override
     {
+        for (cudaEvent_t e : pev) cudaEventDestroy(e);
         if (gA) cudaGraphExecDestroy(gA);
         if (gIter) cudaGraphExecDestroy(gIter);
         if (gSeq) cudaGraphExecDestroy(gSeq);
@@ -601,6 +607,12 @@ struct Plan : PlanBase {
                 return fail(ATM_ERR_UNSUPPORTED, "no kernel instantiation for this grid size and precision");
         }
         build_phases();
+        nprof = 0;
+        if (sv.profile) {
+            Phase &ph = (sv.algorithm == ATM_SEQUENTIAL) ? seq : passA;
+            for (LaunchRec &r : ph)
+                if (r.type == L_SWEEP && r.level == 0 && nprof < 64) r.prof_slot = nprof++;
+        }
         d_jobs = take<Job<T>>(jobs.size() + 1);
         d_ajobs = take<AxpyJob<T>>(ajobs.size() + 1);
         d_dyn = take<Job<T>>((size_t)maxbatch);
@@ -631,7 +643,7 @@ struct Plan : PlanBase {
         return n;
     }
 
-    void launch_sweep(int l, const Job<T> *djobs, int njobs, int neg, double *part)
+    void launch_sweep(int l, const Job<T> *djobs, int njobs, int neg, double *part, int slot = -1)
     {
         const Level<T> &Lv = lv[l];
         SweepArgs<T> a = Lv.args;
@@ -639,12 +651,37 @@ struct Plan : PlanBase {
         a.neg = neg;
         a.partials = part;
         a.mid = mid;
+        const bool prof = slot >= 0 && slot < nprof;
+        if (prof) cudaEventRecordWithFlags(pev[4 * slot], st, cudaEventRecordExternal);
         if (is1d) {
             Lv.row<<<dim3(1, njobs), 32, 0, st>>>(a);
+            if (prof) cudaEventRecordWithFlags(pev[4 * slot + 1], st, cudaEventRecordExternal);
         } else {
             Lv.row<<<dim3(pb.ny / Lv.rows_per_cta, njobs), 32 * Lv.rows_per_cta, Lv.row_smem, st>>>(a);
+            if (prof) {
+                cudaEventRecordWithFlags(pev[4 * slot + 1], st, cudaEventRecordExternal);
+                cudaEventRecordWithFlags(pev[4 * slot + 2], st, cudaEventRecordExternal);
+            }
             Lv.col<<<dim3(pb.nx / 32, njobs), 32 * Lv.col_warps, 0, st>>>(a);
+            if (prof) cudaEventRecordWithFlags(pev[4 * slot + 3], st, cudaEventRecordExternal);
         }
+    }
+
+    // Add the event times of all profiled sweeps (the stream must be idle).
+    void collect_profile()
+    {
+        for (int sl = 0; sl < nprof; ++sl) {
+            float ms = 0;
+            if (cudaEventElapsedTime(&ms, pev[4 * sl], pev[4 * sl + 1]) == cudaSuccess) {
+                prof_ms[0] += ms;
+                prof_n[0] += 1;
+            }
+            if (!is1d && cudaEventElapsedTime(&ms, pev[4 * sl + 2], pev[4 * sl + 3]) == cudaSuccess) {
+                prof_ms[1] += ms;
+                prof_n[1] += 1;
+            }
+        }
+        cudaGetLastError();
     }
 
     void launch_axpy(const AxpyJob<T> *dj, int njobs)
@@ -658,7 +695,7 @@ struct Plan : PlanBase {
     {
         for (const LaunchRec &r : ph) {
             if (r.type == L_SWEEP)
-                launch_sweep(r.level, d_jobs + r.job_index, r.njobs, r.neg, r.partials);
+                launch_sweep(r.level, d_jobs + r.job_index, r.njobs, r.neg, r.partials, r.prof_slot);
             else if (r.type == L_AXPY)
                 launch_axpy(d_ajobs + r.job_index, r.njobs);
             else
@@ -676,7 +713,7 @@ struct Plan : PlanBase {
         for (const Phase *p : phs) {
             for (const LaunchRec &r : *p) {
                 if (r.type == L_SWEEP)
-                    launch_sweep(r.level, d_jobs + r.job_index, r.njobs, r.neg, r.partials);
+                    launch_sweep(r.level, d_jobs + r.job_index, r.njobs, r.neg, r.partials, r.prof_slot);
                 else if (r.type == L_AXPY)
                     launch_axpy(d_ajobs + r.job_index, r.njobs);
                 else
@@ -710,6 +747,8 @@ struct Plan : PlanBase {
         ATM_CK(cudaMemsetAsync(lv[0].u, 0, (size_t)lv[0].N * nsp * sizeof(T), st));
         ATM_CK(cudaEventCreate(&ev0));
         ATM_CK(cudaEventCreate(&ev1));
+        pev.assign(4 * (size_t)nprof, nullptr);
+        for (cudaEvent_t &e : pev) ATM_CK(cudaEventCreate(&e));
         ATM_CK(cudaStreamSynchronize(st));
         if (sv.use_graph && st != nullptr) {
             if (sv.algorithm == ATM_SEQUENTIAL) {
@@ -750,6 +789,7 @@ struct Plan : PlanBase {
             else ATM_TRY(run(passA));
             double r0 = 0;
             ATM_TRY(read_norm(&r0));
+            if (nprof) collect_profile();
             hist.push_back(r0);
             double rmin = r0;
             int growth = 0;
@@ -764,6 +804,7 @@ struct Plan : PlanBase {
                 }
                 double r = 0;
                 ATM_TRY(read_norm(&r));
+                if (nprof) collect_profile();
                 hist.push_back(r);
                 ++it;
                 if (r < rmin) rmin = r;
@@ -781,6 +822,7 @@ struct Plan : PlanBase {
         }
         ATM_CK(cudaEventRecord(ev1, st));
         ATM_CK(cudaEventSynchronize(ev1));
+        if (nprof && sv.algorithm == ATM_SEQUENTIAL) collect_profile();
         float ms = 0;
         ATM_CK(cudaEventElapsedTime(&ms, ev0, ev1));
         R.time_ms = ms;
