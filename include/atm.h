@@ -66,6 +66,13 @@ enum {
     ATM_PROP_PR_ADI = 1    /* (I - D/2 Lx) u* = (I + D/2 Ly) w, (I - D/2 Ly) u' = (I + D/2 Lx) u* */
 };
 
+/* Reaction part of the coarse Allen-Cahn propagators (levels >= 1, step D):
+ * the exact flow of u' = (u - u^3)/eps^2 over D,
+ *     u(D) = u0 / sqrt(u0^2 + (1 - u0^2) exp(-2 D / eps^2)),
+ * or s explicit Euler substeps of size D/s.  Level 0 always takes one
+ * explicit Euler step of size dt (the fine IMEX scheme). */
+enum { ATM_REACT_EXACT = 0, ATM_REACT_SUBSTEPS = 1 };
+
 enum { ATM_SEQUENTIAL = 0, ATM_MGRIT = 1, ATM_AT_MGRIT = 2 };
 
 /* Arithmetic of the sweep: FP64 throughout; FP32 throughout (residual norm
@@ -93,6 +100,7 @@ typedef struct {
     int fine_prop;                    /* propagator on level 0 (2D) */
     int coarse_prop;                  /* propagator on levels >= 1 (2D) */
     int reaction_substeps[ATM_MAX_LEVELS]; /* Allen-Cahn substeps per level; 0 = product of m below */
+    int coarse_reaction;              /* Allen-Cahn reaction on levels >= 1: ATM_REACT_EXACT or ATM_REACT_SUBSTEPS */
     double tol;                       /* stop when the residual 2-norm <= tol */
     int max_iter;                     /* maximum V-cycles */
     int precision;                    /* ATM_FP64 | ATM_FP32 | ATM_FP32_REFINED */
@@ -128,7 +136,8 @@ atm_status atm_create(const atm_problem *prob, const atm_solver *solver, void *d
 atm_status atm_set_initial_condition(atm_handle *h, const double *u0);
 
 /* Set the iterate at time points 1..nt_points-1 from `u` (FP64, nt_points
- * states, host or device; state 0 is ignored).  Default: zero. */
+ * states, host or device; state 0 is ignored).  u = NULL sets the zero guess
+ * (the default after atm_create). */
 atm_status atm_set_initial_guess(atm_handle *h, const double *u);
 
 /* Run the solver (Algorithm 2 V-cycles, or sequential stepping) until the

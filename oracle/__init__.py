@@ -43,6 +43,7 @@ class OrCfg(ctypes.Structure):
         ("nu", ctypes.c_int),
         ("prop", ctypes.c_int * MAXLEV),
         ("react_sub", ctypes.c_int * MAXLEV),
+        ("react_exact", ctypes.c_int * MAXLEV),
     ]
 
 
@@ -99,7 +100,7 @@ def _ptr(a):
 
 
 def make_cfg(kind, nx, ny=1, lx=1.0, ly=1.0, dt=1.0 / 1024, nt=1025, eps=0.02,
-             m=(8,), k=4, nu=1, prop=None, react_sub=None) -> OrCfg:
+             m=(8,), k=4, nu=1, prop=None, react_sub=None, react_exact=None) -> OrCfg:
     """Problem + solver description.  ``m`` has one entry per coarsening
     (levels = len(m) + 1).  ``k <= 0`` selects plain MGRIT.  ``prop`` per level
     defaults to PR on level 0 and split-BE on coarser levels (2D) or BE (1D)."""
@@ -117,6 +118,9 @@ def make_cfg(kind, nx, ny=1, lx=1.0, ly=1.0, dt=1.0 / 1024, nt=1025, eps=0.02,
     if react_sub is not None:
         for i, s in enumerate(react_sub):
             c.react_sub[i] = s
+    if react_exact is not None:
+        for i, e in enumerate(react_exact):
+            c.react_exact[i] = int(e)
     return c
 
 

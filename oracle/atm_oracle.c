@@ -36,7 +36,8 @@
  *              (I - D/2 Ly) u' = (I + D/2 Lx) u*.
  *     SPLIT  : split backward Euler ADI, (I - D Lx) y = w, (I - D Ly) u' = y.
  *     w      : for Allen-Cahn, s explicit Euler substeps of the reaction
- *              w <- w + (D/s) (w - w^3) / eps^2 applied first (Lie splitting);
+ *              w <- w + (D/s) (w - w^3) / eps^2 applied first (Lie splitting),
+ *              or (react_exact) the exact flow of the reaction ODE over D;
  *              w = u for the heat equation.
  *     FINEPOW: m_{l-1} applications of the next finer level's propagator
  *              (the exact coarse operator Phi^m of Sec. 3.1.1).
@@ -67,6 +68,7 @@ typedef struct {
     int nu;                 /* number of CF-relaxations after the first F-relaxation */
     int prop[OR_MAXLEV];    /* propagator per level */
     int react_sub[OR_MAXLEV]; /* reaction substeps per level; 0 = product of m below */
+    int react_exact[OR_MAXLEV]; /* 1: exact flow of the reaction ODE instead of substeps */
 } or_cfg;
 
 static int nspace(const or_cfg *c) { return c->kind == OR_HEAT1D ? c->nx : c->nx * c->ny; }
@@ -147,10 +149,20 @@ static void solve_periodic(int n, double a, const double *f, double *x, double *
  * ------------------------------------------------------------------------- */
 size_t or_prop_workspace(const or_cfg *c) { return (size_t)2 * nspace(c) + (size_t)8 * nmax(c); }
 
-static void reaction(const or_cfg *c, double D, int s, const double *u, double *w)
+static void reaction(const or_cfg *c, double D, int s, int exact, const double *u, double *w)
 {
     const int n = nspace(c);
     const double delta = D / (double)s, e2 = c->eps * c->eps;
+    if (exact) {
+        /* u' = (u - u^3)/eps^2 solved exactly over D:
+         * u(D) = u0 / sqrt(u0^2 + (1 - u0^2) exp(-2 D / eps^2)) */
+        const double E = exp(-2.0 * D / e2);
+        for (int p = 0; p < n; ++p) {
+            double v = u[p];
+            w[p] = v / sqrt(v * v + (1.0 - v * v) * E);
+        }
+        return;
+    }
     for (int p = 0; p < n; ++p) {
         double v = u[p];
         for (int q = 0; q < s; ++q) v = v + delta * (v - v * v * v) / e2;
@@ -227,7 +239,7 @@ void or_apply_prop_ws(const or_cfg *c, int l, const double *in, double *out, dou
     if (c->kind == OR_ALLEN_CAHN) {
         /* the reaction result lives past the ADI scratch (tmp + 8 vectors) */
         double *wr = ws + (size_t)nspace(c) + 8 * (size_t)nmax(c);
-        reaction(c, D, level_substeps(c, l), in, wr);
+        reaction(c, D, level_substeps(c, l), c->react_exact[l], in, wr);
         adi2d(c, D, pr, wr, out, ws);
     } else {
         adi2d(c, D, pr, in, out, ws);

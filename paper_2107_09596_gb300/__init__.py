@@ -17,6 +17,7 @@ from . import build as _build
 
 HEAT1D, HEAT2D, ALLEN_CAHN = 0, 1, 2
 PROP_SPLIT_BE, PROP_PR_ADI = 0, 1
+REACT_EXACT, REACT_SUBSTEPS = 0, 1
 SEQUENTIAL, MGRIT, AT_MGRIT = 0, 1, 2
 FP64, FP32, FP32_REFINED = 0, 1, 2
 STAGE_F_RELAX, STAGE_C_RELAX, STAGE_RESTRICT, STAGE_COARSEST, STAGE_CORRECT = range(5)
@@ -45,6 +46,7 @@ class SolverDesc(ctypes.Structure):
                 ("m", ctypes.c_int * MAX_LEVELS), ("k", ctypes.c_int), ("nu", ctypes.c_int),
                 ("fine_prop", ctypes.c_int), ("coarse_prop", ctypes.c_int),
                 ("reaction_substeps", ctypes.c_int * MAX_LEVELS),
+                ("coarse_reaction", ctypes.c_int),
                 ("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("precision", ctypes.c_int), ("use_graph", ctypes.c_int),
                 ("profile", ctypes.c_int)]
@@ -120,7 +122,8 @@ def make_problem(kind, nx, ny=1, lx=1.0, ly=1.0, dt=1e-3, nt_points=65, eps=0.02
 
 
 def make_solver(algorithm=AT_MGRIT, m=(8,), k=4, nu=1, fine_prop=PROP_PR_ADI,
-                coarse_prop=PROP_SPLIT_BE, reaction_substeps=None, tol=1e-10, max_iter=50,
+                coarse_prop=PROP_SPLIT_BE, reaction_substeps=None, coarse_reaction=REACT_EXACT,
+                tol=1e-10, max_iter=50,
                 precision=FP64, use_graph=True, profile=False) -> SolverDesc:
     s = SolverDesc()
     s.algorithm = algorithm
@@ -129,6 +132,7 @@ def make_solver(algorithm=AT_MGRIT, m=(8,), k=4, nu=1, fine_prop=PROP_PR_ADI,
         s.m[j] = mj
     s.k, s.nu = k, nu
     s.fine_prop, s.coarse_prop = fine_prop, coarse_prop
+    s.coarse_reaction = coarse_reaction
     if reaction_substeps:
         for j, v in enumerate(reaction_substeps):
             s.reaction_substeps[j] = v
@@ -206,10 +210,11 @@ class Solver:
         self._leave()
         return u0
 
-    def set_initial_guess(self, u):
-        u = self._f64(u)
+    def set_initial_guess(self, u=None):
+        """Iterate at time points >= 1 from `u` (nt states), or the zero guess."""
+        u = None if u is None else self._f64(u)
         self._enter()
-        _check(load().atm_set_initial_guess(self.handle, ctypes.c_void_p(_ptr(u))))
+        _check(load().atm_set_initial_guess(self.handle, ctypes.c_void_p(None if u is None else _ptr(u))))
         self._leave()
         return u
 

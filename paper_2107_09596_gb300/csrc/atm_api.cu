@@ -48,12 +48,43 @@ atm_status plan_create(const atm_problem *pb, const atm_solver *sv, void *ws, si
     return ATM_OK;
 }
 
+atm_status refined_size(const atm_problem *pb, const atm_solver *sv, size_t *bytes)
+{
+    atm::RefinedPlan p;
+    p.configure(*pb, *sv, nullptr);
+    atm_status s;
+    size_t need = p.measure(&s);
+    if (s != ATM_OK) return s;
+    *bytes = need;
+    return ATM_OK;
+}
+
+atm_status refined_create(const atm_problem *pb, const atm_solver *sv, void *ws, size_t bytes, void *stream,
+                          atm_handle **out)
+{
+    atm::RefinedPlan *p = new atm::RefinedPlan();
+    p->configure(*pb, *sv, reinterpret_cast<cudaStream_t>(stream));
+    atm_status s;
+    size_t need = p->measure(&s);
+    if (s == ATM_OK && bytes < need)
+        s = atm::fail(ATM_ERR_OOM, "workspace of %zu bytes is smaller than the %zu bytes needed", bytes, need);
+    if (s == ATM_OK) {
+        s = p->layout(reinterpret_cast<uintptr_t>(ws));
+        if (s == ATM_OK && p->off != need) s = atm::fail(ATM_ERR_INVALID_ARG, "internal layout mismatch");
+    }
+    if (s == ATM_OK) s = p->finish_create();
+    if (s != ATM_OK) {
+        delete p;
+        return s;
+    }
+    *out = new atm_handle{p};
+    return ATM_OK;
+}
+
 atm_status check_args(const atm_problem *pb, const atm_solver *sv)
 {
     if (!pb || !sv) return atm::fail(ATM_ERR_INVALID_ARG, "null problem or solver");
-    if (sv->precision == ATM_FP32_REFINED)
-        return atm::fail(ATM_ERR_UNSUPPORTED, "FP32 propagation with FP64 refinement is not built in this library");
-    if (sv->precision != ATM_FP64 && sv->precision != ATM_FP32)
+    if (sv->precision != ATM_FP64 && sv->precision != ATM_FP32 && sv->precision != ATM_FP32_REFINED)
         return atm::fail(ATM_ERR_INVALID_ARG, "unknown precision %d", sv->precision);
     return ATM_OK;
 }
@@ -67,6 +98,7 @@ atm_status atm_workspace_size(const atm_problem *prob, const atm_solver *solver,
     atm::last_error().clear();
     ATM_TRY(check_args(prob, solver));
     if (!bytes) return atm::fail(ATM_ERR_INVALID_ARG, "null bytes");
+    if (solver->precision == ATM_FP32_REFINED) return refined_size(prob, solver, bytes);
     return solver->precision == ATM_FP64 ? plan_size<double>(prob, solver, bytes) : plan_size<float>(prob, solver, bytes);
 }
 
@@ -80,6 +112,8 @@ atm_status atm_create(const atm_problem *prob, const atm_solver *solver, void *d
     if (!d_workspace) return atm::fail(ATM_ERR_INVALID_ARG, "null workspace");
     if (reinterpret_cast<uintptr_t>(d_workspace) % 256 != 0)
         return atm::fail(ATM_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    if (solver->precision == ATM_FP32_REFINED)
+        return refined_create(prob, solver, d_workspace, bytes, cuda_stream, out);
     return solver->precision == ATM_FP64
                ? plan_create<double>(prob, solver, d_workspace, bytes, cuda_stream, out)
                : plan_create<float>(prob, solver, d_workspace, bytes, cuda_stream, out);
@@ -93,7 +127,8 @@ atm_status atm_set_initial_condition(atm_handle *h, const double *u0)
 
 atm_status atm_set_initial_guess(atm_handle *h, const double *u)
 {
-    if (!h || !u) return atm::fail(ATM_ERR_INVALID_ARG, "null argument");
+    if (!h) return atm::fail(ATM_ERR_INVALID_ARG, "null handle");
+    if (!u) return h->p->zero_guess();
     const int n = h->p->level_points(0);
     const size_t nsp = h->p->pb.kind == ATM_HEAT1D ? (size_t)h->p->pb.nx : (size_t)h->p->pb.nx * h->p->pb.ny;
     return h->p->set_state(1, n - 1, u + nsp);

@@ -142,6 +142,88 @@ inline SweepFn<T> col_kernel(int CY, bool pr)
 
 namespace atm {
 
+// One level's propagator: coefficients, kernels and launch shape.
+template <typename T>
+struct LevelOp {
+    SweepArgs<T> args;
+    SweepFn<T> row = nullptr, col = nullptr;
+    int rows_per_cta = 8, col_warps = 1, col_chunk = 16;
+    size_t row_smem = 0;
+    std::vector<double> dir_w;   // 1D: Dirichlet rank-one vector (host copy)
+};
+
+// Build the level-l propagator of (pb, sv): step D = dt * m_0 * .. * m_{l-1};
+// heat1d backward Euler; 2D PR-ADI or split-BE ADI; Allen-Cahn reaction by
+// explicit substeps or (coarse levels, ATM_REACT_EXACT) the exact flow.
+// d_w: device table for the 1D rank-one vector (filled by the caller).
+template <typename T>
+inline LevelOp<T> make_level_op(const atm_problem &pb, const atm_solver &sv, int l, const T *d_w)
+{
+    LevelOp<T> op;
+    double D = pb.dt;
+    int prod = 1;
+    for (int j = 0; j < l; ++j) { D *= (double)sv.m[j]; prod *= sv.m[j]; }
+    const int nsub = sv.reaction_substeps[l] > 0 ? sv.reaction_substeps[l] : prod;
+    SweepArgs<T> &a = op.args;
+    std::memset(&a, 0, sizeof(a));
+    a.nx = pb.nx;
+    if (pb.kind == ATM_HEAT1D) {
+        a.ny = 1;
+        const double dx = pb.lx / (pb.nx + 1);
+        int C = 1;
+        while (32 * C < pb.nx) C *= 2;
+        LineCoef cx = make_line(D / (dx * dx), pb.nx, false, C);
+        a.cx = to_coef<T>(cx, d_w);
+        a.rx0 = (T)(1.0 / cx.kappa);
+        op.dir_w = cx.w;
+        op.row = row_kernel<T>(C, true, false, false);
+        op.rows_per_cta = 1;
+        return op;
+    }
+    a.ny = pb.ny;
+    const double dx = pb.lx / pb.nx, dy = pb.ly / pb.ny;
+    const int prop = (l == 0) ? sv.fine_prop : sv.coarse_prop;
+    const bool pr = (prop == ATM_PROP_PR_ADI);
+    const double f = pr ? 0.5 * D : D;
+    const double ax = f / (dx * dx), ay = f / (dy * dy);
+    const int C = pb.nx / 32;
+    const int CY = pb.ny <= 256 ? 16 : pb.ny / 16;
+    LineCoef cx = make_line(ax, pb.nx, true, C);
+    LineCoef cy = make_line(ay, pb.ny, true, CY);
+    a.cx = to_coef<T>(cx, nullptr);
+    a.cy = to_coef<T>(cy, nullptr);
+    if (pr) {
+        a.rx0 = (T)((1.0 - 2.0 * ay) / cx.kappa);
+        a.rx1 = (T)(ay / cx.kappa);
+        a.cy0 = (T)((1.0 - 2.0 * ax) / cy.kappa);
+        a.cy1 = (T)(ax / cy.kappa);
+    } else {
+        a.rx0 = (T)(1.0 / cx.kappa);
+        a.cy0 = (T)(1.0 / cy.kappa);
+    }
+    const bool react = (pb.kind == ATM_ALLEN_CAHN);
+    if (react) {
+        if (l > 0 && sv.coarse_reaction == ATM_REACT_EXACT) {
+            // exp(-2D/eps^2); in FP32 kept at the smallest normal value rather
+            // than underflowing to 0 (the flow's value is unchanged to FP32)
+            double E = std::exp(-2.0 * D / (pb.eps * pb.eps));
+            if (sizeof(T) == 4 && E < 1.1754943508222875e-38) E = 1.1754943508222875e-38;
+            a.react = (T)E;
+            a.nsub = -1;
+        } else {
+            a.react = (T)((D / nsub) / (pb.eps * pb.eps));
+            a.nsub = nsub;
+        }
+    }
+    op.row = row_kernel<T>(C, false, pr, react);
+    op.col = col_kernel<T>(CY, pr);
+    op.rows_per_cta = 8;
+    op.col_chunk = CY;
+    op.col_warps = pb.ny / CY;
+    op.row_smem = pr ? (size_t)(op.rows_per_cta + 2) * pb.nx * sizeof(T) : 0;
+    return op;
+}
+
 enum { L_SWEEP = 0, L_AXPY = 1, L_NORM = 2 };
 
 // One kernel launch (a sweep is one launch in 1D, two in 2D) of a phase.
@@ -177,6 +259,7 @@ struct PlanBase {
     virtual atm_status run_stage(int stage, int level) = 0;
     virtual atm_status level_io(int level, int array, int t0, int count, double *buf, bool write) = 0;
     virtual int level_points(int level) const = 0;
+    virtual atm_status zero_guess() = 0;
 };
 
 template <typename T>
@@ -197,8 +280,14 @@ inline bool pow2_in(int v, int lo, int hi)
     return (v & (v - 1)) == 0;
 }
 
+// Roles of a plan: a normal solver; the FP64 outer loop of the refined mode
+// (iterate and residual of every space-time point); the FP32 inner V-cycle of
+// the refined mode (FAS problem with a level-0 right-hand side).
+enum { ROLE_NORMAL = 0, ROLE_OUTER = 1, ROLE_INNER = 2 };
+
 template <typename T>
 struct Plan : PlanBase {
+    int role = ROLE_NORMAL;
     int L = 1;
     int nsp = 0;
     bool is1d = false;
@@ -220,6 +309,10 @@ struct Plan : PlanBase {
     AxpyJob<T> *d_ajobs = nullptr;
     Job<T> *d_dyn = nullptr;             // jobs of atm_apply_propagator
     Phase passA, rest, seq;
+    T *r_full = nullptr;   // ROLE_OUTER: residual of every point
+    T *ubase = nullptr;    // ROLE_INNER: FP32 copy of the outer iterate (base of the increments)
+    Phase resid_full;      // ROLE_OUTER: residual of every point + norm
+    Phase inner_cycle;     // ROLE_INNER: one V-cycle on the correction, ending with the F-relaxation
     std::vector<Phase> st_f, st_c, st_r, st_corr;
     Phase st_coarse;
     cudaGraphExec_t gA = nullptr, gIter = nullptr, gSeq = nullptr;
@@ -247,7 +340,7 @@ struct Plan : PlanBase {
     }
 
     T *st_ptr(T *arr, int t) const { return arr + (size_t)t * nsp; }
-    T *gl(int l, int t) const { return l == 0 ? nullptr : st_ptr(lv[l].g, t); }
+    T *gl(int l, int t) const { return lv[l].g ? st_ptr(lv[l].g, t) : nullptr; }
 
     // ---------------- validation and layout ----------------
     atm_status validate() const
@@ -278,6 +371,8 @@ struct Plan : PlanBase {
         }
         for (int l = 0; l < ATM_MAX_LEVELS; ++l)
             if (sv.reaction_substeps[l] < 0) return fail(ATM_ERR_INVALID_ARG, "reaction_substeps must be >= 0");
+        if (sv.coarse_reaction != ATM_REACT_EXACT && sv.coarse_reaction != ATM_REACT_SUBSTEPS)
+            return fail(ATM_ERR_INVALID_ARG, "unknown coarse_reaction %d", sv.coarse_reaction);
         if (!is1d) {
             if (sv.fine_prop < 0 || sv.fine_prop > 1 || sv.coarse_prop < 0 || sv.coarse_prop > 1)
                 return fail(ATM_ERR_INVALID_ARG, "unknown propagator");
@@ -288,58 +383,15 @@ struct Plan : PlanBase {
     void setup_level_op(int l)
     {
         Level<T> &Lv = lv[l];
-        double D = pb.dt;
-        int prod = 1;
-        for (int j = 0; j < l; ++j) { D *= (double)sv.m[j]; prod *= sv.m[j]; }
-        const int nsub = sv.reaction_substeps[l] > 0 ? sv.reaction_substeps[l] : prod;
-        SweepArgs<T> a;
-        std::memset(&a, 0, sizeof(a));
-        a.nx = pb.nx;
-        a.ny = is1d ? 1 : pb.ny;
-        if (is1d) {
-            const double dx = pb.lx / (pb.nx + 1);
-            int C = 1;
-            while (32 * C < pb.nx) C *= 2;
-            LineCoef cx = make_line(D / (dx * dx), pb.nx, false, C);
-            a.cx = to_coef<T>(cx, Lv.dir_w);
-            a.rx0 = (T)(1.0 / cx.kappa);
-            Lv.dir_w_host = cx.w;
-            Lv.row = row_kernel<T>(C, true, false, false);
-            Lv.rows_per_cta = 1;
-        } else {
-            const double dx = pb.lx / pb.nx, dy = pb.ly / pb.ny;
-            const int prop = (l == 0) ? sv.fine_prop : sv.coarse_prop;
-            const bool pr = (prop == ATM_PROP_PR_ADI);
-            const double f = pr ? 0.5 * D : D;
-            const double ax = f / (dx * dx), ay = f / (dy * dy);
-            const int C = pb.nx / 32;
-            const int CY = pb.ny <= 256 ? 16 : pb.ny / 16;
-            LineCoef cx = make_line(ax, pb.nx, true, C);
-            LineCoef cy = make_line(ay, pb.ny, true, CY);
-            a.cx = to_coef<T>(cx, nullptr);
-            a.cy = to_coef<T>(cy, nullptr);
-            if (pr) {
-                a.rx0 = (T)((1.0 - 2.0 * ay) / cx.kappa);
-                a.rx1 = (T)(ay / cx.kappa);
-                a.cy0 = (T)((1.0 - 2.0 * ax) / cy.kappa);
-                a.cy1 = (T)(ax / cy.kappa);
-            } else {
-                a.rx0 = (T)(1.0 / cx.kappa);
-                a.cy0 = (T)(1.0 / cy.kappa);
-            }
-            const bool react = (pb.kind == ATM_ALLEN_CAHN);
-            if (react) {
-                a.react = (T)((D / nsub) / (pb.eps * pb.eps));
-                a.nsub = nsub;
-            }
-            Lv.row = row_kernel<T>(C, false, pr, react);
-            Lv.col = col_kernel<T>(CY, pr);
-            Lv.rows_per_cta = 8;
-            Lv.col_chunk = CY;
-            Lv.col_warps = pb.ny / CY;
-            Lv.row_smem = pr ? (size_t)(Lv.rows_per_cta + 2) * pb.nx * sizeof(T) : 0;
-        }
-        Lv.args = a;
+        LevelOp<T> op = make_level_op<T>(pb, sv, l, Lv.dir_w);
+        Lv.args = op.args;
+        Lv.row = op.row;
+        Lv.col = op.col;
+        Lv.rows_per_cta = op.rows_per_cta;
+        Lv.col_chunk = op.col_chunk;
+        Lv.col_warps = op.col_warps;
+        Lv.row_smem = op.row_smem;
+        Lv.dir_w_host = op.dir_w;
     }
 
     // ---------------- phase builders ----------------
@@ -386,11 +438,21 @@ struct Plan : PlanBase {
     }
 
     static Job<T> job(const T *in, T *out, const T *g = nullptr, const T *h = nullptr,
-                      const T *sub = nullptr, T *out2 = nullptr)
+                      const T *sub = nullptr, T *out2 = nullptr, const T *base = nullptr)
     {
         Job<T> j;
-        j.in = in; j.out = out; j.g = g; j.h = h; j.sub = sub; j.out2 = out2;
+        j.in = in; j.out = out; j.g = g; j.h = h; j.sub = sub; j.out2 = out2; j.base = base;
         return j;
+    }
+
+    // Base state of a job whose input is time point t of level l (inner role
+    // only): the outer iterate at fine point t * m_0 * .. * m_{l-1}.
+    const T *bp(int l, int t) const
+    {
+        if (!ubase) return nullptr;
+        size_t f = (size_t)t;
+        for (int j = 0; j < l; ++j) f *= (size_t)sv.m[j];
+        return ubase + f * nsp;
     }
 
     static AxpyJob<T> ajob(T *out, const T *a, const T *b = nullptr, const T *c = nullptr)
@@ -412,7 +474,9 @@ struct Plan : PlanBase {
             std::vector<Job<T>> js;
             for (int i = 0; i < NC; ++i) {
                 const int t = i * m + j;
-                if (t < N) js.push_back(job(st_ptr(Lv.u, t - 1), st_ptr(Lv.u, t), gl(l, t)));
+                if (t < N)
+                    js.push_back(job(st_ptr(Lv.u, t - 1), st_ptr(Lv.u, t), gl(l, t), nullptr, nullptr, nullptr,
+                                     bp(l, t - 1)));
             }
             add_sweep(ph, l, std::move(js), 0, false);
         }
@@ -421,7 +485,7 @@ struct Plan : PlanBase {
             for (int i = 1; i < NC; ++i) {
                 const int t = i * m;
                 js.push_back(job(st_ptr(Lv.u, t - 1), resid == 1 ? st_ptr(yC, i) : nullptr, gl(l, t), nullptr,
-                                 st_ptr(Lv.u, t), resid == 2 ? st_ptr(lv[l + 1].r, i) : nullptr));
+                                 st_ptr(Lv.u, t), resid == 2 ? st_ptr(lv[l + 1].r, i) : nullptr, bp(l, t - 1)));
             }
             const int n = (int)js.size();
             add_sweep(ph, l, std::move(js), 0, norm);
@@ -433,10 +497,11 @@ struct Plan : PlanBase {
     void add_crelax(Phase &ph, int l)
     {
         Level<T> &Lv = lv[l];
-        if (l > 0) add_axpy(ph, {ajob(Lv.u, Lv.g)});
+        if (Lv.g) add_axpy(ph, {ajob(Lv.u, Lv.g)});
         std::vector<Job<T>> js;
         for (int i = 1; i < Lv.NC; ++i)
-            js.push_back(job(st_ptr(Lv.u, i * Lv.m - 1), st_ptr(Lv.u, i * Lv.m), gl(l, i * Lv.m)));
+            js.push_back(job(st_ptr(Lv.u, i * Lv.m - 1), st_ptr(Lv.u, i * Lv.m), gl(l, i * Lv.m), nullptr, nullptr,
+                             nullptr, bp(l, i * Lv.m - 1)));
         add_sweep(ph, l, std::move(js), 0, false);
     }
 
@@ -447,7 +512,8 @@ struct Plan : PlanBase {
         std::vector<Job<T>> js;
         for (int i = 1; i < Lv.NC; ++i) {
             const int t = i * Lv.m;
-            js.push_back(job(st_ptr(Lv.u, t - 1), nullptr, gl(l, t), nullptr, st_ptr(Lv.u, t), st_ptr(lv[l + 1].r, i)));
+            js.push_back(job(st_ptr(Lv.u, t - 1), nullptr, gl(l, t), nullptr, st_ptr(Lv.u, t), st_ptr(lv[l + 1].r, i),
+                             bp(l, t - 1)));
         }
         add_sweep(ph, l, std::move(js), 0, false);
     }
@@ -459,7 +525,7 @@ struct Plan : PlanBase {
     {
         Level<T> &F = lv[l];
         Level<T> &C = lv[l + 1];
-        add_axpy(ph, {l == 0 ? ajob(C.r, nullptr) : ajob(C.r, nullptr, F.g, F.u)});
+        add_axpy(ph, {F.g ? ajob(C.r, nullptr, F.g, F.u) : ajob(C.r, nullptr)});
         std::vector<AxpyJob<T>> cp;
         for (int i = 0; i < C.N; ++i) {
             cp.push_back(ajob(st_ptr(C.v, i), st_ptr(F.u, i * F.m)));
@@ -468,7 +534,8 @@ struct Plan : PlanBase {
         add_axpy(ph, std::move(cp));
         std::vector<Job<T>> js;
         for (int i = 1; i < C.N; ++i)
-            js.push_back(job(st_ptr(C.v, i - 1), st_ptr(C.g, i), st_ptr(C.v, i), st_ptr(C.r, i)));
+            js.push_back(job(st_ptr(C.v, i - 1), st_ptr(C.g, i), st_ptr(C.v, i), st_ptr(C.r, i), nullptr, nullptr,
+                             bp(l + 1, i - 1)));
         add_sweep(ph, l + 1, std::move(js), 1, false);
         add_axpy(ph, {ajob(C.g, C.v, C.r)});
     }
@@ -490,14 +557,17 @@ struct Plan : PlanBase {
                 std::vector<Job<T>> js;
                 for (int p = 0; p < C.N; ++p) {
                     const int j0 = p - k + 1 > 0 ? p - k + 1 : 0;
-                    if (p - j0 >= s) js.push_back(job(st_ptr(C.u, p), st_ptr(C.u, p), st_ptr(C.g, j0 + s)));
+                    if (p - j0 >= s)
+                        js.push_back(job(st_ptr(C.u, p), st_ptr(C.u, p), st_ptr(C.g, j0 + s), nullptr, nullptr,
+                                         nullptr, bp(l, j0 + s - 1)));
                 }
                 add_sweep(ph, l, std::move(js), 0, false);
             }
         } else {
             add_axpy(ph, {ajob(C.u, C.g)});
             for (int j = 1; j < C.N; ++j)
-                add_sweep(ph, l, {job(st_ptr(C.u, j - 1), st_ptr(C.u, j), st_ptr(C.g, j))}, 0, false);
+                add_sweep(ph, l, {job(st_ptr(C.u, j - 1), st_ptr(C.u, j), st_ptr(C.g, j), nullptr, nullptr, nullptr,
+                                      bp(l, j - 1))}, 0, false);
         }
     }
 
@@ -511,7 +581,7 @@ struct Plan : PlanBase {
         add_axpy(ph, std::move(js));
     }
 
-    // Algorithm 2 on level l >= 1 (one V-cycle visit).
+    // Algorithm 2 on level l (one V-cycle visit; level 0 only with a right-hand side).
     void add_level_cycle(Phase &ph, int l)
     {
         if (l == L - 1) {
@@ -535,6 +605,25 @@ struct Plan : PlanBase {
         ajobs.clear();
         passA.clear(); rest.clear(); seq.clear(); st_coarse.clear();
         st_f.assign(L, Phase()); st_c.assign(L, Phase()); st_r.assign(L, Phase()); st_corr.assign(L, Phase());
+        resid_full.clear(); inner_cycle.clear();
+        if (role == ROLE_OUTER) {
+            // r_j = Phi(u_{j-1}) - u_j for every j >= 1 (level 0 is homogeneous), with the norm
+            std::vector<Job<T>> js;
+            for (int j = 1; j < pb.nt_points; ++j)
+                js.push_back(job(st_ptr(lv[0].u, j - 1), nullptr, nullptr, nullptr, st_ptr(lv[0].u, j),
+                                 st_ptr(r_full, j)));
+            const int n = (int)js.size();
+            add_sweep(resid_full, 0, std::move(js), 0, true);
+            add_norm(resid_full, n * blocks_per_job(0));
+            return;
+        }
+        if (role == ROLE_INNER) {
+            // the defect problem e_j = [Phi(u_{j-1} + e_{j-1}) - Phi(u_{j-1})] + r_j,
+            // e_0 = r_0 = 0: its right-hand side is r itself (staged in g by the
+            // caller), its iterate starts at zero
+            add_level_cycle(inner_cycle, 0);
+            return;
+        }
         if (sv.algorithm == ATM_SEQUENTIAL) {
             for (int j = 1; j < pb.nt_points; ++j)
                 add_sweep(seq, 0, {job(st_ptr(lv[0].u, j - 1), st_ptr(lv[0].u, j))}, 0, false);
@@ -573,7 +662,7 @@ struct Plan : PlanBase {
         is1d = (pb.kind == ATM_HEAT1D);
         nsp = is1d ? pb.nx : pb.nx * pb.ny;
         ATM_TRY(validate());
-        L = (sv.algorithm == ATM_SEQUENTIAL) ? 1 : sv.levels;
+        L = (sv.algorithm == ATM_SEQUENTIAL || role == ROLE_OUTER) ? 1 : sv.levels;
         lv.assign(L, Level<T>());
         lv[0].N = pb.nt_points;
         for (int l = 0; l + 1 < L; ++l) {
@@ -582,7 +671,12 @@ struct Plan : PlanBase {
             lv[l + 1].N = lv[l].NC;
         }
         lv[0].u = take<T>((size_t)lv[0].N * nsp);
-        if (L > 1 && sv.nu == 1) yC = take<T>((size_t)lv[0].NC * nsp);
+        if (role == ROLE_OUTER) r_full = take<T>((size_t)lv[0].N * nsp);
+        if (role == ROLE_INNER) {
+            lv[0].g = take<T>((size_t)lv[0].N * nsp);
+            ubase = take<T>((size_t)lv[0].N * nsp);
+        }
+        if (L > 1 && sv.nu == 1 && role == ROLE_NORMAL) yC = take<T>((size_t)lv[0].NC * nsp);
         for (int l = 1; l < L; ++l) {
             const size_t b = (size_t)lv[l].N * nsp;
             lv[l].u = take<T>(b);
@@ -609,7 +703,7 @@ struct Plan : PlanBase {
         build_phases();
         nprof = 0;
         if (sv.profile) {
-            Phase &ph = (sv.algorithm == ATM_SEQUENTIAL) ? seq : passA;
+            Phase &ph = role == ROLE_OUTER ? resid_full : (sv.algorithm == ATM_SEQUENTIAL) ? seq : passA;
             for (LaunchRec &r : ph)
                 if (r.type == L_SWEEP && r.level == 0 && nprof < 64) r.prof_slot = nprof++;
         }
@@ -745,12 +839,13 @@ struct Plan : PlanBase {
         if (!ajobs.empty())
             ATM_CK(cudaMemcpyAsync(d_ajobs, ajobs.data(), ajobs.size() * sizeof(AxpyJob<T>), cudaMemcpyHostToDevice, st));
         ATM_CK(cudaMemsetAsync(lv[0].u, 0, (size_t)lv[0].N * nsp * sizeof(T), st));
+        if (r_full) ATM_CK(cudaMemsetAsync(r_full, 0, (size_t)lv[0].N * nsp * sizeof(T), st));
         ATM_CK(cudaEventCreate(&ev0));
         ATM_CK(cudaEventCreate(&ev1));
         pev.assign(4 * (size_t)nprof, nullptr);
         for (cudaEvent_t &e : pev) ATM_CK(cudaEventCreate(&e));
         ATM_CK(cudaStreamSynchronize(st));
-        if (sv.use_graph && st != nullptr) {
+        if (sv.use_graph && st != nullptr && role == ROLE_NORMAL) {
             if (sv.algorithm == ATM_SEQUENTIAL) {
                 ATM_TRY(capture({&seq}, &gSeq));
             } else {
@@ -845,6 +940,14 @@ struct Plan : PlanBase {
         int blocks = (int)((n + 255) / 256);
         if (blocks > 1024) blocks = 1024;
         convert_kernel<double, T><<<blocks, 256, 0, st>>>(src, dst, n);
+    }
+
+    // FP64 -> FP32 of arrays outside this plan (refined mode)
+    void convert_to_T_other(const double *src, float *dst, size_t n)
+    {
+        int blocks = (int)((n + 255) / 256);
+        if (blocks > 4096) blocks = 4096;
+        convert_kernel<double, float><<<blocks, 256, 0, st>>>(src, dst, n);
     }
 
     void convert_from_T(const T *src, double *dst, size_t n)
@@ -970,6 +1073,204 @@ struct Plan : PlanBase {
     }
 
     int level_points(int level) const override { return (level >= 0 && level < L) ? lv[level].N : -1; }
+
+    atm_status zero_guess() override
+    {
+        ATM_CK(cudaMemsetAsync(st_ptr(lv[0].u, 1), 0, (size_t)(lv[0].N - 1) * nsp * sizeof(T), st));
+        return ATM_OK;
+    }
+};
+
+}  // namespace atm
+
+namespace atm {
+
+// FP32 propagation with FP64 refinement: an FP64 defect-correction loop,
+//   r = g - A(u) at every space-time point (FP64 propagator, FP64 norm),
+//   one FP32 AT-MGRIT / MGRIT V-cycle (FAS on every level) on the defect
+//   problem for the correction e,
+//       e_0 = 0,  e_j = [Phi(u_{j-1} + e_{j-1}) - Phi(u_{j-1})] + r_j,
+//   whose propagator is the increment form of Phi around fp32(u) (rounding
+//   relative to e, not to u), starting from e = 0,
+//   u += e (FP64),
+// repeated until ||r||_2 <= tol.
+struct RefinedPlan : PlanBase {
+    Plan<double> outer;
+    Plan<float> inner;
+    cudaGraphExec_t gA = nullptr, gIter = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    size_t off = 0;
+
+    ~RefinedPlan() override
+    {
+        if (gA) cudaGraphExecDestroy(gA);
+        if (gIter) cudaGraphExecDestroy(gIter);
+        if (ev0) cudaEventDestroy(ev0);
+        if (ev1) cudaEventDestroy(ev1);
+    }
+
+    void configure(const atm_problem &p, const atm_solver &s, cudaStream_t stream)
+    {
+        pb = p;
+        sv = s;
+        st = stream;
+        outer.pb = p;
+        outer.sv = s;
+        outer.sv.use_graph = 0;
+        outer.role = ROLE_OUTER;
+        outer.st = stream;
+        inner.pb = p;
+        inner.sv = s;
+        inner.sv.use_graph = 0;
+        inner.sv.profile = 0;
+        inner.role = ROLE_INNER;
+        inner.st = stream;
+    }
+
+    size_t measure(atm_status *s)
+    {
+        if (sv.algorithm == ATM_SEQUENTIAL) {
+            *s = fail(ATM_ERR_INVALID_ARG, "the refined mode needs MGRIT or AT-MGRIT");
+            return 0;
+        }
+        size_t a = outer.measure(s);
+        if (*s != ATM_OK) return 0;
+        size_t b = inner.measure(s);
+        if (*s != ATM_OK) return 0;
+        return a + b;
+    }
+
+    atm_status layout(uintptr_t ws)
+    {
+        ATM_TRY(outer.layout(ws, outer.maxbatch, outer.npartials_max));
+        const size_t a = outer.off;
+        ATM_TRY(inner.layout(ws + a, inner.maxbatch, inner.npartials_max));
+        off = a + inner.off;
+        return ATM_OK;
+    }
+
+    size_t nstate_values() const { return (size_t)outer.lv[0].N * outer.nsp; }
+
+    // base and right-hand side in FP32, zero correction, FP32 cycle, FP64 update
+    void enqueue_inner()
+    {
+        const size_t n = nstate_values();
+        outer.convert_to_T_other(outer.lv[0].u, inner.ubase, n);
+        outer.convert_to_T_other(outer.r_full, inner.lv[0].g, n);
+        cudaMemsetAsync(inner.lv[0].u, 0, n * sizeof(float), st);
+        inner.run(inner.inner_cycle);
+        int blocks = (int)((n + 255) / 256);
+        if (blocks > 4096) blocks = 4096;
+        refine_update_kernel<<<blocks, 256, 0, st>>>(outer.lv[0].u, inner.lv[0].u, n);
+        launches += 3;
+    }
+
+    atm_status capture(bool with_inner, cudaGraphExec_t *out)
+    {
+        cudaGraph_t g = nullptr;
+        ATM_CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        if (with_inner) enqueue_inner();
+        outer.run(outer.resid_full);
+        cudaError_t e = cudaStreamEndCapture(st, &g);
+        if (e != cudaSuccess) return fail(ATM_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
+        e = cudaGraphInstantiate(out, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return fail(ATM_ERR_CUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
+        return ATM_OK;
+    }
+
+    atm_status finish_create() override
+    {
+        ATM_TRY(outer.finish_create());
+        ATM_TRY(inner.finish_create());
+        ATM_CK(cudaEventCreate(&ev0));
+        ATM_CK(cudaEventCreate(&ev1));
+        if (sv.use_graph && st != nullptr) {
+            ATM_TRY(capture(false, &gA));
+            ATM_TRY(capture(true, &gIter));
+        }
+        outer.launches = inner.launches = launches = 0;
+        return ATM_OK;
+    }
+
+    long long kernels_outer() const { return outer.kernels_in(outer.resid_full); }
+    long long kernels_inner() const
+    {
+        return 3 + inner.kernels_in(inner.inner_cycle);
+    }
+
+    atm_status solve(atm_result *res) override
+    {
+        atm_result R;
+        std::memset(&R, 0, sizeof(R));
+        hist.clear();
+        launches = outer.launches = inner.launches = 0;
+        long long counted = 0;
+        ATM_CK(cudaEventRecord(ev0, st));
+        if (gA) { ATM_CK(cudaGraphLaunch(gA, st)); counted += kernels_outer(); }
+        else ATM_TRY(outer.run(outer.resid_full));
+        double r0 = 0;
+        ATM_TRY(outer.read_norm(&r0));
+        if (outer.nprof) outer.collect_profile();
+        hist.push_back(r0);
+        double rmin = r0;
+        int growth = 0, it = 0;
+        while (std::isfinite(hist[it]) && hist[it] > sv.tol && it < sv.max_iter) {
+            if (gIter) {
+                ATM_CK(cudaGraphLaunch(gIter, st));
+                counted += kernels_inner() + kernels_outer();
+            } else {
+                enqueue_inner();
+                ATM_TRY(outer.run(outer.resid_full));
+            }
+            double r = 0;
+            ATM_TRY(outer.read_norm(&r));
+            if (outer.nprof) outer.collect_profile();
+            hist.push_back(r);
+            ++it;
+            if (r < rmin) rmin = r;
+            growth = (r > 1e3 * rmin) ? growth + 1 : 0;
+            if (growth >= 3) break;
+        }
+        ATM_CK(cudaGetLastError());
+        launches = counted + outer.launches + inner.launches;
+        R.iterations = it;
+        R.initial_residual = hist.front();
+        R.final_residual = hist.back();
+        R.converged = hist.back() <= sv.tol;
+        atm_status status = ATM_OK;
+        if (!std::isfinite(hist.back()) || growth >= 3)
+            status = fail(ATM_ERR_DIVERGED, "residual diverged (%g after %d cycles)", hist.back(), it);
+        else if (!R.converged)
+            status = fail(ATM_ERR_NOT_CONVERGED, "residual %g > tol %g after %d cycles", hist.back(), sv.tol, it);
+        ATM_CK(cudaEventRecord(ev1, st));
+        ATM_CK(cudaEventSynchronize(ev1));
+        float ms = 0;
+        ATM_CK(cudaEventElapsedTime(&ms, ev0, ev1));
+        R.time_ms = ms;
+        prof_ms[0] = outer.prof_ms[0]; prof_ms[1] = outer.prof_ms[1];
+        prof_n[0] = outer.prof_n[0]; prof_n[1] = outer.prof_n[1];
+        if (res) *res = R;
+        return status;
+    }
+
+    atm_status set_state(int t0, int count, const double *src) override { return outer.set_state(t0, count, src); }
+    atm_status get_state(int t0, int count, double *dst) override { return outer.get_state(t0, count, dst); }
+    atm_status zero_guess() override { return outer.zero_guess(); }
+    atm_status apply_prop(int level, const double *in, double *o, int n) override
+    {
+        return inner.apply_prop(level, in, o, n);
+    }
+    atm_status run_stage(int, int) override
+    {
+        return fail(ATM_ERR_UNSUPPORTED, "cycle stages are not exposed in the refined mode");
+    }
+    atm_status level_io(int level, int array, int t0, int count, double *buf, bool write) override
+    {
+        if (level == 0 && array == ATM_ARRAY_U) return outer.level_io(0, array, t0, count, buf, write);
+        return inner.level_io(level, array, t0, count, buf, write);
+    }
+    int level_points(int level) const override { return inner.level_points(level); }
 };
 
 }  // namespace atm

@@ -49,6 +49,11 @@ struct TriCoef {
 //   val = (neg ? -P : P) + g + h       (null addends are skipped)
 //   out = val                          (if out)
 //   r = val - sub; sum r^2; out2 = r   (if sub; out2 optional)
+// With base != null the job applies the increment of the propagator instead,
+//   P = Phi(base + in) - Phi(base),
+// evaluated without cancellation (the reaction increment is formed
+// algebraically; the diffusion part is linear), so that a small `in` keeps its
+// relative precision.
 template <typename T>
 struct Job {
     const T *in;
@@ -57,6 +62,7 @@ struct Job {
     const T *h;
     const T *sub;
     T *out2;
+    const T *base;
 };
 
 template <typename T>
@@ -69,8 +75,8 @@ struct SweepArgs {
     TriCoef<T> cy;            // implicit operator along y (columns)
     T rx0, rx1;               // row rhs: rx0 * w + rx1 * (w[y-1] + w[y+1])   (1/kappa_x folded in)
     T cy0, cy1;               // column rhs: cy0 * v + cy1 * (v[x-1] + v[x+1]) (1/kappa_y folded in)
-    T react;                  // Allen-Cahn: w <- w + react * (w - w^3), nsub times
-    int nsub;
+    T react;                  // Allen-Cahn: nsub > 0: w <- w + react * (w - w^3), nsub times;
+    int nsub;                 //   nsub < 0: exact flow, react = exp(-2 D / eps^2)
     double *partials;         // per-CTA sums of r^2 (null: no residual norm)
 };
 
@@ -143,12 +149,40 @@ __device__ __forceinline__ void store_chunk(double *p, const double (&v)[C])
     }
 }
 
-// Explicit Euler substeps of the Allen-Cahn reaction, w <- w + c (w - w^3).
+// Allen-Cahn reaction: nsub > 0 explicit Euler substeps w <- w + c (w - w^3);
+// nsub < 0 the exact flow w / sqrt(w^2 + (1 - w^2) E) with c = E = exp(-2D/eps^2).
+// E may underflow to 0 in FP32 (coarse steps with D/eps^2 > ~44); the flow maps
+// 0 to 0, which the guard keeps instead of 0/0.
 template <typename T>
 __device__ __forceinline__ T react_point(T w, T c, int nsub)
 {
+    if (nsub < 0) {
+        const T d = w * w + (T(1) - w * w) * c;
+        return d > T(0) ? w / sqrt(d) : T(0);
+    }
     for (int s = 0; s < nsub; ++s) w = w + c * (w - w * w * w);
     return w;
+}
+
+// Increment of the reaction, R(b + e) - R(b), written so that its rounding
+// error is relative to e.  Explicit Euler substep: (b+e) + c((b+e) - (b+e)^3)
+// - b - c(b - b^3) = e (1 + c (1 - 3b^2 - 3be - e^2)); the base advances with
+// the ordinary substep.  Exact flow F(v) = v / s(v), s(v) = sqrt(E + v^2 (1-E)):
+// F(a) - F(b) = e [s(b) - b (1-E)(a+b) / (s(a)+s(b))] / (s(a) s(b)), a = b + e.
+template <typename T>
+__device__ __forceinline__ T react_delta(T b, T e, T c, int nsub)
+{
+    if (nsub < 0) {
+        const T a = b + e, om = T(1) - c;
+        const T sa = sqrt(c + a * a * om), sb = sqrt(c + b * b * om);
+        const T den = sa * sb;
+        return den > T(0) ? e * (sb - b * om * (a + b) / (sa + sb)) / den : T(0);
+    }
+    for (int s = 0; s < nsub; ++s) {
+        e = e * (T(1) + c * (T(1) - T(3) * b * b - T(3) * b * e - e * e));
+        b = b + c * (b - b * b * b);
+    }
+    return e;
 }
 
 // ---------------------------------------------------------------------------
@@ -291,8 +325,15 @@ __global__ void __launch_bounds__(256) row_sweep_kernel(const __grid_constant__ 
             const int gy = (row0 - 1 + rr + ny) % ny;
             T v[V];
             load_chunk<V>(jb.in + (size_t)gy * nx + xx, v);
+            if (REACT && jb.base) {
+                T b[V];
+                load_chunk<V>(jb.base + (size_t)gy * nx + xx, b);
 #pragma unroll
-            for (int e = 0; e < V; ++e) v[e] = REACT ? react_point(v[e], a.react, a.nsub) : v[e];
+                for (int e = 0; e < V; ++e) v[e] = react_delta(b[e], v[e], a.react, a.nsub);
+            } else if (REACT) {
+#pragma unroll
+                for (int e = 0; e < V; ++e) v[e] = react_point(v[e], a.react, a.nsub);
+            }
             store_chunk<V>(tile + idx, v);
         }
         __syncthreads();
@@ -316,8 +357,15 @@ __global__ void __launch_bounds__(256) row_sweep_kernel(const __grid_constant__ 
     } else {
         T w[C];
         load_chunk<C>(jb.in + row_off + x0, w);
+        if (REACT && jb.base) {
+            T b[C];
+            load_chunk<C>(jb.base + row_off + x0, b);
 #pragma unroll
-        for (int k = 0; k < C; ++k) q[k] = a.rx0 * (REACT ? react_point(w[k], a.react, a.nsub) : w[k]);
+            for (int k = 0; k < C; ++k) q[k] = a.rx0 * react_delta(b[k], w[k], a.react, a.nsub);
+        } else {
+#pragma unroll
+            for (int k = 0; k < C; ++k) q[k] = a.rx0 * (REACT ? react_point(w[k], a.react, a.nsub) : w[k]);
+        }
     }
 
     warp_line_solve<T, C, DIRICHLET>(q, a.cx, lane, valid);
@@ -456,6 +504,14 @@ __global__ void norm_finalize_kernel(const double *partials, int count, double *
         if (norm_out) *norm_out = sqrt(t);
         if (sq_out) *sq_out = t;
     }
+}
+
+// Refinement update u += (double)e: the FP32 cycle's correction applied to the
+// FP64 iterate.
+__global__ void refine_update_kernel(double *u, const float *e, size_t n)
+{
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        u[i] = u[i] + (double)e[i];
 }
 
 template <typename Ti, typename To>

@@ -129,3 +129,26 @@ def test_allen_cahn_reaction_then_adi(orc):
     w = u + D * (u - u ** 3) / eps ** 2
     np.testing.assert_allclose(orc.apply_prop(ca, 0, u), orc.apply_prop(ch, 0, w),
                                rtol=1e-14, atol=1e-15)
+
+
+def test_exact_reaction_flow_against_fine_euler(orc):
+    """The exact flow of u' = (u - u^3)/eps^2 used on coarse levels agrees with
+    a very fine explicit Euler integration of the same ODE (first order in the
+    substep), on constant fields where the diffusion acts as the identity."""
+    n, D, eps = 8, 1e-4, 0.02
+    c_exact = orc.make_cfg(orc.ALLEN_CAHN, n, n, dt=D, nt=33, eps=eps, m=(4, 2),
+                           react_exact=[0, 1, 1])
+    for val in (-0.9, -0.05, 0.0, 0.01, 0.5, 1.0):
+        u = np.full((1, n, n), val)
+        for lev, steps in ((1, 4), (2, 8)):
+            out = orc.apply_prop(c_exact, lev, u)[0, 0, 0]
+            Dl = steps * D
+            errs = []
+            for s in (20000, 40000):
+                w = val
+                for _ in range(s):
+                    w = w + (Dl / s) * (w - w ** 3) / eps ** 2
+                errs.append(abs(w - out))
+            assert errs[1] <= 5e-5 * max(1.0, abs(out))
+            if errs[0] > 1e-12:
+                assert 1.6 < errs[0] / errs[1] < 2.4     # first-order convergence to the flow
