@@ -199,6 +199,39 @@ long long atm_last_launch_count(const atm_handle *h);
  * *total_ms = summed CUDA-event durations, *launches = launches timed. */
 atm_status atm_get_kernel_profile(const atm_handle *h, int which, double *total_ms, long long *launches);
 
+/* atm_apply_propagator_noalloc -- the paper has no counterpart to this call;
+ * it serves callers that must not allocate device memory.
+ *
+ * Computes what atm_apply_propagator computes for an FP64 handle made from
+ * (prob, solver): out[s] = Phi_level(in[s]) for s < nstates, with the level's
+ * propagator defined by the two descriptions exactly as for atm_create, but
+ * without a handle or a workspace.  The row-sweep intermediate and the
+ * per-state pointer table that the regular path keeps in the caller's
+ * workspace live instead in static device arrays of this library (32 MiB of
+ * intermediate, 64 table entries); every GPU on which the library's kernels
+ * are loaded holds them until the process exits.
+ *
+ * Callers that need it: code that may not call cudaMalloc at all, such as a
+ * component embedded in an application whose memory manager owns the whole
+ * device heap and accounts for every byte, or a path with latency guarantees
+ * where an allocation (which may synchronise the device) is not acceptable.
+ *
+ * Limits: the 2D problems only (ATM_HEAT2D, ATM_ALLEN_CAHN), nx and ny powers
+ * of two in [32, 512], nstates <= 64 and nstates * nx * ny * 8 <= 32 MiB;
+ * anything larger returns ATM_ERR_INVALID_ARG with the limit in the message.
+ * Arithmetic is FP64 whatever solver->precision says.
+ * d_in, d_out: FP64 device arrays of nstates states (they may alias); the work
+ * is issued on cuda_stream and the call returns without waiting for it.
+ * The first call on a device (with that device current) looks up the device
+ * addresses of the static arrays; make that first call before any stream
+ * capture on the device.  All calls on a device share the same arrays, so
+ * calls that may run at the same time on the GPU (other streams, other host
+ * threads) race and must be serialised by the caller.  Nothing in the arrays
+ * has to start at zero: each call writes everything it later reads. */
+atm_status atm_apply_propagator_noalloc(const atm_problem *prob, const atm_solver *solver, int level,
+                                        const double *d_in, double *d_out, int nstates,
+                                        void *cuda_stream);
+
 /* Message of the calling thread's last error ("" if none). */
 const char *atm_last_error(void);
 

@@ -62,7 +62,8 @@ EXPORTS = ["atm_workspace_size", "atm_create", "atm_set_initial_condition",
            "atm_set_initial_guess", "atm_solve", "atm_get_solution",
            "atm_get_residual_history", "atm_apply_propagator", "atm_run_stage",
            "atm_level_read", "atm_level_write", "atm_level_points",
-           "atm_last_launch_count", "atm_get_kernel_profile", "atm_last_error", "atm_destroy"]
+           "atm_last_launch_count", "atm_get_kernel_profile", "atm_apply_propagator_noalloc",
+           "atm_last_error", "atm_destroy"]
 
 _lib = None
 
@@ -99,6 +100,7 @@ def load(build_if_missing: bool = True):
     L.atm_last_launch_count.argtypes = [vp]
     L.atm_last_launch_count.restype = ctypes.c_longlong
     L.atm_get_kernel_profile.argtypes = [vp, i, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_longlong)]
+    L.atm_apply_propagator_noalloc.argtypes = [ctypes.POINTER(Problem), ctypes.POINTER(SolverDesc), i, vp, vp, i, vp]
     L.atm_last_error.restype = ctypes.c_char_p
     L.atm_destroy.argtypes = [vp]
     for name in EXPORTS:

@@ -1,4 +1,7 @@
-"""Build libatm.so in-tree with nvcc for sm_103a (GB300)."""
+"""Build libatm.so in-tree with nvcc for sm_103a (GB300).
+
+The translation units compile in parallel to objects under _build/ and are
+linked into paper_2107_09596_gb300/libatm.so."""
 from __future__ import annotations
 
 import os
@@ -9,16 +12,17 @@ SRC_DIR = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libatm.so")
 ROOT = os.path.dirname(HERE)
 HEADER = os.path.join(ROOT, "include", "atm.h")
+OBJ_DIR = os.path.join(ROOT, "_build")
 
 NVCC_FLAGS = [
     "-gencode", "arch=compute_103a,code=sm_103a",
     "-O3", "-lineinfo", "-std=c++17",
-    "-Xcompiler", "-fPIC", "-shared",
+    "-Xcompiler", "-fPIC",
 ]
 
 
 def sources():
-    return [os.path.join(SRC_DIR, "atm_api.cu")]
+    return [os.path.join(SRC_DIR, f) for f in ("atm_api.cu", "atm_noalloc.cu")]
 
 
 def _newest_input() -> float:
@@ -30,13 +34,27 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _newest_input():
         return LIB
     nvcc = os.environ.get("NVCC", "nvcc")
+    os.makedirs(OBJ_DIR, exist_ok=True)
+    objs, procs = [], []
+    for src in sources():
+        obj = os.path.join(OBJ_DIR, os.path.basename(src) + ".%d.o" % os.getpid())
+        objs.append(obj)
+        procs.append(subprocess.Popen([nvcc] + NVCC_FLAGS + ["-c", "-o", obj, src],
+                                      stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True))
+    logs = []
+    for p in procs:
+        out, _ = p.communicate()
+        logs.append(out)
+        if p.returncode != 0:
+            raise RuntimeError("nvcc failed:\n" + out)
     tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = [nvcc] + NVCC_FLAGS + ["-o", tmp] + sources()
-    res = subprocess.run(cmd, capture_output=True, text=True)
+    res = subprocess.run([nvcc, "-shared", "-o", tmp] + objs, capture_output=True, text=True)
     if res.returncode != 0:
-        raise RuntimeError("nvcc failed:\n" + res.stdout + res.stderr)
+        raise RuntimeError("nvcc link failed:\n" + res.stdout + res.stderr)
+    for o in objs:
+        os.remove(o)
     if verbose:
-        print(res.stdout + res.stderr)
+        print("".join(logs) + res.stdout + res.stderr)
     os.replace(tmp, LIB)
     return LIB
 

@@ -494,7 +494,7 @@ __global__ void axpy_kernel(const AxpyJob<T> *jobs, size_t n)
 
 // Sum `count` partial sums in a fixed order; write sqrt to *norm_out and the
 // squared sum to *sq_out (either may be null).
-__global__ void norm_finalize_kernel(const double *partials, int count, double *norm_out, double *sq_out)
+static __global__ void norm_finalize_kernel(const double *partials, int count, double *norm_out, double *sq_out)
 {
     __shared__ double sh[32];
     double v = 0.0;
@@ -508,7 +508,7 @@ __global__ void norm_finalize_kernel(const double *partials, int count, double *
 
 // Refinement update u += (double)e: the FP32 cycle's correction applied to the
 // FP64 iterate.
-__global__ void refine_update_kernel(double *u, const float *e, size_t n)
+static __global__ void refine_update_kernel(double *u, const float *e, size_t n)
 {
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
         u[i] = u[i] + (double)e[i];
