@@ -276,7 +276,7 @@ def main():
     for _ in range(args.warmup):
         res = step()
     torch.cuda.synchronize(device)
-    prof0 = [solver.kernel_profile(0), solver.kernel_profile(1)]
+    prof0 = [solver.kernel_profile(i) for i in range(3)]
     clocks = ClockSampler(device.index if device.index is not None else 0)
     barrier(dist, device)
     torch.cuda.synchronize(device)
@@ -297,7 +297,7 @@ def main():
     ms = e0.elapsed_time(e1) / args.steps
     ms = max_over_ranks(dist, ms, device)
     value = world * (w["nt"] - 1) / (ms / 1e3)
-    prof1 = [solver.kernel_profile(0), solver.kernel_profile(1)]
+    prof1 = [solver.kernel_profile(i) for i in range(3)]
 
     # end to end through host buffers: u0 from pinned host memory in, the final
     # state and the residual history out, copies inside the timed region
@@ -317,44 +317,46 @@ def main():
     e2e_ms = max_over_ranks(dist, e2e_ms, device)
     state_bytes = int(np.prod(shape)) * 8
 
-    # roofline of the dominant level-0 sweep kernel (event-timed during the timed steps)
+    # roofline of the level-0 propagator application (row + column sweep of
+    # every state of one launch table), event-timed during the timed steps
     pk = peaks()
     n_val = int(np.prod(shape))
-    # states per profiled launch: the level-0 relaxation launches cover every
-    # interval; in the refined mode the profiled launch is the FP64 residual of
-    # every time point
+    # states per profiled launch table: the level-0 relaxation launches cover
+    # every interval; in the refined mode the profiled table is the FP64
+    # residual of every time point
     jobs = {"allen_cahn_256": 256, "heat1d_127": 128}[args.workload]
     if args.precision == "fp32r":
         jobs = w["nt"] - 1
-    tot = [prof1[i][0] - prof0[i][0] for i in range(2)]
-    cnt = [prof1[i][1] - prof0[i][1] for i in range(2)]
-    which = 0 if tot[0] >= tot[1] else 1
-    avg_ms = tot[which] / max(cnt[which], 1)
+    if args.algorithm == "seq":
+        jobs = 1
+    tot = prof1[2][0] - prof0[2][0]
+    cnt = prof1[2][1] - prof0[2][1]
+    avg_ms = tot / max(cnt, 1)
     if not avg_ms > 0:
         raise RuntimeError("kernel profile recorded no launches")
-    name = ["row_sweep", "col_sweep"][which]
+    name = "row_sweep_kernel+col_sweep_kernel (level-0 propagator)"
     if w["kind"] == "heat1d":
-        fkey = ("row", "heat1d")
+        fpv = FLOPS_PER_VALUE[("row", "heat1d")]
+        name = "row_sweep_kernel (level-0 propagator)"
     else:
-        fkey = ("row", "pr_react") if which == 0 else ("col", "pr")
+        fpv = FLOPS_PER_VALUE[("row", "pr_react")] + FLOPS_PER_VALUE[("col", "pr")]
     traffic_db = load_json(os.path.join(ROOT, "profiles", "traffic.json"), {}) or {}
-    tkey = f"{args.workload}:{args.precision}:{name}"
-    tr = traffic_db.get(tkey)
+    tr = traffic_db.get(f"{args.workload}:{args.precision}")
     traffic = tr["bytes_per_launch"] if tr and tr.get("source_hash") == kernel_source_hash() else None
     if args.precision in ("fp64", "fp32r"):
-        flops = FLOPS_PER_VALUE[fkey] * n_val * jobs
+        flops = fpv * n_val * jobs
         achieved = flops / (avg_ms / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": pk["fp64_tflops"], "unit": "TFLOP/s",
                 "frac": achieved / pk["fp64_tflops"], "traffic": traffic, "kernel": name,
-                "avg_launch_ms": avg_ms, "launches_timed": cnt[which],
+                "avg_launch_ms": avg_ms, "launches_timed": cnt,
                 "peak_source": "derived FP64 FMA rate (152 SMs x 2 DFMA/clk x 2.07 GHz)",
-                "algorithmic": f"{FLOPS_PER_VALUE[fkey]} flop/value x {n_val} values x {jobs} states"}
+                "algorithmic": f"{fpv} flop/value x {n_val} values x {jobs} states"}
     else:
         nbytes = 2 * n_val * 4 * jobs
         achieved = nbytes / (avg_ms / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / pk["hbm_gbs"], "traffic": traffic, "kernel": name,
-                "avg_launch_ms": avg_ms, "launches_timed": cnt[which],
+                "avg_launch_ms": avg_ms, "launches_timed": cnt,
                 "peak_source": f"{pk['hbm_src']} STREAM copy (MEASURED_PEAKS.json)",
                 "algorithmic": f"read + write of {jobs} states of {n_val} fp32 values"}
 

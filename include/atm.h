@@ -195,8 +195,10 @@ long long atm_last_launch_count(const atm_handle *h);
 
 /* Kernel time of the level-0 relaxation sweeps of all solves since
  * atm_create (needs solver.profile = 1): `which` = 0 row sweeps (implicit in
- * x; the whole propagator for heat1d), 1 column sweeps (implicit in y).
- * *total_ms = summed CUDA-event durations, *launches = launches timed. */
+ * x), 1 column sweeps (implicit in y), 2 whole propagator applications (row +
+ * column sweeps of one launch table; the only one for heat1d, and the only
+ * one when a sweep runs in several row/column chunks).
+ * *total_ms = summed CUDA-event durations, *launches = sweeps timed. */
 atm_status atm_get_kernel_profile(const atm_handle *h, int which, double *total_ms, long long *launches);
 
 /* atm_apply_propagator_noalloc -- the paper has no counterpart to this call;

@@ -192,7 +192,7 @@ long long atm_last_launch_count(const atm_handle *h)
 
 atm_status atm_get_kernel_profile(const atm_handle *h, int which, double *total_ms, long long *launches)
 {
-    if (!h || !total_ms || !launches || which < 0 || which > 1)
+    if (!h || !total_ms || !launches || which < 0 || which > 2)
         return atm::fail(ATM_ERR_INVALID_ARG, "invalid argument");
     *total_ms = h->p->prof_ms[which];
     *launches = h->p->prof_n[which];

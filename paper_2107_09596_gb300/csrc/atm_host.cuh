@@ -127,13 +127,28 @@ inline SweepFn<T> row_kernel(int C, bool dirichlet, bool pr, bool react)
     return react ? pick_row<T, false, false, true, false>(C) : pick_row<T, false, false, false, false>(C);
 }
 
-template <typename T>
-inline SweepFn<T> col_kernel(int CY, bool pr)
+template <typename T, int CY, int W>
+inline SweepFn<T> col_pick(bool pr)
 {
-    if (CY == 16) return pr ? col_sweep_kernel<T, 16, true> : col_sweep_kernel<T, 16, false>;
-    if (CY == 32) return pr ? col_sweep_kernel<T, 32, true> : col_sweep_kernel<T, 32, false>;
+    return pr ? col_sweep_kernel<T, CY, W, true> : col_sweep_kernel<T, CY, W, false>;
+}
+
+// Column kernel for ny rows: CY rows per thread, W = ny / CY warps.
+template <typename T>
+inline SweepFn<T> col_kernel(int CY, int W, bool pr)
+{
+    if (CY == 16) {
+        switch (W) {
+        case 2: return col_pick<T, 16, 2>(pr);
+        case 4: return col_pick<T, 16, 4>(pr);
+        case 8: return col_pick<T, 16, 8>(pr);
+        case 16: return col_pick<T, 16, 16>(pr);
+        default: return nullptr;
+        }
+    }
+    if (CY == 32 && W == 16) return col_pick<T, 32, 16>(pr);
     if constexpr (sizeof(T) == 4) {
-        if (CY == 64) return pr ? col_sweep_kernel<T, 64, true> : col_sweep_kernel<T, 64, false>;
+        if (CY == 64 && W == 16) return col_pick<T, 64, 16>(pr);
     }
     return nullptr;
 }
@@ -216,11 +231,13 @@ inline LevelOp<T> make_level_op(const atm_problem &pb, const atm_solver &sv, int
         }
     }
     op.row = row_kernel<T>(C, false, pr, react);
-    op.col = col_kernel<T>(CY, pr);
+    op.col = col_kernel<T>(CY, pb.ny / CY, pr);
     op.rows_per_cta = 8;
     op.col_chunk = CY;
     op.col_warps = pb.ny / CY;
-    op.row_smem = pr ? (size_t)(op.rows_per_cta + 2) * pb.nx * sizeof(T) : 0;
+    // padded tile rows: 16 bytes after every 128 bytes (see row_sweep_kernel)
+    const size_t pitch = (size_t)pb.nx + (size_t)(pb.nx * sizeof(T) / 128) * (16 / sizeof(T));
+    op.row_smem = pr ? (size_t)(op.rows_per_cta + 2) * pitch * sizeof(T) : 0;
     return op;
 }
 
@@ -248,8 +265,10 @@ struct PlanBase {
     cudaStream_t st = nullptr;
     std::vector<double> hist;
     long long launches = 0;
-    double prof_ms[2] = {0, 0};
-    long long prof_n[2] = {0, 0};
+    double prof_ms[3] = {0, 0, 0};   // row sweeps, column sweeps, whole propagator applications
+    long long prof_n[3] = {0, 0, 0};
+    int chunk = 0;                    // states per row+column launch pair on level 0 (0 = all)
+    float tuned_ms = 0;               // autotuned sweep time
     virtual ~PlanBase() {}
     virtual atm_status finish_create() = 0;
     virtual atm_status set_state(int t0, int count, const double *src) = 0;
@@ -317,7 +336,7 @@ struct Plan : PlanBase {
     Phase st_coarse;
     cudaGraphExec_t gA = nullptr, gIter = nullptr, gSeq = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    std::vector<cudaEvent_t> pev;   // 4 per profiled sweep: row start/end, column start/end
+    std::vector<cudaEvent_t> pev;   // 4 per profiled sweep: start, after the rows, before the columns, end
     int nprof = 0;
 
     ~Plan() override
@@ -733,32 +752,51 @@ struct Plan : PlanBase {
     long long kernels_in(const Phase &ph) const
     {
         long long n = 0;
-        for (const LaunchRec &r : ph) n += (r.type == L_SWEEP && !is1d) ? 2 : 1;
+        for (const LaunchRec &r : ph) n += (r.type == L_SWEEP && !is1d) ? 2 * sweep_pairs(r.level, r.njobs) : 1;
         return n;
     }
 
+    // One propagator application per job.  2D: row sweep then column sweep; on
+    // level 0 the jobs go in chunks of `chunk` states per row/column pair so
+    // that the row-sweep intermediate is still in L2 when the column sweep
+    // reads it.
     void launch_sweep(int l, const Job<T> *djobs, int njobs, int neg, double *part, int slot = -1)
     {
         const Level<T> &Lv = lv[l];
         SweepArgs<T> a = Lv.args;
-        a.jobs = djobs;
         a.neg = neg;
-        a.partials = part;
         a.mid = mid;
         const bool prof = slot >= 0 && slot < nprof;
         if (prof) cudaEventRecordWithFlags(pev[4 * slot], st, cudaEventRecordExternal);
         if (is1d) {
+            a.jobs = djobs;
+            a.partials = part;
             Lv.row<<<dim3(1, njobs), 32, 0, st>>>(a);
-            if (prof) cudaEventRecordWithFlags(pev[4 * slot + 1], st, cudaEventRecordExternal);
-        } else {
-            Lv.row<<<dim3(pb.ny / Lv.rows_per_cta, njobs), 32 * Lv.rows_per_cta, Lv.row_smem, st>>>(a);
-            if (prof) {
+            if (prof) cudaEventRecordWithFlags(pev[4 * slot + 3], st, cudaEventRecordExternal);
+            return;
+        }
+        const int cs = (l == 0 && chunk > 0 && chunk < njobs) ? chunk : njobs;
+        const bool split = cs == njobs;
+        for (int j0 = 0; j0 < njobs; j0 += cs) {
+            const int nj = njobs - j0 < cs ? njobs - j0 : cs;
+            a.jobs = djobs + j0;
+            a.partials = part ? part + (size_t)j0 * (pb.nx / 32) : nullptr;
+            Lv.row<<<dim3(pb.ny / Lv.rows_per_cta, nj), 32 * Lv.rows_per_cta, Lv.row_smem, st>>>(a);
+            if (prof && split) {
                 cudaEventRecordWithFlags(pev[4 * slot + 1], st, cudaEventRecordExternal);
                 cudaEventRecordWithFlags(pev[4 * slot + 2], st, cudaEventRecordExternal);
             }
-            Lv.col<<<dim3(pb.nx / 32, njobs), 32 * Lv.col_warps, 0, st>>>(a);
-            if (prof) cudaEventRecordWithFlags(pev[4 * slot + 3], st, cudaEventRecordExternal);
+            Lv.col<<<dim3(pb.nx / 32, nj), 32 * Lv.col_warps, 0, st>>>(a);
         }
+        if (prof) cudaEventRecordWithFlags(pev[4 * slot + 3], st, cudaEventRecordExternal);
+    }
+
+    // Number of row/column launch pairs of a sweep of njobs states on level l.
+    int sweep_pairs(int l, int njobs) const
+    {
+        if (is1d) return 1;
+        const int cs = (l == 0 && chunk > 0 && chunk < njobs) ? chunk : njobs;
+        return (njobs + cs - 1) / cs;
     }
 
     // Add the event times of all profiled sweeps (the stream must be idle).
@@ -766,7 +804,11 @@ struct Plan : PlanBase {
     {
         for (int sl = 0; sl < nprof; ++sl) {
             float ms = 0;
-            if (cudaEventElapsedTime(&ms, pev[4 * sl], pev[4 * sl + 1]) == cudaSuccess) {
+            if (cudaEventElapsedTime(&ms, pev[4 * sl], pev[4 * sl + 3]) == cudaSuccess) {
+                prof_ms[2] += ms;
+                prof_n[2] += 1;
+            }
+            if (!is1d && cudaEventElapsedTime(&ms, pev[4 * sl], pev[4 * sl + 1]) == cudaSuccess) {
                 prof_ms[0] += ms;
                 prof_n[0] += 1;
             }
@@ -778,6 +820,51 @@ struct Plan : PlanBase {
         cudaGetLastError();
     }
 
+    // Autotuner for the level-0 chunk size: times every level-0 sweep of `ph`
+    // in order (the dependent steps of a relaxation pass, so that inputs come
+    // from where a real cycle finds them) for each candidate, with CUDA events
+    // over 2 repetitions after a warm-up, and keeps the fastest.  Runs on the
+    // state present at create time (zero), for which the sweeps write zeros.
+    atm_status autotune_chunk(const Phase &ph)
+    {
+        std::vector<const LaunchRec *> recs;
+        int maxjobs = 0;
+        for (const LaunchRec &r : ph)
+            if (r.type == L_SWEEP && r.level == 0) {
+                recs.push_back(&r);
+                if (r.njobs > maxjobs) maxjobs = r.njobs;
+            }
+        chunk = 0;
+        if (is1d || recs.empty() || maxjobs <= 64) return ATM_OK;
+        const int cands[] = {0, 64, 128, 256, 512};
+        float best = 1e30f;
+        int best_c = 0;
+        cudaEvent_t e0, e1;
+        ATM_CK(cudaEventCreate(&e0));
+        ATM_CK(cudaEventCreate(&e1));
+        for (int c : cands) {
+            if (c >= maxjobs) continue;
+            chunk = c;
+            for (const LaunchRec *r : recs)
+                launch_sweep(0, d_jobs + r->job_index, r->njobs, r->neg, r->partials);
+            cudaEventRecord(e0, st);
+            for (int rep = 0; rep < 2; ++rep)
+                for (const LaunchRec *r : recs)
+                    launch_sweep(0, d_jobs + r->job_index, r->njobs, r->neg, r->partials);
+            cudaEventRecord(e1, st);
+            cudaEventSynchronize(e1);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) { best = ms; best_c = c; }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        chunk = best_c;
+        tuned_ms = best / 2;
+        ATM_CK(cudaGetLastError());
+        return ATM_OK;
+    }
+
     void launch_axpy(const AxpyJob<T> *dj, int njobs)
     {
         int blocks = (int)((nsp + 255) / 256);
@@ -785,7 +872,7 @@ struct Plan : PlanBase {
         axpy_kernel<T><<<dim3(blocks, njobs), 256, 0, st>>>(dj, (size_t)nsp);
     }
 
-    atm_status run(const Phase &ph)
+    void enqueue(const Phase &ph)
     {
         for (const LaunchRec &r : ph) {
             if (r.type == L_SWEEP)
@@ -795,6 +882,11 @@ struct Plan : PlanBase {
             else
                 norm_finalize_kernel<<<1, 1024, 0, st>>>(r.partials, r.npartials, r.norm_out, nullptr);
         }
+    }
+
+    atm_status run(const Phase &ph)
+    {
+        enqueue(ph);
         ATM_CK(cudaGetLastError());
         launches += kernels_in(ph);
         return ATM_OK;
@@ -804,16 +896,7 @@ struct Plan : PlanBase {
     {
         cudaGraph_t g = nullptr;
         ATM_CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-        for (const Phase *p : phs) {
-            for (const LaunchRec &r : *p) {
-                if (r.type == L_SWEEP)
-                    launch_sweep(r.level, d_jobs + r.job_index, r.njobs, r.neg, r.partials, r.prof_slot);
-                else if (r.type == L_AXPY)
-                    launch_axpy(d_ajobs + r.job_index, r.njobs);
-                else
-                    norm_finalize_kernel<<<1, 1024, 0, st>>>(r.partials, r.npartials, r.norm_out, nullptr);
-            }
-        }
+        for (const Phase *p : phs) enqueue(*p);
         cudaError_t e = cudaStreamEndCapture(st, &g);
         if (e != cudaSuccess) return fail(ATM_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
         e = cudaGraphInstantiate(out, g, 0);
@@ -840,10 +923,17 @@ struct Plan : PlanBase {
             ATM_CK(cudaMemcpyAsync(d_ajobs, ajobs.data(), ajobs.size() * sizeof(AxpyJob<T>), cudaMemcpyHostToDevice, st));
         ATM_CK(cudaMemsetAsync(lv[0].u, 0, (size_t)lv[0].N * nsp * sizeof(T), st));
         if (r_full) ATM_CK(cudaMemsetAsync(r_full, 0, (size_t)lv[0].N * nsp * sizeof(T), st));
+        if (role == ROLE_INNER) {
+            ATM_CK(cudaMemsetAsync(lv[0].g, 0, (size_t)lv[0].N * nsp * sizeof(T), st));
+            ATM_CK(cudaMemsetAsync(ubase, 0, (size_t)lv[0].N * nsp * sizeof(T), st));
+        }
         ATM_CK(cudaEventCreate(&ev0));
         ATM_CK(cudaEventCreate(&ev1));
         pev.assign(4 * (size_t)nprof, nullptr);
         for (cudaEvent_t &e : pev) ATM_CK(cudaEventCreate(&e));
+        if (sv.algorithm != ATM_SEQUENTIAL || role == ROLE_OUTER)
+            ATM_TRY(autotune_chunk(role == ROLE_OUTER ? resid_full : role == ROLE_INNER ? inner_cycle : passA));
+        ATM_CK(cudaMemsetAsync(lv[0].u, 0, (size_t)lv[0].N * nsp * sizeof(T), st));
         ATM_CK(cudaStreamSynchronize(st));
         if (sv.use_graph && st != nullptr && role == ROLE_NORMAL) {
             if (sv.algorithm == ATM_SEQUENTIAL) {
@@ -1248,8 +1338,10 @@ struct RefinedPlan : PlanBase {
         float ms = 0;
         ATM_CK(cudaEventElapsedTime(&ms, ev0, ev1));
         R.time_ms = ms;
-        prof_ms[0] = outer.prof_ms[0]; prof_ms[1] = outer.prof_ms[1];
-        prof_n[0] = outer.prof_n[0]; prof_n[1] = outer.prof_n[1];
+        for (int q = 0; q < 3; ++q) {
+            prof_ms[q] = outer.prof_ms[q];
+            prof_n[q] = outer.prof_n[q];
+        }
         if (res) *res = R;
         return status;
     }

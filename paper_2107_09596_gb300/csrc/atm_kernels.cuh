@@ -256,21 +256,22 @@ __device__ __forceinline__ void warp_line_solve(T (&q)[C], const TriCoef<T> &c, 
     }
 }
 
-// Epilogue of one value at flat index idx of job jb; returns r^2 (0 if no sub).
-template <typename T>
-__device__ __forceinline__ double apply_epilogue(const Job<T> &jb, size_t idx, T phi, int neg)
+// Epilogue of one value at flat index idx of job jb: val = (+-)phi + g + h,
+// stored to out; with a residual (jb.sub), r = val - sub is stored to out2 and
+// r^2 added to acc (FP64).  The caller tests jb.sub once per job, so jobs
+// without a residual issue no FP64 work.
+template <typename T, bool RES>
+__device__ __forceinline__ void apply_epilogue(const Job<T> &jb, size_t idx, T phi, int neg, double &acc)
 {
     T val = neg ? -phi : phi;
     if (jb.g) val = val + jb.g[idx];
     if (jb.h) val = val + jb.h[idx];
-    double acc = 0.0;
-    if (jb.sub) {
+    if (RES) {
         T r = val - jb.sub[idx];
-        acc = (double)r * (double)r;
+        acc = fma((double)r, (double)r, acc);
         if (jb.out2) jb.out2[idx] = r;
     }
     if (jb.out) jb.out[idx] = val;
-    return acc;
 }
 
 // Deterministic CTA sum of one double per thread; thread 0 gets the total.
@@ -316,7 +317,11 @@ __global__ void __launch_bounds__(256) row_sweep_kernel(const __grid_constant__ 
     T q[C];
 
     if constexpr (PR) {
-        T *tile = reinterpret_cast<T *>(smem_raw);       // (nw + 2) rows of nx
+        // (nw + 2) rows of nx values; value x of a row sits at x + 16/S * (x / (128/S))
+        // so that the lanes' 16-byte chunk reads fall in distinct banks
+        T *tile = reinterpret_cast<T *>(smem_raw);
+        constexpr int GRP = 128 / sizeof(T), PADV = 16 / sizeof(T);
+        const int rowpitch = nx + (nx / GRP) * PADV;
         const int row0 = blockIdx.x * nw;
         const int total = (nw + 2) * nx;
         constexpr int V = 16 / sizeof(T);
@@ -334,16 +339,17 @@ __global__ void __launch_bounds__(256) row_sweep_kernel(const __grid_constant__ 
 #pragma unroll
                 for (int e = 0; e < V; ++e) v[e] = react_point(v[e], a.react, a.nsub);
             }
-            store_chunk<V>(tile + idx, v);
+            store_chunk<V>(tile + (size_t)rr * rowpitch + xx + (xx / GRP) * PADV, v);
         }
         __syncthreads();
         constexpr int P = (C % V == 0) ? V : 1;   // piece size
 #pragma unroll
         for (int p = 0; p < C; p += P) {
             T w[P], up[P], dn[P];
-            load_chunk<P>(tile + (size_t)(warp + 1) * nx + x0 + p, w);
-            load_chunk<P>(tile + (size_t)warp * nx + x0 + p, up);
-            load_chunk<P>(tile + (size_t)(warp + 2) * nx + x0 + p, dn);
+            const int xs = x0 + p + ((x0 + p) / GRP) * PADV;
+            load_chunk<P>(tile + (size_t)(warp + 1) * rowpitch + xs, w);
+            load_chunk<P>(tile + (size_t)warp * rowpitch + xs, up);
+            load_chunk<P>(tile + (size_t)(warp + 2) * rowpitch + xs, dn);
 #pragma unroll
             for (int k = 0; k < P; ++k) q[p + k] = fma(a.rx1, up[k] + dn[k], a.rx0 * w[k]);
         }
@@ -372,9 +378,15 @@ __global__ void __launch_bounds__(256) row_sweep_kernel(const __grid_constant__ 
 
     if constexpr (FINAL) {
         double acc = 0.0;
+        if (jb.sub) {
 #pragma unroll
-        for (int k = 0; k < C; ++k)
-            if (k < valid) acc += apply_epilogue(jb, row_off + x0 + k, q[k], a.neg);
+            for (int k = 0; k < C; ++k)
+                if (k < valid) apply_epilogue<T, true>(jb, row_off + x0 + k, q[k], a.neg, acc);
+        } else {
+#pragma unroll
+            for (int k = 0; k < C; ++k)
+                if (k < valid) apply_epilogue<T, false>(jb, row_off + x0 + k, q[k], a.neg, acc);
+        }
         if (a.partials) {
             __shared__ double sh[32];
             __syncthreads();
@@ -394,12 +406,12 @@ __global__ void __launch_bounds__(256) row_sweep_kernel(const __grid_constant__ 
 // each tile edge).  Applies the job epilogue and the residual sum.
 // Grid: x = nx / 32, y = jobs.  Block: 32 * (ny / CY) threads.
 // ---------------------------------------------------------------------------
-template <typename T, int CY, bool PR>
-__global__ void __launch_bounds__(512) col_sweep_kernel(const __grid_constant__ SweepArgs<T> a)
+template <typename T, int CY, int W, bool PR>
+__global__ void __launch_bounds__(W * 32, 1024 / (W * 32)) col_sweep_kernel(const __grid_constant__ SweepArgs<T> a)
 {
-    __shared__ T carry[32][33];
+    __shared__ T carry[W][33];
     __shared__ double sh[32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nx = a.nx, ny = a.ny;
     const Job<T> jb = a.jobs[blockIdx.y];
     const T *mid = a.mid + (size_t)blockIdx.y * nx * ny;
@@ -431,10 +443,14 @@ __global__ void __launch_bounds__(512) col_sweep_kernel(const __grid_constant__ 
     __syncthreads();
     {
         const T m = c.scan[0];  // rho^CY
+        T e[W];
+#pragma unroll
+        for (int j = 0; j < W; ++j) e[j] = carry[j][lane];
         T tot = T(0), pre = T(0);
+#pragma unroll
         for (int j = 0; j < W; ++j) {
             if (j == warp) pre = tot;
-            tot = fma(m, tot, carry[j][lane]);
+            tot = fma(m, tot, e[j]);
         }
         const T cin = fma(c.chunk_pw[warp], tot * c.inv1m, pre);
 #pragma unroll
@@ -450,10 +466,14 @@ __global__ void __launch_bounds__(512) col_sweep_kernel(const __grid_constant__ 
     __syncthreads();
     {
         const T m = c.scan[0];
+        T e[W];
+#pragma unroll
+        for (int j = 0; j < W; ++j) e[j] = carry[j][lane];
         T tot = T(0), pre = T(0);
+#pragma unroll
         for (int j = W - 1; j >= 0; --j) {
             if (j == warp) pre = tot;
-            tot = fma(m, tot, carry[j][lane]);
+            tot = fma(m, tot, e[j]);
         }
         const T din = fma(c.chunk_pw[W - 1 - warp], tot * c.inv1m, pre);
 #pragma unroll
@@ -461,8 +481,13 @@ __global__ void __launch_bounds__(512) col_sweep_kernel(const __grid_constant__ 
     }
 
     double acc = 0.0;
+    if (jb.sub) {
 #pragma unroll
-    for (int k = 0; k < CY; ++k) acc += apply_epilogue(jb, (size_t)(y0 + k) * nx + x, q[k], a.neg);
+        for (int k = 0; k < CY; ++k) apply_epilogue<T, true>(jb, (size_t)(y0 + k) * nx + x, q[k], a.neg, acc);
+    } else {
+#pragma unroll
+        for (int k = 0; k < CY; ++k) apply_epilogue<T, false>(jb, (size_t)(y0 + k) * nx + x, q[k], a.neg, acc);
+    }
     if (a.partials) {
         double t = block_sum(acc, sh);
         if (threadIdx.x == 0) a.partials[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = t;
