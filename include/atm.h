@@ -63,7 +63,9 @@ enum {
  * explicit Euler substeps of size D/s (Lie splitting), then the diffusion: */
 enum {
     ATM_PROP_SPLIT_BE = 0, /* (I - D Lx) y = w, (I - D Ly) u' = y */
-    ATM_PROP_PR_ADI = 1    /* (I - D/2 Lx) u* = (I + D/2 Ly) w, (I - D/2 Ly) u' = (I + D/2 Lx) u* */
+    ATM_PROP_PR_ADI = 1,   /* (I - D/2 Lx) u* = (I + D/2 Ly) w, (I - D/2 Ly) u' = (I + D/2 Lx) u* */
+    ATM_PROP_LEARNED = 2   /* coarse_prop only: level 1 uses the learned Psi_NN (weights from
+                              atm_set_learned_coarse), deeper levels split-BE ADI */
 };
 
 /* Reaction part of the coarse Allen-Cahn propagators (levels >= 1, step D):
@@ -200,6 +202,62 @@ long long atm_last_launch_count(const atm_handle *h);
  * one when a sweep runs in several row/column chunks).
  * *total_ms = summed CUDA-event durations, *launches = sweeps timed. */
 atm_status atm_get_kernel_profile(const atm_handle *h, int which, double *total_ms, long long *launches);
+
+/* ---------------------------------------------------------------------------
+ * Learned coarse propagator.  The paper lets the coarse propagator be any
+ * approximation of m fine steps (Sec. 2.1, last paragraph); this one is
+ *     Psi_NN(u) = u + N(u),
+ * N = five 3x3 convolutions with circular padding (1 -> 32 -> 32 -> 32 -> 32
+ * -> 1 channels), GELU x*Phi(x) after the first four, a bias per layer.
+ * Parameters: a flat FP32 vector of atm_nn_param_count() values, layer by
+ * layer W[c_out][c_in][3][3] (taps row-major) then b[c_out].  Convolutions run
+ * on the tensor cores (BF16 operands, FP32 accumulation); states are FP32
+ * [nstates][ny][nx]; nx * ny must be a multiple of 2048.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    int steps;               /* Adam steps */
+    int batch;               /* pairs per step; step s uses pairs [(s mod (npairs/batch)) * batch, +batch) */
+    float lr, beta1, beta2, eps;
+    int log_every;           /* loss is read back every log_every steps and at the last step */
+    float *h_loss_history;   /* host array for the logged losses (may be NULL) */
+    int history_cap;
+} atm_train_cfg;
+
+typedef struct {
+    int steps;
+    int logged;
+    double final_loss;       /* MSE of the last logged batch */
+    double time_ms;
+} atm_train_result;
+
+int atm_nn_param_count(void);
+
+/* Device workspace for atm_nn_apply (training = 0, nstates states) or for
+ * atm_nn_loss_grad / atm_train_learned_coarse (training = 1, batch nstates). */
+atm_status atm_nn_workspace_size(int nstates, int nx, int ny, int training, size_t *bytes);
+
+/* d_out[s] = Psi_NN(d_in[s]) for s < nstates (device FP32 arrays). */
+atm_status atm_nn_apply(const float *d_params, const float *d_in, float *d_out, int nstates, int nx, int ny,
+                        void *d_ws, size_t bytes, void *cuda_stream);
+
+/* Mean squared error of Psi_NN(d_in) against d_target over nstates states
+ * (to *loss, host) and its gradient with respect to the parameters (d_grad,
+ * device, atm_nn_param_count() values).  Blocks until done. */
+atm_status atm_nn_loss_grad(const float *d_params, const float *d_in, const float *d_target, int nstates, int nx,
+                            int ny, float *d_grad, double *loss, void *d_ws, size_t bytes, void *cuda_stream);
+
+/* Adam on the mean squared error of Psi_NN(in) against target over npairs
+ * (u, Phi^m u) pairs (device FP32 [npairs][ny][nx]).  d_params is updated in
+ * place; d_adam holds the two Adam moments (2 * atm_nn_param_count() values,
+ * zero before the first call).  Blocks until done. */
+atm_status atm_train_learned_coarse(float *d_params, float *d_adam, const float *d_in, const float *d_target,
+                                    int npairs, int nx, int ny, const atm_train_cfg *cfg, atm_train_result *res,
+                                    void *d_ws, size_t bytes, void *cuda_stream);
+
+/* Give a handle created with coarse_prop = ATM_PROP_LEARNED its network
+ * (device FP32 parameters, copied into the handle's workspace).  Required
+ * before atm_solve on such a handle.  Not available in the refined mode. */
+atm_status atm_set_learned_coarse(atm_handle *h, const float *d_params);
 
 /* atm_apply_propagator_noalloc -- the paper has no counterpart to this call;
  * it serves callers that must not allocate device memory.

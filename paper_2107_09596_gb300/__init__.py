@@ -16,7 +16,7 @@ import numpy as np
 from . import build as _build
 
 HEAT1D, HEAT2D, ALLEN_CAHN = 0, 1, 2
-PROP_SPLIT_BE, PROP_PR_ADI = 0, 1
+PROP_SPLIT_BE, PROP_PR_ADI, PROP_LEARNED = 0, 1, 2
 REACT_EXACT, REACT_SUBSTEPS = 0, 1
 SEQUENTIAL, MGRIT, AT_MGRIT = 0, 1, 2
 FP64, FP32, FP32_REFINED = 0, 1, 2
@@ -52,6 +52,18 @@ class SolverDesc(ctypes.Structure):
                 ("profile", ctypes.c_int)]
 
 
+class TrainCfg(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int), ("batch", ctypes.c_int), ("lr", ctypes.c_float),
+                ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float),
+                ("log_every", ctypes.c_int), ("h_loss_history", ctypes.c_void_p),
+                ("history_cap", ctypes.c_int)]
+
+
+class TrainResult(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int), ("logged", ctypes.c_int), ("final_loss", ctypes.c_double),
+                ("time_ms", ctypes.c_double)]
+
+
 class Result(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int),
                 ("initial_residual", ctypes.c_double), ("final_residual", ctypes.c_double),
@@ -63,7 +75,8 @@ EXPORTS = ["atm_workspace_size", "atm_create", "atm_set_initial_condition",
            "atm_get_residual_history", "atm_apply_propagator", "atm_run_stage",
            "atm_level_read", "atm_level_write", "atm_level_points",
            "atm_last_launch_count", "atm_get_kernel_profile", "atm_apply_propagator_noalloc",
-           "atm_last_error", "atm_destroy"]
+           "atm_nn_param_count", "atm_nn_workspace_size", "atm_nn_apply", "atm_nn_loss_grad",
+           "atm_train_learned_coarse", "atm_set_learned_coarse", "atm_last_error", "atm_destroy"]
 
 _lib = None
 
@@ -101,10 +114,18 @@ def load(build_if_missing: bool = True):
     L.atm_last_launch_count.restype = ctypes.c_longlong
     L.atm_get_kernel_profile.argtypes = [vp, i, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_longlong)]
     L.atm_apply_propagator_noalloc.argtypes = [ctypes.POINTER(Problem), ctypes.POINTER(SolverDesc), i, vp, vp, i, vp]
+    L.atm_nn_param_count.restype = i
+    L.atm_nn_workspace_size.argtypes = [i, i, i, i, ctypes.POINTER(ctypes.c_size_t)]
+    L.atm_nn_apply.argtypes = [vp, vp, vp, i, i, i, vp, ctypes.c_size_t, vp]
+    L.atm_nn_loss_grad.argtypes = [vp, vp, vp, i, i, i, vp, ctypes.POINTER(d), vp, ctypes.c_size_t, vp]
+    L.atm_train_learned_coarse.argtypes = [vp, vp, vp, vp, i, i, i, ctypes.POINTER(TrainCfg),
+                                           ctypes.POINTER(TrainResult), vp, ctypes.c_size_t, vp]
+    L.atm_set_learned_coarse.argtypes = [vp, vp]
     L.atm_last_error.restype = ctypes.c_char_p
     L.atm_destroy.argtypes = [vp]
     for name in EXPORTS:
-        if name not in ("atm_level_points", "atm_last_launch_count", "atm_last_error", "atm_destroy"):
+        if name not in ("atm_level_points", "atm_last_launch_count", "atm_last_error", "atm_destroy",
+                        "atm_nn_param_count"):
             getattr(L, name).restype = i
     _lib = L
     return L
@@ -283,5 +304,89 @@ class Solver:
         _check(load().atm_get_kernel_profile(self.handle, which, ctypes.byref(ms), ctypes.byref(n)))
         return ms.value, n.value
 
+    def set_learned_coarse(self, params):
+        """Network weights (torch float32 device tensor) for coarse_prop = PROP_LEARNED."""
+        params = params.to(device=self.device, dtype=self.torch.float32).contiguous()
+        self._enter()
+        _check(load().atm_set_learned_coarse(self.handle, ctypes.c_void_p(params.data_ptr())))
+        self._leave()
+        self._nn_params = params
+
     def level_points(self, level) -> int:
         return load().atm_level_points(self.handle, level)
+
+
+class LearnedCoarse:
+    """The learned coarse propagator Psi_NN(u) = u + N(u) (include/atm.h):
+    inference, loss/gradient and Adam training through the C ABI, on torch
+    float32 device tensors of shape (n, ny, nx)."""
+
+    def __init__(self, device="cuda:0", stream=None):
+        import torch
+        self.torch = torch
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
+        self.nparams = load().atm_nn_param_count()
+        self._ws = {}
+
+    def _workspace(self, n, ny, nx, training):
+        key = (n, ny, nx, training)
+        if key not in self._ws:
+            b = ctypes.c_size_t()
+            _check(load().atm_nn_workspace_size(n, nx, ny, int(training), ctypes.byref(b)))
+            self._ws[key] = self.torch.empty(b.value + 256, dtype=self.torch.uint8, device=self.device)
+        w = self._ws[key]
+        base = (w.data_ptr() + 255) // 256 * 256
+        return ctypes.c_void_p(base), w.numel() - 256
+
+    def _sync_in(self):
+        self.stream.wait_stream(self.torch.cuda.current_stream(self.device))
+
+    def _sync_out(self):
+        self.torch.cuda.current_stream(self.device).wait_stream(self.stream)
+
+    def apply(self, params, u):
+        u = u.to(device=self.device, dtype=self.torch.float32).contiguous()
+        out = self.torch.empty_like(u)
+        n, ny, nx = u.shape
+        ws, nb = self._workspace(n, ny, nx, False)
+        self._sync_in()
+        _check(load().atm_nn_apply(ctypes.c_void_p(params.data_ptr()), ctypes.c_void_p(u.data_ptr()),
+                                   ctypes.c_void_p(out.data_ptr()), n, nx, ny, ws, nb,
+                                   ctypes.c_void_p(self.stream.cuda_stream)))
+        self._sync_out()
+        return out
+
+    def loss_grad(self, params, u, target):
+        u = u.to(device=self.device, dtype=self.torch.float32).contiguous()
+        target = target.to(device=self.device, dtype=self.torch.float32).contiguous()
+        n, ny, nx = u.shape
+        grad = self.torch.empty(self.nparams, dtype=self.torch.float32, device=self.device)
+        loss = ctypes.c_double()
+        ws, nb = self._workspace(n, ny, nx, True)
+        self._sync_in()
+        _check(load().atm_nn_loss_grad(ctypes.c_void_p(params.data_ptr()), ctypes.c_void_p(u.data_ptr()),
+                                       ctypes.c_void_p(target.data_ptr()), n, nx, ny,
+                                       ctypes.c_void_p(grad.data_ptr()), ctypes.byref(loss), ws, nb,
+                                       ctypes.c_void_p(self.stream.cuda_stream)))
+        self._sync_out()
+        return loss.value, grad
+
+    def train(self, params, adam, inputs, targets, steps, batch, lr=1e-3, beta1=0.9, beta2=0.999,
+              eps=1e-8, log_every=50):
+        """Adam steps on (inputs, targets) pairs; params and adam (2 * nparams zeros
+        at the start) are updated in place.  Returns (losses, result dict)."""
+        n, ny, nx = inputs.shape
+        hist = np.zeros(steps // max(log_every, 1) + 2, dtype=np.float32)
+        cfg = TrainCfg(steps, batch, lr, beta1, beta2, eps, log_every,
+                       ctypes.c_void_p(hist.ctypes.data), hist.size)
+        res = TrainResult()
+        ws, nb = self._workspace(batch, ny, nx, True)
+        self._sync_in()
+        _check(load().atm_train_learned_coarse(ctypes.c_void_p(params.data_ptr()), ctypes.c_void_p(adam.data_ptr()),
+                                               ctypes.c_void_p(inputs.data_ptr()), ctypes.c_void_p(targets.data_ptr()),
+                                               n, nx, ny, ctypes.byref(cfg), ctypes.byref(res), ws, nb,
+                                               ctypes.c_void_p(self.stream.cuda_stream)))
+        self._sync_out()
+        return hist[: res.logged].copy(), {"steps": res.steps, "final_loss": res.final_loss,
+                                            "time_ms": res.time_ms}

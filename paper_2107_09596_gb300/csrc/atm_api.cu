@@ -199,6 +199,12 @@ atm_status atm_get_kernel_profile(const atm_handle *h, int which, double *total_
     return ATM_OK;
 }
 
+atm_status atm_set_learned_coarse(atm_handle *h, const float *d_params)
+{
+    if (!h) return atm::fail(ATM_ERR_INVALID_ARG, "null handle");
+    return h->p->set_learned(d_params);
+}
+
 const char *atm_last_error(void)
 {
     return atm::last_error().c_str();

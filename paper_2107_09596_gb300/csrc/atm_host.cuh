@@ -12,42 +12,11 @@
 #include <vector>
 
 #include "../../include/atm.h"
+#include "atm_common.cuh"
 #include "atm_kernels.cuh"
+#include "atm_nn.h"
 
 namespace atm {
-
-// ---------------------------------------------------------------------------
-// Errors
-// ---------------------------------------------------------------------------
-inline std::string &last_error()
-{
-    static thread_local std::string s;
-    return s;
-}
-
-inline atm_status fail(atm_status st, const char *fmt, ...)
-{
-    char buf[512];
-    va_list ap;
-    va_start(ap, fmt);
-    vsnprintf(buf, sizeof(buf), fmt, ap);
-    va_end(ap);
-    last_error() = buf;
-    return st;
-}
-
-#define ATM_CK(call)                                                                        \
-    do {                                                                                    \
-        cudaError_t e_ = (call);                                                            \
-        if (e_ != cudaSuccess)                                                              \
-            return ::atm::fail(ATM_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
-    } while (0)
-
-#define ATM_TRY(expr)                         \
-    do {                                      \
-        atm_status s_ = (expr);               \
-        if (s_ != ATM_OK) return s_;          \
-    } while (0)
 
 // ---------------------------------------------------------------------------
 // Line-operator coefficients (host, FP64), converted to the working type.
@@ -165,6 +134,7 @@ struct LevelOp {
     int rows_per_cta = 8, col_warps = 1, col_chunk = 16;
     size_t row_smem = 0;
     std::vector<double> dir_w;   // 1D: Dirichlet rank-one vector (host copy)
+    bool learned = false;        // the level's propagator is the learned Psi_NN
 };
 
 // Build the level-l propagator of (pb, sv): step D = dt * m_0 * .. * m_{l-1};
@@ -196,8 +166,13 @@ inline LevelOp<T> make_level_op(const atm_problem &pb, const atm_solver &sv, int
         return op;
     }
     a.ny = pb.ny;
+    if (l == 1 && sv.coarse_prop == ATM_PROP_LEARNED) {
+        op.learned = true;
+        return op;
+    }
     const double dx = pb.lx / pb.nx, dy = pb.ly / pb.ny;
-    const int prop = (l == 0) ? sv.fine_prop : sv.coarse_prop;
+    int prop = (l == 0) ? sv.fine_prop : sv.coarse_prop;
+    if (prop == ATM_PROP_LEARNED) prop = ATM_PROP_SPLIT_BE;
     const bool pr = (prop == ATM_PROP_PR_ADI);
     const double f = pr ? 0.5 * D : D;
     const double ax = f / (dx * dx), ay = f / (dy * dy);
@@ -279,6 +254,7 @@ struct PlanBase {
     virtual atm_status level_io(int level, int array, int t0, int count, double *buf, bool write) = 0;
     virtual int level_points(int level) const = 0;
     virtual atm_status zero_guess() = 0;
+    virtual atm_status set_learned(const float *d_params) = 0;
 };
 
 template <typename T>
@@ -291,6 +267,7 @@ struct Level {
     size_t row_smem = 0;
     T *dir_w = nullptr;
     std::vector<double> dir_w_host;
+    bool learned = false;
 };
 
 inline bool pow2_in(int v, int lo, int hi)
@@ -327,6 +304,15 @@ struct Plan : PlanBase {
     Job<T> *d_jobs = nullptr;
     AxpyJob<T> *d_ajobs = nullptr;
     Job<T> *d_dyn = nullptr;             // jobs of atm_apply_propagator
+    // learned propagator (level 1 when coarse_prop = ATM_PROP_LEARNED)
+    bool any_learned = false;
+    bool net_ready = false;
+    bool launch_failed = false;          // a launch helper reported an error
+    float *nn_params = nullptr;
+    void *nn_packed = nullptr;
+    void *nn_scratch = nullptr;
+    int *nn_err = nullptr;
+    nn::Net net;
     Phase passA, rest, seq;
     T *r_full = nullptr;   // ROLE_OUTER: residual of every point
     T *ubase = nullptr;    // ROLE_INNER: FP32 copy of the outer iterate (base of the increments)
@@ -393,8 +379,14 @@ struct Plan : PlanBase {
         if (sv.coarse_reaction != ATM_REACT_EXACT && sv.coarse_reaction != ATM_REACT_SUBSTEPS)
             return fail(ATM_ERR_INVALID_ARG, "unknown coarse_reaction %d", sv.coarse_reaction);
         if (!is1d) {
-            if (sv.fine_prop < 0 || sv.fine_prop > 1 || sv.coarse_prop < 0 || sv.coarse_prop > 1)
+            if (sv.fine_prop < 0 || sv.fine_prop > 1 || sv.coarse_prop < 0 || sv.coarse_prop > 2)
                 return fail(ATM_ERR_INVALID_ARG, "unknown propagator");
+        }
+        if (sv.coarse_prop == ATM_PROP_LEARNED) {
+            if (is1d) return fail(ATM_ERR_INVALID_ARG, "the learned propagator is for the 2D problems");
+            if (sv.algorithm == ATM_SEQUENTIAL) return fail(ATM_ERR_INVALID_ARG, "the learned propagator needs levels >= 2");
+            if (((size_t)pb.nx * pb.ny) % 2048 != 0) return fail(ATM_ERR_INVALID_ARG, "the learned propagator needs nx*ny % 2048 == 0");
+            if (role != ROLE_NORMAL) return fail(ATM_ERR_UNSUPPORTED, "the learned propagator is not available in the refined mode");
         }
         return ATM_OK;
     }
@@ -411,10 +403,16 @@ struct Plan : PlanBase {
         Lv.col_warps = op.col_warps;
         Lv.row_smem = op.row_smem;
         Lv.dir_w_host = op.dir_w;
+        Lv.learned = op.learned;
     }
 
     // ---------------- phase builders ----------------
-    int blocks_per_job(int l) const { return is1d ? 1 : pb.nx / 32; }
+    int blocks_per_job(int l) const
+    {
+        if (is1d) return 1;
+        if (l < (int)lv.size() && lv[l].learned) return pb.nx * pb.ny / nn::kNNTile;
+        return pb.nx / 32;
+    }
 
     void add_sweep(Phase &ph, int l, std::vector<Job<T>> &&js, int neg, bool norm)
     {
@@ -713,10 +711,18 @@ struct Plan : PlanBase {
         stage64 = take<double>((size_t)nsp);
         partials = take<double>((size_t)(npartials_max > 0 ? npartials_max : 1));
         norm_cur = take<double>(1);
+        any_learned = !is1d && L > 1 && sv.coarse_prop == ATM_PROP_LEARNED;
+        if (any_learned) {
+            nn_params = take<float>((size_t)nn::param_count());
+            nn_packed = take<unsigned char>(nn::packed_bytes());
+            const int ch = maxbatch < nn::kInferChunk ? maxbatch : nn::kInferChunk;
+            nn_scratch = take<unsigned char>(nn::infer_scratch_bytes(ch, pb.ny, pb.nx));
+            nn_err = take<int>(1);
+        }
         for (int l = 0; l < L; ++l) {
             if (is1d) lv[l].dir_w = take<T>((size_t)pb.nx);
             setup_level_op(l);
-            if (!lv[l].row || (!is1d && !lv[l].col))
+            if (!lv[l].learned && (!lv[l].row || (!is1d && !lv[l].col)))
                 return fail(ATM_ERR_UNSUPPORTED, "no kernel instantiation for this grid size and precision");
         }
         build_phases();
@@ -752,7 +758,11 @@ struct Plan : PlanBase {
     long long kernels_in(const Phase &ph) const
     {
         long long n = 0;
-        for (const LaunchRec &r : ph) n += (r.type == L_SWEEP && !is1d) ? 2 * sweep_pairs(r.level, r.njobs) : 1;
+        for (const LaunchRec &r : ph) {
+            if (r.type != L_SWEEP || is1d) n += 1;
+            else if (lv[r.level].learned) n += sweep_pairs(r.level, r.njobs);
+            else n += 2 * sweep_pairs(r.level, r.njobs);
+        }
         return n;
     }
 
@@ -763,6 +773,12 @@ struct Plan : PlanBase {
     void launch_sweep(int l, const Job<T> *djobs, int njobs, int neg, double *part, int slot = -1)
     {
         const Level<T> &Lv = lv[l];
+        if (Lv.learned) {
+            const int ch = maxbatch < nn::kInferChunk ? maxbatch : nn::kInferChunk;
+            if (nn::infer_jobs<T>(net, djobs, njobs, neg, part, pb.ny, pb.nx, nn_scratch, ch, nn_err, st) != ATM_OK)
+                launch_failed = true;
+            return;
+        }
         SweepArgs<T> a = Lv.args;
         a.neg = neg;
         a.mid = mid;
@@ -795,6 +811,10 @@ struct Plan : PlanBase {
     int sweep_pairs(int l, int njobs) const
     {
         if (is1d) return 1;
+        if (lv[l].learned) {
+            const int ch = maxbatch < nn::kInferChunk ? maxbatch : nn::kInferChunk;
+            return 5 * ((njobs + ch - 1) / ch);   // counted as kernels / 2 by kernels_in
+        }
         const int cs = (l == 0 && chunk > 0 && chunk < njobs) ? chunk : njobs;
         return (njobs + cs - 1) / cs;
     }
@@ -888,6 +908,7 @@ struct Plan : PlanBase {
     {
         enqueue(ph);
         ATM_CK(cudaGetLastError());
+        if (launch_failed) return fail(ATM_ERR_CUDA, "a launch of the learned propagator failed: %s", last_error().c_str());
         launches += kernels_in(ph);
         return ATM_OK;
     }
@@ -898,6 +919,10 @@ struct Plan : PlanBase {
         ATM_CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
         for (const Phase *p : phs) enqueue(*p);
         cudaError_t e = cudaStreamEndCapture(st, &g);
+        if (launch_failed) {
+            if (g) cudaGraphDestroy(g);
+            return fail(ATM_ERR_CUDA, "a launch of the learned propagator failed during capture");
+        }
         if (e != cudaSuccess) return fail(ATM_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
         e = cudaGraphInstantiate(out, g, 0);
         cudaGraphDestroy(g);
@@ -907,7 +932,14 @@ struct Plan : PlanBase {
 
     atm_status finish_create() override
     {
+        if (any_learned) {
+            nn::carve_packed(nn_packed, &net);
+            net.params = nn_params;
+            ATM_TRY(nn::prepare<T>());
+            ATM_CK(cudaMemsetAsync(nn_err, 0, sizeof(int), st));
+        }
         for (int l = 0; l < L; ++l) {
+            if (lv[l].learned) continue;
             if (lv[l].row_smem > 48 * 1024)
                 ATM_CK(cudaFuncSetAttribute((const void *)lv[l].row, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)lv[l].row_smem));
@@ -959,6 +991,8 @@ struct Plan : PlanBase {
         std::memset(&R, 0, sizeof(R));
         launches = 0;
         hist.clear();
+        if (any_learned && !net_ready)
+            return fail(ATM_ERR_INVALID_ARG, "the learned coarse propagator has no weights (atm_set_learned_coarse)");
         ATM_CK(cudaEventRecord(ev0, st));
         atm_status status = ATM_OK;
         if (sv.algorithm == ATM_SEQUENTIAL) {
@@ -1008,6 +1042,11 @@ struct Plan : PlanBase {
         ATM_CK(cudaEventRecord(ev1, st));
         ATM_CK(cudaEventSynchronize(ev1));
         if (nprof && sv.algorithm == ATM_SEQUENTIAL) collect_profile();
+        if (any_learned) {
+            int e = 0;
+            ATM_CK(cudaMemcpy(&e, nn_err, sizeof(int), cudaMemcpyDeviceToHost));
+            if (e) status = fail(ATM_ERR_TIMEOUT, "a tensor-core wait of the learned propagator timed out");
+        }
         float ms = 0;
         ATM_CK(cudaEventElapsedTime(&ms, ev0, ev1));
         R.time_ms = ms;
@@ -1167,6 +1206,17 @@ struct Plan : PlanBase {
     atm_status zero_guess() override
     {
         ATM_CK(cudaMemsetAsync(st_ptr(lv[0].u, 1), 0, (size_t)(lv[0].N - 1) * nsp * sizeof(T), st));
+        return ATM_OK;
+    }
+
+    atm_status set_learned(const float *d_params) override
+    {
+        if (!any_learned) return fail(ATM_ERR_INVALID_ARG, "the handle was not created with coarse_prop = ATM_PROP_LEARNED");
+        if (!d_params) return fail(ATM_ERR_INVALID_ARG, "null parameters");
+        ATM_CK(cudaMemcpyAsync(nn_params, d_params, (size_t)nn::param_count() * sizeof(float), cudaMemcpyDeviceToDevice, st));
+        ATM_TRY(nn::pack(nn_params, &net, st));
+        ATM_CK(cudaStreamSynchronize(st));
+        net_ready = true;
         return ATM_OK;
     }
 };
@@ -1349,6 +1399,10 @@ struct RefinedPlan : PlanBase {
     atm_status set_state(int t0, int count, const double *src) override { return outer.set_state(t0, count, src); }
     atm_status get_state(int t0, int count, double *dst) override { return outer.get_state(t0, count, dst); }
     atm_status zero_guess() override { return outer.zero_guess(); }
+    atm_status set_learned(const float *) override
+    {
+        return fail(ATM_ERR_UNSUPPORTED, "the learned propagator is not available in the refined mode");
+    }
     atm_status apply_prop(int level, const double *in, double *o, int n) override
     {
         return inner.apply_prop(level, in, o, n);

@@ -1,0 +1,139 @@
+"""The learned coarse propagator on the GPU against its FP64 oracle
+(oracle/nn.py).  The GPU rounds every tensor-core operand to bfloat16 and
+accumulates in FP32; the comparisons below feed the oracle the same
+bfloat16-rounded operands (layer inputs, stored activations, weights, and the
+data-gradient inputs) so that the remaining difference is FP32 accumulation
+order: relative L2 <= 1e-3 for the network output increment and <= 2e-3 for
+the gradients (summed over 8192 pixels with FP32 atomics)."""
+import numpy as np
+import pytest
+
+import atm_inputs as I
+import oracle
+from oracle import nn as onn
+import paper_2107_09596_gb300 as atm
+from helpers import pair, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+bf = onn.bf16_round
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch
+    assert torch.cuda.is_available()
+    atm._build.build()
+    atm.load()
+    return torch
+
+
+def flat(params):
+    return np.concatenate([np.concatenate([w.ravel(), b.ravel()]) for (w, b) in params])
+
+
+def make_params(seed=0):
+    ps = onn.init_params(seed)
+    rng = np.random.default_rng(seed + 100)
+    return [(w * 2.0, rng.standard_normal(b.shape) * 0.05) for (w, b) in ps]
+
+
+def emu_forward(params, u):
+    h = bf(u)[:, None]
+    hs, zs = [h], []
+    for li, (w, b) in enumerate(params):
+        z = onn.conv3x3(h, bf(w), b)
+        zs.append(z)
+        if li < len(params) - 1:
+            h = bf(onn.gelu(z))
+            hs.append(h)
+    return u + z[:, 0], hs, zs
+
+
+def emu_grads(params, u, target):
+    out, hs, zs = emu_forward(params, u)
+    n = out.size
+    dz = (2.0 / n) * (out - target)[:, None]
+    grads = [None] * len(params)
+    for li in range(len(params) - 1, -1, -1):
+        w, b = params[li]
+        x = u[:, None] if li == 0 else hs[li]
+        _, dw, db = onn.conv3x3_backward(x, bf(w), dz)
+        grads[li] = (dw, db)
+        if li > 0:
+            dx, _, _ = onn.conv3x3_backward(x, bf(w), bf(dz))
+            dz = dx * onn.gelu_grad(zs[li - 1])
+    return grads
+
+
+def test_nn_forward_matches_oracle(torch):
+    params = make_params(0)
+    u = I.uniform_field((2, 64, 64), 5, -1.0, 1.0)
+    net = atm.LearnedCoarse()
+    p = torch.as_tensor(flat(params), dtype=torch.float32, device="cuda:0")
+    got = net.apply(p, torch.as_tensor(u, dtype=torch.float32)).cpu().numpy().astype(np.float64)
+    want, _, _ = emu_forward(params, u)
+    u32 = u.astype(np.float32).astype(np.float64)
+    assert rel_l2(got - u32, want - u) <= 1e-3, rel_l2(got - u32, want - u)
+    # and, more loosely, against the exact FP64 network (bfloat16 operands cost ~1e-2)
+    exact, _ = onn.forward(params, u)
+    assert rel_l2(got - u32, exact - u) <= 3e-2
+
+
+def test_nn_gradients_match_oracle(torch):
+    params = make_params(1)
+    u = I.uniform_field((2, 64, 64), 6, -1.0, 1.0)
+    target = u + 0.3 * I.uniform_field((2, 64, 64), 7, -1.0, 1.0)
+    net = atm.LearnedCoarse()
+    p = torch.as_tensor(flat(params), dtype=torch.float32, device="cuda:0")
+    loss, g = net.loss_grad(p, torch.as_tensor(u, dtype=torch.float32), torch.as_tensor(target, dtype=torch.float32))
+    g = g.cpu().numpy().astype(np.float64)
+    want = flat(emu_grads(params, u, target))
+    out, _, _ = emu_forward(params, u)
+    assert abs(loss - np.mean((out - target) ** 2)) <= 1e-3 * loss
+    off = 0
+    for (w, b) in params:
+        nw, nb = w.size, b.size
+        assert rel_l2(g[off:off + nw], want[off:off + nw]) <= 2e-3, (off, rel_l2(g[off:off + nw], want[off:off + nw]))
+        assert rel_l2(g[off + nw:off + nw + nb], want[off + nw:off + nw + nb]) <= 2e-3
+        off += nw + nb
+
+
+def test_training_lowers_the_loss_on_propagator_pairs(torch):
+    # pairs (u, Phi^16 u) of the Allen-Cahn fine propagator on 64^2
+    oc = oracle.make_cfg(oracle.ALLEN_CAHN, 64, 64, dt=1e-4, nt=17, eps=0.02, m=(16,), k=2)
+    u = I.uniform_field((32, 64, 64), 8, -1.0, 1.0)
+    y = u.copy()
+    for _ in range(16):
+        y = oracle.apply_prop(oc, 0, y)
+    net = atm.LearnedCoarse()
+    params = torch.as_tensor(flat(onn.init_params(2)), dtype=torch.float32, device="cuda:0")
+    adam = torch.zeros(2 * net.nparams, dtype=torch.float32, device="cuda:0")
+    ut = torch.as_tensor(u, dtype=torch.float32, device="cuda:0")
+    yt = torch.as_tensor(y, dtype=torch.float32, device="cuda:0")
+    l0, _ = net.loss_grad(params, ut[:8], yt[:8])
+    hist, res = net.train(params, adam, ut, yt, steps=300, batch=8, lr=2e-3, log_every=50)
+    l1, _ = net.loss_grad(params, ut[:8], yt[:8])
+    assert np.all(np.isfinite(hist)) and res["steps"] == 300
+    assert l1 < 0.5 * l0, (l0, l1, hist)
+
+
+def test_solve_with_learned_coarse_reaches_the_sequential_solution(torch):
+    """The fixed point does not depend on the coarse propagator: two-level
+    AT-MGRIT with an (untrained) Psi_NN on the coarse grid converges to the
+    fine sequential solution, exact after N_T = 16 cycles at most (C-points
+    0..j are exact after j cycles whatever the coarse operator, Sec. 2.1).
+    The linear heat problem keeps the untrained network's poor corrections
+    from leaving the range where the explicit Allen-Cahn reaction is stable."""
+    oc, gp, gs = pair(kind="heat2d", nx=64, ny=64, dt=2e-4, nt=257, m=(16,), k=4, nu=1, tol=1e-10,
+                      max_iter=40, coarse_prop=atm.PROP_LEARNED)
+    s = atm.Solver(gp, gs)
+    with pytest.raises(atm.AtmError, match="no weights"):
+        s.solve()
+    s.set_learned_coarse(torch.as_tensor(flat(onn.init_params(3)), dtype=torch.float32))
+    u0 = I.uniform_field((64, 64), 9)
+    s.set_initial_condition(torch.as_tensor(u0, device="cuda:0"))
+    r = s.solve()
+    assert r["converged"] and r["iterations"] <= 16, r
+    seq = oracle.sequential(oc, u0)
+    assert rel_l2(s.solution().cpu().numpy(), seq) <= 1e-9
