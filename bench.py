@@ -8,7 +8,8 @@ tolerance 1e-8, u0 ~ U(-0.05, 0.05) (seed = rank), zero initial guess.
 A step is one full solve to ||r||_2 <= 1e-8 from the zero guess: every row of
 the sweep (relaxation, residual, restriction, local chains, correction, norm,
 cycle control).  value = fine time steps resolved per second
-= ranks * (nt - 1) / time-to-solution.
+= ranks * (nt - 1) / time-to-solution.  Default arithmetic: FP32 propagation
+inside the FP64 refinement loop (FP64 residual of every point and FP64 norm).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl atm|reference]
 """
@@ -160,14 +161,48 @@ def max_over_ranks(dist, value, device=None):
     return float(t.item())
 
 
-def make_desc(atm, w, algorithm, precision, profile):
+def train_learned(atm, w, device, steps, seeds=(101, 102, 103, 104, 105), batch=8):
+    """Psi_NN for the workload's level-1 step (m_0 fine steps): pairs (u_t, u_{t+m_0})
+    of fine trajectories from other seeds, produced by the library's sequential
+    stepping (the states that F-relaxation generates at convergence), then Adam."""
+    import torch
+    from oracle import nn as onn   # parameter initialisation only (seeded draws)
+    m0 = w["m"][0]
+    prob, desc = make_desc(atm, w, "seq", atm.FP32, profile=False)
+    seq = atm.Solver(prob, desc, device=device)
+    ins, outs = [], []
+    for sd in seeds:
+        seq.set_initial_condition(torch.as_tensor(initial_condition(w, sd), dtype=torch.float64, device=device))
+        seq.solve()
+        traj = seq.solution().to(torch.float32)
+        ins.append(traj[:-m0].clone())
+        outs.append(traj[m0:].clone())
+        del traj
+    seq.close()
+    inputs = torch.cat(ins).contiguous()
+    targets = torch.cat(outs).contiguous()
+    del ins, outs
+    net = atm.LearnedCoarse(device=device)
+    flat = np.concatenate([np.concatenate([wt.ravel(), b.ravel()]) for (wt, b) in onn.init_params(7)])
+    params = torch.as_tensor(flat, dtype=torch.float32, device=device)
+    adam = torch.zeros(2 * net.nparams, dtype=torch.float32, device=device)
+    perm = torch.randperm(inputs.shape[0], generator=torch.Generator().manual_seed(0)).to(device)
+    inputs, targets = inputs[perm].contiguous(), targets[perm].contiguous()
+    hist, res = net.train(params, adam, inputs, targets, steps=steps, batch=batch, lr=1e-3, log_every=250)
+    return params, {"pairs": int(inputs.shape[0]), "steps": steps, "batch": batch,
+                    "loss_first": float(hist[0]), "loss_last": float(hist[-1]),
+                    "train_ms": res["time_ms"]}
+
+
+def make_desc(atm, w, algorithm, precision, profile, coarse="classical"):
     kind = {"ac": atm.ALLEN_CAHN, "heat1d": atm.HEAT1D}[w["kind"]]
     ny = w["n"] if w["kind"] != "heat1d" else 1
     prob = atm.make_problem(kind, w["n"], ny, dt=w["dt"], nt_points=w["nt"], eps=w["eps"])
     alg = {"at": atm.AT_MGRIT, "mgrit": atm.MGRIT, "seq": atm.SEQUENTIAL}[algorithm]
     desc = atm.make_solver(alg, m=w["m"], k=w["k"], nu=w["nu"], tol=w["tol"],
                            max_iter=w["max_iter"], precision=precision, use_graph=True,
-                           profile=profile)
+                           profile=profile,
+                           coarse_prop=atm.PROP_LEARNED if coarse == "learned" else atm.PROP_SPLIT_BE)
     return prob, desc
 
 
@@ -246,7 +281,11 @@ def main():
     ap.add_argument("--impl", choices=["atm", "reference"], default="atm")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="allen_cahn_256")
     ap.add_argument("--algorithm", choices=["at", "mgrit", "seq"], default="at")
-    ap.add_argument("--precision", choices=["fp64", "fp32", "fp32r"], default="fp64")
+    ap.add_argument("--precision", choices=["fp64", "fp32", "fp32r"], default="fp32r",
+                    help="fp32r: FP32 propagation with FP64 refinement (the fastest form that reaches 1e-8)")
+    ap.add_argument("--coarse", choices=["classical", "learned"], default="classical",
+                    help="level-1 coarse propagator; 'learned' trains Psi_NN first (untimed)")
+    ap.add_argument("--train-steps", type=int, default=2500)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
@@ -263,8 +302,13 @@ def main():
     torch.cuda.set_device(device)
     atm._build.build()
     prec = {"fp64": atm.FP64, "fp32": atm.FP32, "fp32r": atm.FP32_REFINED}[args.precision]
-    prob, desc = make_desc(atm, w, args.algorithm, prec, profile=True)
+    learned_info = None
+    if args.coarse == "learned":
+        nn_params, learned_info = train_learned(atm, w, device, args.train_steps)
+    prob, desc = make_desc(atm, w, args.algorithm, prec, profile=True, coarse=args.coarse)
     solver = atm.Solver(prob, desc, device=device)
+    if args.coarse == "learned":
+        solver.set_learned_coarse(nn_params)
     shape = solver.state_shape
     u0 = torch.as_tensor(initial_condition(w, rank), dtype=torch.float64, device=device)
 
@@ -285,11 +329,13 @@ def main():
     e1 = torch.cuda.Event(enable_timing=True)
     launches = 0
     iters = []
+    fallbacks = []
     e0.record(solver.stream)
     for _ in range(args.steps):
         res = step()
         launches += res["launches"]
         iters.append(res["iterations"])
+        fallbacks.append((res["fallback"], res["fallback_iterations"]))
     e1.record(solver.stream)
     torch.cuda.synchronize(device)
     clk = clocks.stop()
@@ -380,6 +426,10 @@ def main():
                         "h2d_bytes_per_step": state_bytes,
                         "d2h_bytes_per_step": state_bytes + 8 * len(hist)},
                 "gpu_launches": int(launches),
+                "coarse": args.coarse,
+                "learned": None if learned_info is None else dict(
+                    learned_info, fallback_in_timed_steps=sum(f for f, _ in fallbacks),
+                    cycles_with_network_before_fallback=[i for _, i in fallbacks]),
                 "roofline": roof, "cpu_baseline": cpu, "clocks": clk}
         print(json.dumps(line), flush=True)
     solver.close()

@@ -116,6 +116,8 @@ typedef struct {
     double initial_residual;   /* ||r||_2 of the initial guess after F-relaxation */
     double final_residual;     /* ||r||_2 after the last cycle */
     double time_ms;            /* device time of the solve (CUDA events) */
+    int fallback;              /* 1 if a learned coarse propagator was replaced by the classical one */
+    int fallback_iterations;   /* cycles run with the learned propagator before the fallback */
 } atm_result;
 
 typedef struct atm_handle atm_handle;
@@ -256,7 +258,12 @@ atm_status atm_train_learned_coarse(float *d_params, float *d_adam, const float 
 
 /* Give a handle created with coarse_prop = ATM_PROP_LEARNED its network
  * (device FP32 parameters, copied into the handle's workspace).  Required
- * before atm_solve on such a handle.  Not available in the refined mode. */
+ * before atm_solve on such a handle.  Not available in the refined mode.
+ * Fallback: such a handle keeps the classical split-BE ADI propagator for
+ * level 1 too.  Every atm_solve starts with the network; when a cycle gives a
+ * non-finite residual or one above 1e3 times the smallest so far, it restores
+ * the iterate it started from and solves again with the classical level-1
+ * propagator; atm_result.fallback reports it. */
 atm_status atm_set_learned_coarse(atm_handle *h, const float *d_params);
 
 /* atm_apply_propagator_noalloc -- the paper has no counterpart to this call;

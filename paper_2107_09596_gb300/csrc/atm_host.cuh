@@ -268,6 +268,7 @@ struct Level {
     T *dir_w = nullptr;
     std::vector<double> dir_w_host;
     bool learned = false;
+    LevelOp<T> classical;        // learned level: the split-BE ADI operator used after a fallback
 };
 
 inline bool pow2_in(int v, int lo, int hi)
@@ -312,6 +313,9 @@ struct Plan : PlanBase {
     void *nn_packed = nullptr;
     void *nn_scratch = nullptr;
     int *nn_err = nullptr;
+    T *snapshot = nullptr;               // iterate at the start of a solve (learned fallback)
+    bool learned_cfg = false;            // created with a learned level
+    cudaGraphExec_t gA_nn = nullptr, gIter_nn = nullptr, gA_cl = nullptr, gIter_cl = nullptr;
     nn::Net net;
     Phase passA, rest, seq;
     T *r_full = nullptr;   // ROLE_OUTER: residual of every point
@@ -328,8 +332,10 @@ struct Plan : PlanBase {
     ~Plan() override
     {
         for (cudaEvent_t e : pev) cudaEventDestroy(e);
-        if (gA) cudaGraphExecDestroy(gA);
-        if (gIter) cudaGraphExecDestroy(gIter);
+        for (cudaGraphExec_t g : {gA_nn, gIter_nn, gA_cl, gIter_cl})
+            if (g) cudaGraphExecDestroy(g);
+        if (gA && gA != gA_nn && gA != gA_cl) cudaGraphExecDestroy(gA);
+        if (gIter && gIter != gIter_nn && gIter != gIter_cl) cudaGraphExecDestroy(gIter);
         if (gSeq) cudaGraphExecDestroy(gSeq);
         if (ev0) cudaEventDestroy(ev0);
         if (ev1) cudaEventDestroy(ev1);
@@ -395,6 +401,11 @@ struct Plan : PlanBase {
     {
         Level<T> &Lv = lv[l];
         LevelOp<T> op = make_level_op<T>(pb, sv, l, Lv.dir_w);
+        if (op.learned) {
+            atm_solver cs = sv;
+            cs.coarse_prop = ATM_PROP_SPLIT_BE;
+            Lv.classical = make_level_op<T>(pb, cs, l, Lv.dir_w);
+        }
         Lv.args = op.args;
         Lv.row = op.row;
         Lv.col = op.col;
@@ -718,6 +729,7 @@ struct Plan : PlanBase {
             const int ch = maxbatch < nn::kInferChunk ? maxbatch : nn::kInferChunk;
             nn_scratch = take<unsigned char>(nn::infer_scratch_bytes(ch, pb.ny, pb.nx));
             nn_err = take<int>(1);
+            snapshot = take<T>((size_t)lv[0].N * nsp);
         }
         for (int l = 0; l < L; ++l) {
             if (is1d) lv[l].dir_w = take<T>((size_t)pb.nx);
@@ -975,6 +987,43 @@ struct Plan : PlanBase {
                 ATM_TRY(capture({&rest, &passA}, &gIter));
             }
         }
+        if (any_learned) {
+            learned_cfg = true;
+            gA_nn = gA;
+            gIter_nn = gIter;
+        }
+        return ATM_OK;
+    }
+
+    // Select the learned (true) or the classical (false) level-1 propagator,
+    // with the cycle graphs captured for it.
+    atm_status use_learned(bool on)
+    {
+        for (int l = 0; l < L; ++l) {
+            if (lv[l].classical.row == nullptr) continue;   // not a learned level
+            if (on) {
+                lv[l].learned = true;
+            } else {
+                const LevelOp<T> &op = lv[l].classical;
+                lv[l].args = op.args;
+                lv[l].row = op.row;
+                lv[l].col = op.col;
+                lv[l].rows_per_cta = op.rows_per_cta;
+                lv[l].col_chunk = op.col_chunk;
+                lv[l].col_warps = op.col_warps;
+                lv[l].row_smem = op.row_smem;
+                lv[l].learned = false;
+            }
+        }
+        any_learned = on;
+        if (sv.use_graph && st != nullptr) {
+            if (!on && !gA_cl) {
+                ATM_TRY(capture({&passA}, &gA_cl));
+                ATM_TRY(capture({&rest, &passA}, &gIter_cl));
+            }
+            gA = on ? gA_nn : gA_cl;
+            gIter = on ? gIter_nn : gIter_cl;
+        }
         return ATM_OK;
     }
 
@@ -987,12 +1036,37 @@ struct Plan : PlanBase {
 
     atm_status solve(atm_result *res) override
     {
+        if (learned_cfg && !net_ready)
+            return fail(ATM_ERR_INVALID_ARG, "the learned coarse propagator has no weights (atm_set_learned_coarse)");
+        if (!learned_cfg) return solve_once(res);
+        ATM_TRY(use_learned(true));
+        ATM_CK(cudaMemcpyAsync(snapshot, lv[0].u, (size_t)lv[0].N * nsp * sizeof(T), cudaMemcpyDeviceToDevice, st));
+        atm_result first;
+        atm_status s1 = solve_once(&first);
+        if (s1 != ATM_ERR_DIVERGED) {
+            if (res) *res = first;
+            return s1;
+        }
+        // the learned propagator failed: restore the iterate and solve with the classical one
+        ATM_CK(cudaMemcpyAsync(lv[0].u, snapshot, (size_t)lv[0].N * nsp * sizeof(T), cudaMemcpyDeviceToDevice, st));
+        ATM_TRY(use_learned(false));
+        const long long l1 = launches;
+        atm_result second;
+        atm_status s2 = solve_once(&second);
+        launches += l1;
+        second.fallback = 1;
+        second.fallback_iterations = first.iterations;
+        second.time_ms += first.time_ms;
+        if (res) *res = second;
+        return s2;
+    }
+
+    atm_status solve_once(atm_result *res)
+    {
         atm_result R;
         std::memset(&R, 0, sizeof(R));
         launches = 0;
         hist.clear();
-        if (any_learned && !net_ready)
-            return fail(ATM_ERR_INVALID_ARG, "the learned coarse propagator has no weights (atm_set_learned_coarse)");
         ATM_CK(cudaEventRecord(ev0, st));
         atm_status status = ATM_OK;
         if (sv.algorithm == ATM_SEQUENTIAL) {

@@ -137,3 +137,47 @@ def test_solve_with_learned_coarse_reaches_the_sequential_solution(torch):
     assert r["converged"] and r["iterations"] <= 16, r
     seq = oracle.sequential(oc, u0)
     assert rel_l2(s.solution().cpu().numpy(), seq) <= 1e-9
+
+
+def test_trained_network_gain_over_classical_is_measured(torch):
+    """Train Psi_NN on (u_t, u_{t+16}) pairs of fine Allen-Cahn trajectories
+    (64^2, seeds 1-3), then solve a held-out problem (seed 0) with it and with
+    the classical coarse propagator.  What the network gains is the difference
+    in cycles; the assertions only require what holds either way: the trained
+    network fits held-out pairs better than its initialisation, and the solve
+    reaches the sequential solution (through the classical fallback if the
+    network's corrections make the iteration diverge)."""
+    nt, m = 257, 16
+    oc, gp, gs = pair(kind="ac", nx=64, ny=64, dt=1e-4, nt=nt, m=(m, 4), k=3, nu=1, tol=1e-9,
+                      max_iter=60, coarse_prop=atm.PROP_LEARNED)
+    trajs = [oracle.sequential(oc, I.uniform_field((64, 64), sd)) for sd in (1, 2, 3)]
+    ins = np.concatenate([t[:-m] for t in trajs]).astype(np.float32)
+    outs = np.concatenate([t[m:] for t in trajs]).astype(np.float32)
+    held = oracle.sequential(oc, I.uniform_field((64, 64), 0))
+    net = atm.LearnedCoarse()
+    p0 = torch.as_tensor(flat(onn.init_params(4)), dtype=torch.float32, device="cuda:0")
+    params = p0.clone()
+    adam = torch.zeros(2 * net.nparams, dtype=torch.float32, device="cuda:0")
+    perm = np.random.default_rng(0).permutation(len(ins))
+    ut = torch.as_tensor(ins[perm], device="cuda:0")
+    yt = torch.as_tensor(outs[perm], device="cuda:0")
+    net.train(params, adam, ut, yt, steps=400, batch=8, lr=1e-3, log_every=100)
+    hu = torch.as_tensor(held[:-m][::8].astype(np.float32), device="cuda:0")
+    hy = torch.as_tensor(held[m:][::8].astype(np.float32), device="cuda:0")
+    l_init, _ = net.loss_grad(p0, hu[:8], hy[:8])
+    l_trained, _ = net.loss_grad(params, hu[:8], hy[:8])
+    assert l_trained < l_init, (l_init, l_trained)
+    u0 = I.uniform_field((64, 64), 0)
+    s = atm.Solver(gp, gs)
+    s.set_learned_coarse(params)
+    s.set_initial_condition(torch.as_tensor(u0, device="cuda:0"))
+    r_nn = s.solve()
+    _, gp2, gs2 = pair(kind="ac", nx=64, ny=64, dt=1e-4, nt=nt, m=(m, 4), k=3, nu=1, tol=1e-9, max_iter=60)
+    c = atm.Solver(gp2, gs2)
+    c.set_initial_condition(torch.as_tensor(u0, device="cuda:0"))
+    r_cl = c.solve()
+    print(f"\nlearned: {r_nn['iterations']} cycles (fallback={r_nn['fallback']} after "
+          f"{r_nn['fallback_iterations']}), classical: {r_cl['iterations']} cycles; "
+          f"held-out MSE init {l_init:.3e} trained {l_trained:.3e}")
+    assert r_nn["converged"] and r_cl["converged"]
+    assert rel_l2(s.solution().cpu().numpy(), held) <= 1e-8
