@@ -106,7 +106,11 @@ typedef struct {
     double tol;                       /* stop when the residual 2-norm <= tol */
     int max_iter;                     /* maximum V-cycles */
     int precision;                    /* ATM_FP64 | ATM_FP32 | ATM_FP32_REFINED */
-    int use_graph;                    /* 1: replay the cycle as a captured CUDA graph */
+    int use_graph;                    /* 0: direct launches; 1: each cycle is a captured CUDA graph
+                                         (the host reads the residual after every cycle); 2: the
+                                         whole solve is one graph launch whose conditional WHILE
+                                         node repeats the cycle until a kernel finds the residual
+                                         below tol (no host round trip until the end) */
     int profile;                      /* 1: time the level-0 relaxation sweeps with CUDA events */
 } atm_solver;
 
@@ -204,6 +208,18 @@ long long atm_last_launch_count(const atm_handle *h);
  * one when a sweep runs in several row/column chunks).
  * *total_ms = summed CUDA-event durations, *launches = sweeps timed. */
 atm_status atm_get_kernel_profile(const atm_handle *h, int which, double *total_ms, long long *launches);
+
+/* Solve several independent problems with one CUDA graph launch on
+ * `cuda_stream`: the graph holds, for every handle, its first relaxation pass
+ * and a conditional WHILE node that repeats its cycle until a kernel finds its
+ * residual below its tol (or max_iter, divergence); the problems' loops are
+ * independent branches, so the GPU runs them concurrently and each stops on
+ * its own.  Handles may differ in problem, grid, levels, m, k and precision
+ * (FP64, FP32); not supported: sequential stepping, the refined mode and the
+ * learned propagator (ATM_ERR_UNSUPPORTED).  Each handle's iterate, residual
+ * history and outs[i] are filled as by atm_solve; the return value is the
+ * first non-OK status of the problems.  Blocks until all are done. */
+atm_status atm_batch_solve(atm_handle *const *hs, int n, void *cuda_stream, atm_result *outs);
 
 /* ---------------------------------------------------------------------------
  * Learned coarse propagator.  The paper lets the coarse propagator be any

@@ -77,7 +77,8 @@ EXPORTS = ["atm_workspace_size", "atm_create", "atm_set_initial_condition",
            "atm_level_read", "atm_level_write", "atm_level_points",
            "atm_last_launch_count", "atm_get_kernel_profile", "atm_apply_propagator_noalloc",
            "atm_nn_param_count", "atm_nn_workspace_size", "atm_nn_apply", "atm_nn_loss_grad",
-           "atm_train_learned_coarse", "atm_set_learned_coarse", "atm_last_error", "atm_destroy"]
+           "atm_train_learned_coarse", "atm_set_learned_coarse", "atm_batch_solve", "atm_last_error",
+           "atm_destroy"]
 
 _lib = None
 
@@ -122,6 +123,7 @@ def load(build_if_missing: bool = True):
     L.atm_train_learned_coarse.argtypes = [vp, vp, vp, vp, i, i, i, ctypes.POINTER(TrainCfg),
                                            ctypes.POINTER(TrainResult), vp, ctypes.c_size_t, vp]
     L.atm_set_learned_coarse.argtypes = [vp, vp]
+    L.atm_batch_solve.argtypes = [ctypes.POINTER(vp), i, vp, ctypes.POINTER(Result)]
     L.atm_last_error.restype = ctypes.c_char_p
     L.atm_destroy.argtypes = [vp]
     for name in EXPORTS:
@@ -316,6 +318,27 @@ class Solver:
 
     def level_points(self, level) -> int:
         return load().atm_level_points(self.handle, level)
+
+
+def batch_solve(solvers, allow_not_converged=True):
+    """Solve several Solver objects with one graph launch (atm_batch_solve).
+    Returns one result dict per solver."""
+    import torch
+    n = len(solvers)
+    hs = (ctypes.c_void_p * n)(*[s.handle.value for s in solvers])
+    outs = (Result * n)()
+    cur = torch.cuda.current_stream(solvers[0].device)
+    for s in solvers:
+        cur.wait_stream(s.stream)
+    st = load().atm_batch_solve(hs, n, ctypes.c_void_p(cur.cuda_stream), outs)
+    _check(st, (0, 4) if allow_not_converged else (0,))
+    res = []
+    for s, r in zip(solvers, outs):
+        s.stream.wait_stream(cur)
+        res.append({"iterations": r.iterations, "converged": bool(r.converged),
+                    "initial_residual": r.initial_residual, "final_residual": r.final_residual,
+                    "time_ms": r.time_ms})
+    return res
 
 
 class LearnedCoarse:

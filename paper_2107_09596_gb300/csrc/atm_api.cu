@@ -205,6 +205,48 @@ atm_status atm_set_learned_coarse(atm_handle *h, const float *d_params)
     return h->p->set_learned(d_params);
 }
 
+atm_status atm_batch_solve(atm_handle *const *hs, int n, void *cuda_stream, atm_result *outs)
+{
+    atm::last_error().clear();
+    if (!hs || n < 1) return atm::fail(ATM_ERR_INVALID_ARG, "empty batch");
+    for (int i = 0; i < n; ++i)
+        if (!hs[i]) return atm::fail(ATM_ERR_INVALID_ARG, "null handle %d", i);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
+    cudaGraph_t g = nullptr;
+    ATM_CK(cudaGraphCreate(&g, 0));
+    atm_status s = ATM_OK;
+    for (int i = 0; i < n && s == ATM_OK; ++i) s = hs[i]->p->add_loop(g);
+    cudaGraphExec_t ge = nullptr;
+    if (s == ATM_OK) {
+        cudaError_t e = cudaGraphInstantiate(&ge, g, 0);
+        if (e != cudaSuccess) s = atm::fail(ATM_ERR_CUDA, "instantiating the batch graph failed: %s", cudaGetErrorString(e));
+    }
+    cudaGraphDestroy(g);
+    if (s != ATM_OK) return s;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, st);
+    cudaError_t e = cudaGraphLaunch(ge, st);
+    cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaGraphExecDestroy(ge);
+    if (e != cudaSuccess) return atm::fail(ATM_ERR_CUDA, "batch graph launch failed: %s", cudaGetErrorString(e));
+    atm_status first = ATM_OK;
+    for (int i = 0; i < n; ++i) {
+        atm_result r;
+        atm_status si = hs[i]->p->loop_result(&r);
+        r.time_ms = ms;
+        if (outs) outs[i] = r;
+        if (first == ATM_OK && si != ATM_OK) first = si;
+    }
+    return first;
+}
+
 const char *atm_last_error(void)
 {
     return atm::last_error().c_str();

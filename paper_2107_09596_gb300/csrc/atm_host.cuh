@@ -255,6 +255,10 @@ struct PlanBase {
     virtual int level_points(int level) const = 0;
     virtual atm_status zero_guess() = 0;
     virtual atm_status set_learned(const float *d_params) = 0;
+    // device-side loop (use_graph = 2, batches): add this solve's loop to g;
+    // after the graph ran, collect the result
+    virtual atm_status add_loop(cudaGraph_t g) = 0;
+    virtual atm_status loop_result(atm_result *res) = 0;
 };
 
 template <typename T>
@@ -309,6 +313,10 @@ struct Plan : PlanBase {
     bool any_learned = false;
     bool net_ready = false;
     bool launch_failed = false;          // a launch helper reported an error
+    bool no_events = false;              // capturing a conditional body: no event nodes
+    double *loop_hist = nullptr;         // device residual history of the device-side loop
+    double *loop_state = nullptr;        // cycles, growth count, smallest residual
+    cudaGraphExec_t gLoop = nullptr;
     float *nn_params = nullptr;
     void *nn_packed = nullptr;
     void *nn_scratch = nullptr;
@@ -337,6 +345,7 @@ struct Plan : PlanBase {
         if (gA && gA != gA_nn && gA != gA_cl) cudaGraphExecDestroy(gA);
         if (gIter && gIter != gIter_nn && gIter != gIter_cl) cudaGraphExecDestroy(gIter);
         if (gSeq) cudaGraphExecDestroy(gSeq);
+        if (gLoop) cudaGraphExecDestroy(gLoop);
         if (ev0) cudaEventDestroy(ev0);
         if (ev1) cudaEventDestroy(ev1);
     }
@@ -722,6 +731,8 @@ struct Plan : PlanBase {
         stage64 = take<double>((size_t)nsp);
         partials = take<double>((size_t)(npartials_max > 0 ? npartials_max : 1));
         norm_cur = take<double>(1);
+        loop_hist = take<double>((size_t)(sv.max_iter > 0 ? sv.max_iter : 0) + 2);
+        loop_state = take<double>(4);
         any_learned = !is1d && L > 1 && sv.coarse_prop == ATM_PROP_LEARNED;
         if (any_learned) {
             nn_params = take<float>((size_t)nn::param_count());
@@ -794,7 +805,7 @@ struct Plan : PlanBase {
         SweepArgs<T> a = Lv.args;
         a.neg = neg;
         a.mid = mid;
-        const bool prof = slot >= 0 && slot < nprof;
+        const bool prof = !no_events && slot >= 0 && slot < nprof;
         if (prof) cudaEventRecordWithFlags(pev[4 * slot], st, cudaEventRecordExternal);
         if (is1d) {
             a.jobs = djobs;
@@ -992,6 +1003,9 @@ struct Plan : PlanBase {
             gA_nn = gA;
             gIter_nn = gIter;
         }
+        if (sv.use_graph == 2 && st != nullptr && role == ROLE_NORMAL && sv.algorithm != ATM_SEQUENTIAL &&
+            !learned_cfg)
+            ATM_TRY(build_loop_graph());
         return ATM_OK;
     }
 
@@ -1025,6 +1039,88 @@ struct Plan : PlanBase {
             gIter = on ? gIter_nn : gIter_cl;
         }
         return ATM_OK;
+    }
+
+    // The solve as a graph fragment: the first relaxation pass and its
+    // residual, then a WHILE node whose body is one cycle (rest of the cycle +
+    // next pass) followed by the decision kernel.
+    atm_status add_loop(cudaGraph_t g) override
+    {
+        if (role != ROLE_NORMAL || sv.algorithm == ATM_SEQUENTIAL || learned_cfg)
+            return fail(ATM_ERR_UNSUPPORTED, "device-side loops need an MGRIT/AT-MGRIT handle without the learned propagator");
+        if (st == nullptr) return fail(ATM_ERR_INVALID_ARG, "device-side loops need a non-default stream");
+        cudaGraphConditionalHandle h;
+        ATM_CK(cudaGraphConditionalHandleCreate(&h, g, 0, 0));
+        no_events = true;
+        cudaError_t e = cudaStreamBeginCaptureToGraph(st, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) { no_events = false; return fail(ATM_ERR_CUDA, "capture failed: %s", cudaGetErrorString(e)); }
+        enqueue(passA);
+        loop_decide_kernel<<<1, 1, 0, st>>>(norm_cur, loop_hist, loop_state, sv.max_iter, sv.tol, h, 1);
+        cudaStreamCaptureStatus cs;
+        const cudaGraphNode_t *deps = nullptr;
+        size_t nd = 0;
+        cudaGraph_t cg = nullptr;
+        e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &cg, &deps, nullptr, &nd);
+        cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t node;
+        if (e == cudaSuccess) e = cudaGraphAddNode(&node, g, deps, nullptr, nd, &cp);
+        cudaGraph_t tmp = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(st, &tmp);
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+            no_events = false;
+            return fail(ATM_ERR_CUDA, "building the loop failed: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+        }
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        e = cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            enqueue(rest);
+            enqueue(passA);
+            loop_decide_kernel<<<1, 1, 0, st>>>(norm_cur, loop_hist, loop_state, sv.max_iter, sv.tol, h, 0);
+            e = cudaStreamEndCapture(st, &tmp);
+        }
+        no_events = false;
+        if (e != cudaSuccess) return fail(ATM_ERR_CUDA, "capturing the loop body failed: %s", cudaGetErrorString(e));
+        if (launch_failed) return fail(ATM_ERR_CUDA, "a launch failed while building the loop");
+        return ATM_OK;
+    }
+
+    atm_status loop_result(atm_result *res) override
+    {
+        double stv[4];
+        ATM_CK(cudaMemcpy(stv, loop_state, sizeof(stv), cudaMemcpyDeviceToHost));
+        const int it = (int)stv[0];
+        hist.assign((size_t)it + 1, 0.0);
+        ATM_CK(cudaMemcpy(hist.data(), loop_hist, sizeof(double) * (it + 1), cudaMemcpyDeviceToHost));
+        launches = (long long)kernels_in(passA) + 1 + (long long)it * (kernels_in(rest) + kernels_in(passA) + 1);
+        atm_result R;
+        std::memset(&R, 0, sizeof(R));
+        R.iterations = it;
+        R.initial_residual = hist.front();
+        R.final_residual = hist.back();
+        R.converged = hist.back() <= sv.tol;
+        atm_status status = ATM_OK;
+        if (!std::isfinite(hist.back()) || (int)stv[1] >= 3)
+            status = fail(ATM_ERR_DIVERGED, "residual diverged (%g after %d cycles)", hist.back(), it);
+        else if (!R.converged)
+            status = fail(ATM_ERR_NOT_CONVERGED, "residual %g > tol %g after %d cycles", hist.back(), sv.tol, it);
+        if (res) *res = R;
+        return status;
+    }
+
+    atm_status build_loop_graph()
+    {
+        cudaGraph_t g = nullptr;
+        ATM_CK(cudaGraphCreate(&g, 0));
+        atm_status s = add_loop(g);
+        if (s == ATM_OK) {
+            cudaError_t e = cudaGraphInstantiate(&gLoop, g, 0);
+            if (e != cudaSuccess) s = fail(ATM_ERR_CUDA, "instantiating the loop graph failed: %s", cudaGetErrorString(e));
+        }
+        cudaGraphDestroy(g);
+        return s;
     }
 
     atm_status read_norm(double *v)
@@ -1063,6 +1159,19 @@ struct Plan : PlanBase {
 
     atm_status solve_once(atm_result *res)
     {
+        if (gLoop) {
+            ATM_CK(cudaEventRecord(ev0, st));
+            ATM_CK(cudaGraphLaunch(gLoop, st));
+            ATM_CK(cudaEventRecord(ev1, st));
+            ATM_CK(cudaEventSynchronize(ev1));
+            float ms = 0;
+            ATM_CK(cudaEventElapsedTime(&ms, ev0, ev1));
+            atm_result R;
+            atm_status s = loop_result(&R);
+            R.time_ms = ms;
+            if (res) *res = R;
+            return s;
+        }
         atm_result R;
         std::memset(&R, 0, sizeof(R));
         launches = 0;
@@ -1477,6 +1586,11 @@ struct RefinedPlan : PlanBase {
     {
         return fail(ATM_ERR_UNSUPPORTED, "the learned propagator is not available in the refined mode");
     }
+    atm_status add_loop(cudaGraph_t) override
+    {
+        return fail(ATM_ERR_UNSUPPORTED, "device-side loops are not available in the refined mode");
+    }
+    atm_status loop_result(atm_result *) override { return fail(ATM_ERR_UNSUPPORTED, "refined mode"); }
     atm_status apply_prop(int level, const double *in, double *o, int n) override
     {
         return inner.apply_prop(level, in, o, n);

@@ -539,6 +539,27 @@ static __global__ void refine_update_kernel(double *u, const float *e, size_t n)
         u[i] = u[i] + (double)e[i];
 }
 
+// Device-side convergence control of one solve (one thread).  state[0] =
+// cycles completed, state[1] = consecutive growths above 1e3 x the smallest
+// residual, state[2] = smallest residual.  Records the residual of the current
+// iterate and sets the loop condition: continue while the residual is finite,
+// above tol, below max_iter cycles and not growing three times in a row.
+static __global__ void loop_decide_kernel(const double *norm, double *hist, double *state, int max_iter, double tol,
+                                          cudaGraphConditionalHandle handle, int first)
+{
+    const double r = *norm;
+    int it = first ? 0 : (int)state[0] + 1;
+    double rmin = first ? r : state[2];
+    if (r < rmin) rmin = r;
+    const int growth = (!first && r > 1e3 * rmin) ? (int)state[1] + 1 : 0;
+    state[0] = it;
+    state[1] = growth;
+    state[2] = rmin;
+    hist[it] = r;
+    const bool go = isfinite(r) && r > tol && it < max_iter && growth < 3;
+    cudaGraphSetConditional(handle, go ? 1u : 0u);
+}
+
 template <typename Ti, typename To>
 __global__ void convert_kernel(const Ti *in, To *out, size_t n)
 {
