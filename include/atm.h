@@ -112,6 +112,16 @@ typedef struct {
                                          node repeats the cycle until a kernel finds the residual
                                          below tol (no host round trip until the end) */
     int profile;                      /* 1: time the level-0 relaxation sweeps with CUDA events */
+    int cpoint_storage_only;          /* 1: level 0 keeps only its C-points (t = i m_0) and one
+                                         working state per C-interval, about 3 N_t / m_0 states
+                                         instead of N_t + N_t / m_0 (Sec. 2.1: the F-points of an
+                                         iterate are the F-relaxation of its C-points).  F-points
+                                         are recomputed from their C-point when read; F-points after
+                                         the last C-point are not computed by the cycle.  With
+                                         ATM_FP32_REFINED the FP64 residual is taken at the C-points
+                                         (zero at F-points by construction) and the FP32 inner cycle
+                                         regenerates the base F-chain it linearises around.  With
+                                         ATM_SEQUENTIAL every m_0-th state is kept (m_0 = 0: 16). */
 } atm_solver;
 
 typedef struct {
@@ -145,7 +155,9 @@ atm_status atm_set_initial_condition(atm_handle *h, const double *u0);
 
 /* Set the iterate at time points 1..nt_points-1 from `u` (FP64, nt_points
  * states, host or device; state 0 is ignored).  u = NULL sets the zero guess
- * (the default after atm_create). */
+ * (the default after atm_create).  Only C-point values influence the
+ * iteration (its first F-relaxation overwrites the F-points); with C-point
+ * storage only they are kept. */
 atm_status atm_set_initial_guess(atm_handle *h, const double *u);
 
 /* Run the solver (Algorithm 2 V-cycles, or sequential stepping) until the
@@ -156,7 +168,10 @@ atm_status atm_set_initial_guess(atm_handle *h, const double *u);
 atm_status atm_solve(atm_handle *h, atm_result *out);
 
 /* Copy states t0..t0+count-1 of the level-0 iterate to `dst` (FP64, host or
- * device pointer).  Blocks for host destinations. */
+ * device pointer).  Blocks for host destinations.  With C-point storage the
+ * F-points of the range are recomputed from their C-points with the level-0
+ * propagator (one launch per F-point offset); after a solve they equal the
+ * values a fully stored iterate holds. */
 atm_status atm_get_solution(atm_handle *h, int t0, int count, double *dst);
 
 /* Residual norms of the last solve: hist[0] for the initial guess, hist[i]

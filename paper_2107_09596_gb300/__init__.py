@@ -49,7 +49,7 @@ class SolverDesc(ctypes.Structure):
                 ("coarse_reaction", ctypes.c_int),
                 ("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("precision", ctypes.c_int), ("use_graph", ctypes.c_int),
-                ("profile", ctypes.c_int)]
+                ("profile", ctypes.c_int), ("cpoint_storage_only", ctypes.c_int)]
 
 
 class TrainCfg(ctypes.Structure):
@@ -150,7 +150,7 @@ def make_problem(kind, nx, ny=1, lx=1.0, ly=1.0, dt=1e-3, nt_points=65, eps=0.02
 def make_solver(algorithm=AT_MGRIT, m=(8,), k=4, nu=1, fine_prop=PROP_PR_ADI,
                 coarse_prop=PROP_SPLIT_BE, reaction_substeps=None, coarse_reaction=REACT_EXACT,
                 tol=1e-10, max_iter=50,
-                precision=FP64, use_graph=True, profile=False) -> SolverDesc:
+                precision=FP64, use_graph=True, profile=False, cpoint_only=False) -> SolverDesc:
     s = SolverDesc()
     s.algorithm = algorithm
     s.levels = len(m) + 1
@@ -164,6 +164,7 @@ def make_solver(algorithm=AT_MGRIT, m=(8,), k=4, nu=1, fine_prop=PROP_PR_ADI,
             s.reaction_substeps[j] = v
     s.tol, s.max_iter, s.precision, s.use_graph = tol, max_iter, precision, int(use_graph)
     s.profile = int(profile)
+    s.cpoint_storage_only = int(cpoint_only)
     return s
 
 

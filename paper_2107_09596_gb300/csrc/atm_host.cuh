@@ -293,11 +293,16 @@ struct Plan : PlanBase {
     int nsp = 0;
     bool is1d = false;
     int maxbatch = 16;
+    int midcap = 16;        // states in the row-sweep intermediate (launches are chunked to it)
     // workspace layout
     uintptr_t base = 0;
     size_t off = 0;
     std::vector<Level<T>> lv;
     T *yC = nullptr;        // level-0 C-relaxation values (FCF)
+    bool cpo = false;       // level 0 stores C-points only (u holds them, `work` the F-chains)
+    T *work = nullptr;      // cpo: one working state per interval (the latest F-point)
+    T *bwork = nullptr;     // cpo, inner role: the base chain of each interval (latest F-point)
+    size_t regen_index = 0; // cpo: jobs u[i] -> work[i] (NC), then work[i] -> work[i] (NC)
     T *mid = nullptr;       // row-sweep results, maxbatch states
     T *sin = nullptr, *sout = nullptr;   // FP64 <-> T staging for atm_apply_propagator
     double *stage64 = nullptr;           // one FP64 state for host transfers
@@ -360,7 +365,30 @@ struct Plan : PlanBase {
     }
 
     T *st_ptr(T *arr, int t) const { return arr + (size_t)t * nsp; }
-    T *gl(int l, int t) const { return lv[l].g ? st_ptr(lv[l].g, t) : nullptr; }
+
+    // State of level l at time point t.  With C-point-only storage level 0
+    // keeps C-point i at u[i] and the latest F-point of interval i at work[i].
+    T *up(int l, int t) const
+    {
+        if (l == 0 && cpo) {
+            const int m = lv[0].m, i = t / m;
+            return (t % m == 0) ? st_ptr(lv[0].u, i) : st_ptr(work, i);
+        }
+        return st_ptr(lv[l].u, t);
+    }
+    // Right-hand side of level l at t.  With C-point storage the level-0
+    // right-hand side (inner role) is nonzero at C-points only and stored per C-point.
+    T *gl(int l, int t) const
+    {
+        if (!lv[l].g) return nullptr;
+        if (l == 0 && cpo) return (t % lv[0].m == 0) ? st_ptr(lv[0].g, t / lv[0].m) : nullptr;
+        return st_ptr(lv[l].g, t);
+    }
+    // Number of level-0 states held in memory.
+    int ustates() const { return cpo ? lv[0].NC : lv[0].N; }
+    // With C-point storage, is the level-0 interval i followed by a C-point?
+    // (F-points after the last C-point feed nothing and are not computed.)
+    bool full_interval(int i) const { return (i + 1) * lv[0].m <= lv[0].N - 1; }
 
     // ---------------- validation and layout ----------------
     atm_status validate() const
@@ -397,6 +425,8 @@ struct Plan : PlanBase {
             if (sv.fine_prop < 0 || sv.fine_prop > 1 || sv.coarse_prop < 0 || sv.coarse_prop > 2)
                 return fail(ATM_ERR_INVALID_ARG, "unknown propagator");
         }
+        if (sv.cpoint_storage_only && sv.algorithm == ATM_SEQUENTIAL && sv.m[0] == 1)
+            return fail(ATM_ERR_INVALID_ARG, "C-point storage needs m[0] >= 2 (or 0 for the default 16)");
         if (sv.coarse_prop == ATM_PROP_LEARNED) {
             if (is1d) return fail(ATM_ERR_INVALID_ARG, "the learned propagator is for the 2D problems");
             if (sv.algorithm == ATM_SEQUENTIAL) return fail(ATM_ERR_INVALID_ARG, "the learned propagator needs levels >= 2");
@@ -489,6 +519,11 @@ struct Plan : PlanBase {
         if (!ubase) return nullptr;
         size_t f = (size_t)t;
         for (int j = 0; j < l; ++j) f *= (size_t)sv.m[j];
+        if (cpo) {
+            // C-point storage: ubase holds the C-points, bwork the regenerated base chain
+            const size_t m0 = (size_t)lv[0].m;
+            return (f % m0 == 0) ? ubase + (f / m0) * nsp : bwork + (f / m0) * nsp;
+        }
         return ubase + f * nsp;
     }
 
@@ -507,13 +542,19 @@ struct Plan : PlanBase {
     {
         Level<T> &Lv = lv[l];
         const int N = Lv.N, m = Lv.m, NC = Lv.NC;
+        const bool c0 = cpo && l == 0;
         for (int j = 1; j < m; ++j) {
             std::vector<Job<T>> js;
             for (int i = 0; i < NC; ++i) {
                 const int t = i * m + j;
-                if (t < N)
-                    js.push_back(job(st_ptr(Lv.u, t - 1), st_ptr(Lv.u, t), gl(l, t), nullptr, nullptr, nullptr,
-                                     bp(l, t - 1)));
+                if (t < N && (!c0 || full_interval(i)))
+                    js.push_back(job(up(l, t - 1), up(l, t), gl(l, t), nullptr, nullptr, nullptr, bp(l, t - 1)));
+            }
+            if (c0 && bwork) {
+                // advance the base chain after every increment of this step has read it
+                for (int i = 0; i < NC; ++i)
+                    if (full_interval(i))
+                        js.push_back(job(j == 1 ? st_ptr(ubase, i) : st_ptr(bwork, i), st_ptr(bwork, i)));
             }
             add_sweep(ph, l, std::move(js), 0, false);
         }
@@ -521,8 +562,8 @@ struct Plan : PlanBase {
             std::vector<Job<T>> js;
             for (int i = 1; i < NC; ++i) {
                 const int t = i * m;
-                js.push_back(job(st_ptr(Lv.u, t - 1), resid == 1 ? st_ptr(yC, i) : nullptr, gl(l, t), nullptr,
-                                 st_ptr(Lv.u, t), resid == 2 ? st_ptr(lv[l + 1].r, i) : nullptr, bp(l, t - 1)));
+                js.push_back(job(up(l, t - 1), resid == 1 ? st_ptr(yC, i) : nullptr, gl(l, t), nullptr,
+                                 up(l, t), resid == 2 ? st_ptr(lv[l + 1].r, i) : nullptr, bp(l, t - 1)));
             }
             const int n = (int)js.size();
             add_sweep(ph, l, std::move(js), 0, norm);
@@ -537,7 +578,7 @@ struct Plan : PlanBase {
         if (Lv.g) add_axpy(ph, {ajob(Lv.u, Lv.g)});
         std::vector<Job<T>> js;
         for (int i = 1; i < Lv.NC; ++i)
-            js.push_back(job(st_ptr(Lv.u, i * Lv.m - 1), st_ptr(Lv.u, i * Lv.m), gl(l, i * Lv.m), nullptr, nullptr,
+            js.push_back(job(up(l, i * Lv.m - 1), up(l, i * Lv.m), gl(l, i * Lv.m), nullptr, nullptr,
                              nullptr, bp(l, i * Lv.m - 1)));
         add_sweep(ph, l, std::move(js), 0, false);
     }
@@ -549,7 +590,7 @@ struct Plan : PlanBase {
         std::vector<Job<T>> js;
         for (int i = 1; i < Lv.NC; ++i) {
             const int t = i * Lv.m;
-            js.push_back(job(st_ptr(Lv.u, t - 1), nullptr, gl(l, t), nullptr, st_ptr(Lv.u, t), st_ptr(lv[l + 1].r, i),
+            js.push_back(job(up(l, t - 1), nullptr, gl(l, t), nullptr, up(l, t), st_ptr(lv[l + 1].r, i),
                              bp(l, t - 1)));
         }
         add_sweep(ph, l, std::move(js), 0, false);
@@ -562,11 +603,11 @@ struct Plan : PlanBase {
     {
         Level<T> &F = lv[l];
         Level<T> &C = lv[l + 1];
-        add_axpy(ph, {F.g ? ajob(C.r, nullptr, F.g, F.u) : ajob(C.r, nullptr)});
+        add_axpy(ph, {F.g ? ajob(C.r, nullptr, F.g, up(l, 0)) : ajob(C.r, nullptr)});
         std::vector<AxpyJob<T>> cp;
         for (int i = 0; i < C.N; ++i) {
-            cp.push_back(ajob(st_ptr(C.v, i), st_ptr(F.u, i * F.m)));
-            cp.push_back(ajob(st_ptr(C.u, i), st_ptr(F.u, i * F.m)));
+            cp.push_back(ajob(st_ptr(C.v, i), up(l, i * F.m)));
+            cp.push_back(ajob(st_ptr(C.u, i), up(l, i * F.m)));
         }
         add_axpy(ph, std::move(cp));
         std::vector<Job<T>> js;
@@ -613,7 +654,7 @@ struct Plan : PlanBase {
     {
         std::vector<AxpyJob<T>> js;
         for (int i = 0; i < lv[l + 1].N; ++i)
-            js.push_back(ajob(st_ptr(lv[l].u, i * lv[l].m), st_ptr(lv[l].u, i * lv[l].m), st_ptr(lv[l + 1].u, i),
+            js.push_back(ajob(up(l, i * lv[l].m), up(l, i * lv[l].m), st_ptr(lv[l + 1].u, i),
                               st_ptr(lv[l + 1].v, i)));
         add_axpy(ph, std::move(js));
     }
@@ -633,7 +674,9 @@ struct Plan : PlanBase {
         add_restrict(ph, l);
         add_level_cycle(ph, l + 1);
         add_correct(ph, l);
-        add_frelax(ph, l, 0, false);
+        // with C-point storage the F-points of the correction are not kept: the
+        // next residual pass recomputes the F-chains from the corrected C-points
+        if (!(cpo && l == 0 && role == ROLE_INNER)) add_frelax(ph, l, 0, false);
     }
 
     void build_phases()
@@ -643,6 +686,20 @@ struct Plan : PlanBase {
         passA.clear(); rest.clear(); seq.clear(); st_coarse.clear();
         st_f.assign(L, Phase()); st_c.assign(L, Phase()); st_r.assign(L, Phase()); st_corr.assign(L, Phase());
         resid_full.clear(); inner_cycle.clear();
+        if (role == ROLE_OUTER && cpo) {
+            // C-point storage: the F-points are the F-chains of the C-points, so the
+            // residual is zero there; r_i = Phi(u_{im-1}) - u_im at the C-points i >= 1
+            add_frelax(resid_full, 0, 0, false);
+            std::vector<Job<T>> js;
+            for (int i = 1; i < lv[0].NC; ++i)
+                js.push_back(job(up(0, i * lv[0].m - 1), nullptr, nullptr, nullptr, up(0, i * lv[0].m),
+                                 st_ptr(r_full, i)));
+            const int n = (int)js.size();
+            add_sweep(resid_full, 0, std::move(js), 0, true);
+            add_norm(resid_full, n * blocks_per_job(0));
+            add_regen_jobs();
+            return;
+        }
         if (role == ROLE_OUTER) {
             // r_j = Phi(u_{j-1}) - u_j for every j >= 1 (level 0 is homogeneous), with the norm
             std::vector<Job<T>> js;
@@ -663,14 +720,15 @@ struct Plan : PlanBase {
         }
         if (sv.algorithm == ATM_SEQUENTIAL) {
             for (int j = 1; j < pb.nt_points; ++j)
-                add_sweep(seq, 0, {job(st_ptr(lv[0].u, j - 1), st_ptr(lv[0].u, j))}, 0, false);
+                add_sweep(seq, 0, {job(up(0, j - 1), up(0, j))}, 0, false);
+            add_regen_jobs();
             return;
         }
         // level 0: pass A = F-relaxation + residual (norm); the rest of the cycle
         add_frelax(passA, 0, sv.nu == 1 ? 1 : 2, true);
         if (sv.nu == 1) {
             std::vector<AxpyJob<T>> cp;
-            for (int i = 1; i < lv[0].NC; ++i) cp.push_back(ajob(st_ptr(lv[0].u, i * lv[0].m), st_ptr(yC, i)));
+            for (int i = 1; i < lv[0].NC; ++i) cp.push_back(ajob(up(0, i * lv[0].m), st_ptr(yC, i)));
             add_axpy(rest, std::move(cp));
             add_frelax(rest, 0, 2, false);
         }
@@ -688,6 +746,17 @@ struct Plan : PlanBase {
             }
         }
         add_coarsest(st_coarse);
+        add_regen_jobs();
+    }
+
+    // Jobs that recompute F-points from the C-points (C-point storage):
+    // u[i] -> work[i] for the first step of each interval, work[i] -> work[i] after.
+    void add_regen_jobs()
+    {
+        if (!cpo) return;
+        regen_index = jobs.size();
+        for (int i = 0; i < lv[0].NC; ++i) jobs.push_back(job(st_ptr(lv[0].u, i), st_ptr(work, i)));
+        for (int i = 0; i < lv[0].NC; ++i) jobs.push_back(job(st_ptr(work, i), st_ptr(work, i)));
     }
 
     // ---------------- layout (two passes: sizes, then real pointers) ----------------
@@ -707,11 +776,22 @@ struct Plan : PlanBase {
             lv[l].NC = (lv[l].N - 1) / sv.m[l] + 1;
             lv[l + 1].N = lv[l].NC;
         }
-        lv[0].u = take<T>((size_t)lv[0].N * nsp);
-        if (role == ROLE_OUTER) r_full = take<T>((size_t)lv[0].N * nsp);
+        cpo = sv.cpoint_storage_only != 0;
+        if (cpo && L == 1) {
+            // sequential stepping and the FP64 outer loop keep every m-th point
+            // (m = m_0, or 16 for sequential stepping when m_0 is not given)
+            lv[0].m = sv.m[0] >= 2 ? sv.m[0] : 16;
+            lv[0].NC = (lv[0].N - 1) / lv[0].m + 1;
+        }
+        const size_t n0 = (size_t)(cpo ? lv[0].NC : lv[0].N) * nsp;
+        lv[0].u = take<T>(n0);
+        bwork = nullptr;
+        if (cpo) work = take<T>(n0);
+        if (role == ROLE_OUTER) r_full = take<T>(n0);
         if (role == ROLE_INNER) {
-            lv[0].g = take<T>((size_t)lv[0].N * nsp);
-            ubase = take<T>((size_t)lv[0].N * nsp);
+            lv[0].g = take<T>(n0);
+            ubase = take<T>(n0);
+            if (cpo) bwork = take<T>(n0);
         }
         if (L > 1 && sv.nu == 1 && role == ROLE_NORMAL) yC = take<T>((size_t)lv[0].NC * nsp);
         for (int l = 1; l < L; ++l) {
@@ -723,10 +803,17 @@ struct Plan : PlanBase {
         }
         maxbatch = batch_hint;
         npartials_max = npart_hint;
-        if (!is1d) mid = take<T>((size_t)maxbatch * nsp);
+        {
+            // at most 1 GiB of intermediate (and at least 16 states)
+            const size_t cap = ((size_t)1 << 30) / ((size_t)nsp * sizeof(T));
+            midcap = maxbatch;
+            if ((size_t)midcap > cap) midcap = cap < 16 ? 16 : (int)cap;
+            if (midcap > 32768) midcap = 32768;   // grid y limit of a launch
+        }
+        if (!is1d) mid = take<T>((size_t)midcap * nsp);
         if (sizeof(T) != sizeof(double)) {
-            sin = take<T>((size_t)maxbatch * nsp);
-            sout = take<T>((size_t)maxbatch * nsp);
+            sin = take<T>((size_t)midcap * nsp);
+            sout = take<T>((size_t)midcap * nsp);
         }
         stage64 = take<double>((size_t)nsp);
         partials = take<double>((size_t)(npartials_max > 0 ? npartials_max : 1));
@@ -740,7 +827,7 @@ struct Plan : PlanBase {
             const int ch = maxbatch < nn::kInferChunk ? maxbatch : nn::kInferChunk;
             nn_scratch = take<unsigned char>(nn::infer_scratch_bytes(ch, pb.ny, pb.nx));
             nn_err = take<int>(1);
-            snapshot = take<T>((size_t)lv[0].N * nsp);
+            snapshot = take<T>(n0);
         }
         for (int l = 0; l < L; ++l) {
             if (is1d) lv[l].dir_w = take<T>((size_t)pb.nx);
@@ -757,7 +844,7 @@ struct Plan : PlanBase {
         }
         d_jobs = take<Job<T>>(jobs.size() + 1);
         d_ajobs = take<AxpyJob<T>>(ajobs.size() + 1);
-        d_dyn = take<Job<T>>((size_t)maxbatch);
+        d_dyn = take<Job<T>>((size_t)midcap);
         off = (off + 255) & ~(size_t)255;
         return ATM_OK;
     }
@@ -793,6 +880,14 @@ struct Plan : PlanBase {
     // level 0 the jobs go in chunks of `chunk` states per row/column pair so
     // that the row-sweep intermediate is still in L2 when the column sweep
     // reads it.
+    // Jobs per row/column launch pair: the tuned level-0 chunk, and never more
+    // than the intermediate holds.
+    int chunk_size(int l, int njobs) const
+    {
+        int cs = (l == 0 && chunk > 0 && chunk < njobs) ? chunk : njobs;
+        return cs > midcap ? midcap : cs;
+    }
+
     void launch_sweep(int l, const Job<T> *djobs, int njobs, int neg, double *part, int slot = -1)
     {
         const Level<T> &Lv = lv[l];
@@ -814,7 +909,7 @@ struct Plan : PlanBase {
             if (prof) cudaEventRecordWithFlags(pev[4 * slot + 3], st, cudaEventRecordExternal);
             return;
         }
-        const int cs = (l == 0 && chunk > 0 && chunk < njobs) ? chunk : njobs;
+        const int cs = chunk_size(l, njobs);
         const bool split = cs == njobs;
         for (int j0 = 0; j0 < njobs; j0 += cs) {
             const int nj = njobs - j0 < cs ? njobs - j0 : cs;
@@ -838,7 +933,7 @@ struct Plan : PlanBase {
             const int ch = maxbatch < nn::kInferChunk ? maxbatch : nn::kInferChunk;
             return 5 * ((njobs + ch - 1) / ch);   // counted as kernels / 2 by kernels_in
         }
-        const int cs = (l == 0 && chunk > 0 && chunk < njobs) ? chunk : njobs;
+        const int cs = chunk_size(l, njobs);
         return (njobs + cs - 1) / cs;
     }
 
@@ -976,11 +1071,14 @@ struct Plan : PlanBase {
             ATM_CK(cudaMemcpyAsync(d_jobs, jobs.data(), jobs.size() * sizeof(Job<T>), cudaMemcpyHostToDevice, st));
         if (!ajobs.empty())
             ATM_CK(cudaMemcpyAsync(d_ajobs, ajobs.data(), ajobs.size() * sizeof(AxpyJob<T>), cudaMemcpyHostToDevice, st));
-        ATM_CK(cudaMemsetAsync(lv[0].u, 0, (size_t)lv[0].N * nsp * sizeof(T), st));
-        if (r_full) ATM_CK(cudaMemsetAsync(r_full, 0, (size_t)lv[0].N * nsp * sizeof(T), st));
+        const size_t n0 = (size_t)ustates() * nsp * sizeof(T);
+        ATM_CK(cudaMemsetAsync(lv[0].u, 0, n0, st));
+        if (work) ATM_CK(cudaMemsetAsync(work, 0, n0, st));
+        if (r_full) ATM_CK(cudaMemsetAsync(r_full, 0, n0, st));
         if (role == ROLE_INNER) {
-            ATM_CK(cudaMemsetAsync(lv[0].g, 0, (size_t)lv[0].N * nsp * sizeof(T), st));
-            ATM_CK(cudaMemsetAsync(ubase, 0, (size_t)lv[0].N * nsp * sizeof(T), st));
+            ATM_CK(cudaMemsetAsync(lv[0].g, 0, n0, st));
+            ATM_CK(cudaMemsetAsync(ubase, 0, n0, st));
+            if (bwork) ATM_CK(cudaMemsetAsync(bwork, 0, n0, st));
         }
         ATM_CK(cudaEventCreate(&ev0));
         ATM_CK(cudaEventCreate(&ev1));
@@ -988,7 +1086,7 @@ struct Plan : PlanBase {
         for (cudaEvent_t &e : pev) ATM_CK(cudaEventCreate(&e));
         if (sv.algorithm != ATM_SEQUENTIAL || role == ROLE_OUTER)
             ATM_TRY(autotune_chunk(role == ROLE_OUTER ? resid_full : role == ROLE_INNER ? inner_cycle : passA));
-        ATM_CK(cudaMemsetAsync(lv[0].u, 0, (size_t)lv[0].N * nsp * sizeof(T), st));
+        ATM_CK(cudaMemsetAsync(lv[0].u, 0, n0, st));
         ATM_CK(cudaStreamSynchronize(st));
         if (sv.use_graph && st != nullptr && role == ROLE_NORMAL) {
             if (sv.algorithm == ATM_SEQUENTIAL) {
@@ -1136,7 +1234,7 @@ struct Plan : PlanBase {
             return fail(ATM_ERR_INVALID_ARG, "the learned coarse propagator has no weights (atm_set_learned_coarse)");
         if (!learned_cfg) return solve_once(res);
         ATM_TRY(use_learned(true));
-        ATM_CK(cudaMemcpyAsync(snapshot, lv[0].u, (size_t)lv[0].N * nsp * sizeof(T), cudaMemcpyDeviceToDevice, st));
+        ATM_CK(cudaMemcpyAsync(snapshot, lv[0].u, (size_t)ustates() * nsp * sizeof(T), cudaMemcpyDeviceToDevice, st));
         atm_result first;
         atm_status s1 = solve_once(&first);
         if (s1 != ATM_ERR_DIVERGED) {
@@ -1144,7 +1242,7 @@ struct Plan : PlanBase {
             return s1;
         }
         // the learned propagator failed: restore the iterate and solve with the classical one
-        ATM_CK(cudaMemcpyAsync(lv[0].u, snapshot, (size_t)lv[0].N * nsp * sizeof(T), cudaMemcpyDeviceToDevice, st));
+        ATM_CK(cudaMemcpyAsync(lv[0].u, snapshot, (size_t)ustates() * nsp * sizeof(T), cudaMemcpyDeviceToDevice, st));
         ATM_TRY(use_learned(false));
         const long long l1 = launches;
         atm_result second;
@@ -1314,24 +1412,56 @@ struct Plan : PlanBase {
         return ATM_OK;
     }
 
+    // With C-point storage only the C-points of a written range are kept: the
+    // iteration recomputes every F-point from the C-points before it reads one.
     atm_status set_state(int t0, int count, const double *src) override
     {
         if (!src || t0 < 0 || count < 0 || t0 + count > lv[0].N) return fail(ATM_ERR_INVALID_ARG, "state range out of bounds");
         if (count == 0) return ATM_OK;
-        return write_states(st_ptr(lv[0].u, t0), src, count);
+        if (!cpo) return write_states(st_ptr(lv[0].u, t0), src, count);
+        const int m = lv[0].m;
+        for (int i = (t0 + m - 1) / m; i * m < t0 + count; ++i)
+            ATM_TRY(write_states(st_ptr(lv[0].u, i), src + (size_t)(i * m - t0) * nsp, 1));
+        return ATM_OK;
     }
 
+    // With C-point storage the F-points of the range are recomputed from their
+    // C-points by the level-0 propagator (the operations of the F-relaxation, so
+    // the values equal those a fully stored iterate would hold); `work` is scratch
+    // between solves.
     atm_status get_state(int t0, int count, double *dst) override
     {
         if (!dst || t0 < 0 || count < 0 || t0 + count > lv[0].N) return fail(ATM_ERR_INVALID_ARG, "state range out of bounds");
         if (count == 0) return ATM_OK;
-        return read_states(st_ptr(lv[0].u, t0), dst, count);
+        if (!cpo) return read_states(st_ptr(lv[0].u, t0), dst, count);
+        const int m = lv[0].m, N = lv[0].N, NC = lv[0].NC, t1 = t0 + count;
+        const int i_lo = t0 / m, i_hi = (t1 - 1) / m;
+        for (int i = i_lo; i <= i_hi; ++i)
+            if (i * m >= t0) ATM_TRY(read_states(st_ptr(lv[0].u, i), dst + (size_t)(i * m - t0) * nsp, 1));
+        const int G = midcap;
+        for (int g0 = i_lo; g0 <= i_hi; g0 += G) {
+            const int g1 = (i_hi + 1 < g0 + G) ? i_hi + 1 : g0 + G;
+            for (int j = 1; j < m && g0 * m + j < t1; ++j) {
+                int n = 0;   // intervals of the group whose point i m + j exists (a prefix)
+                while (g0 + n < g1 && (g0 + n) * m + j < N) ++n;
+                if (n == 0) break;
+                launch_sweep(0, d_jobs + regen_index + (j == 1 ? 0 : NC) + g0, n, 0, nullptr);
+                if (launch_failed) return fail(ATM_ERR_CUDA, "F-point recomputation failed");
+                for (int i = g0; i < g0 + n; ++i) {
+                    const int t = i * m + j;
+                    if (t >= t0 && t < t1) ATM_TRY(read_states(st_ptr(work, i), dst + (size_t)(t - t0) * nsp, 1));
+                }
+            }
+        }
+        ATM_CK(cudaGetLastError());
+        ATM_CK(cudaStreamSynchronize(st));
+        return ATM_OK;
     }
 
     atm_status apply_prop(int level, const double *in, double *out, int n) override
     {
         if (level < 0 || level >= L) return fail(ATM_ERR_INVALID_ARG, "level %d out of range", level);
-        if (n < 0 || n > maxbatch) return fail(ATM_ERR_INVALID_ARG, "nstates %d exceeds the batch limit %d", n, maxbatch);
+        if (n < 0 || n > midcap) return fail(ATM_ERR_INVALID_ARG, "nstates %d exceeds the batch limit %d", n, midcap);
         if (n == 0) return ATM_OK;
         if (!in || !out || !is_device_ptr(in) || !is_device_ptr(out))
             return fail(ATM_ERR_INVALID_ARG, "in/out must be device pointers");
@@ -1377,6 +1507,12 @@ struct Plan : PlanBase {
         default: return fail(ATM_ERR_INVALID_ARG, "unknown array %d", array);
         }
         if (!arr) return fail(ATM_ERR_INVALID_ARG, "array %d does not exist on level %d", array, level);
+        if (level == 0 && array == ATM_ARRAY_U && cpo) {
+            ATM_TRY(write ? set_state(t0, count, buf) : get_state(t0, count, buf));
+            ATM_CK(cudaStreamSynchronize(st));
+            return ATM_OK;
+        }
+        if (level == 0 && cpo) return fail(ATM_ERR_UNSUPPORTED, "level-0 arrays other than u are per C-point with C-point storage");
         if (!buf || t0 < 0 || count < 0 || t0 + count > lv[level].N) return fail(ATM_ERR_INVALID_ARG, "state range out of bounds");
         if (count == 0) return ATM_OK;
         ATM_TRY(write ? write_states(st_ptr(arr, t0), buf, count) : read_states(st_ptr(arr, t0), buf, count));
@@ -1388,7 +1524,7 @@ struct Plan : PlanBase {
 
     atm_status zero_guess() override
     {
-        ATM_CK(cudaMemsetAsync(st_ptr(lv[0].u, 1), 0, (size_t)(lv[0].N - 1) * nsp * sizeof(T), st));
+        ATM_CK(cudaMemsetAsync(st_ptr(lv[0].u, 1), 0, (size_t)(ustates() - 1) * nsp * sizeof(T), st));
         return ATM_OK;
     }
 
@@ -1417,6 +1553,12 @@ namespace atm {
 //   relative to e, not to u), starting from e = 0,
 //   u += e (FP64),
 // repeated until ||r||_2 <= tol.
+// With C-point storage the iterate is its C-points (its F-points being their
+// FP64 F-chains), so r is nonzero at C-points only and is computed there after
+// an FP64 F-relaxation; the inner cycle's level-0 steps regenerate the FP32
+// base chain fp32(u_C) -> Phi(.) -> ... beside the increments (a rounding of the
+// linearisation point, not of the residual), and its final level-0
+// F-relaxation is left out (the next residual pass recomputes the F-chains).
 struct RefinedPlan : PlanBase {
     Plan<double> outer;
     Plan<float> inner;
@@ -1472,7 +1614,7 @@ struct RefinedPlan : PlanBase {
         return ATM_OK;
     }
 
-    size_t nstate_values() const { return (size_t)outer.lv[0].N * outer.nsp; }
+    size_t nstate_values() const { return (size_t)outer.ustates() * outer.nsp; }
 
     // base and right-hand side in FP32, zero correction, FP32 cycle, FP64 update
     void enqueue_inner()
