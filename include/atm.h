@@ -82,6 +82,9 @@ enum { ATM_SEQUENTIAL = 0, ATM_MGRIT = 1, ATM_AT_MGRIT = 2 };
  * loop (FP64 residual, correction and norm). */
 enum { ATM_FP64 = 0, ATM_FP32 = 1, ATM_FP32_REFINED = 2 };
 
+/* 2D propagator kernels (atm_solver.sweep_kernel). */
+enum { ATM_SWEEP_AUTO = 0, ATM_SWEEP_SPLIT = 1, ATM_SWEEP_FUSED = 2 };
+
 #define ATM_MAX_LEVELS 8
 
 typedef struct {
@@ -112,6 +115,13 @@ typedef struct {
                                          node repeats the cycle until a kernel finds the residual
                                          below tol (no host round trip until the end) */
     int profile;                      /* 1: time the level-0 relaxation sweeps with CUDA events */
+    int sweep_kernel;                 /* 2D propagator kernels: ATM_SWEEP_AUTO (level 0 autotuned
+                                         between the split and the fused kernels, fused on coarse
+                                         levels where available), ATM_SWEEP_SPLIT (row kernel +
+                                         column kernel through an HBM intermediate), ATM_SWEEP_FUSED
+                                         (one cluster kernel per application, the state held in
+                                         shared memory; FP32 on 64^2, 128^2, 256^2, 512^2 grids,
+                                         split kernels elsewhere) */
     int cpoint_storage_only;          /* 1: level 0 keeps only its C-points (t = i m_0) and one
                                          working state per C-interval, about 3 N_t / m_0 states
                                          instead of N_t + N_t / m_0 (Sec. 2.1: the F-points of an
@@ -223,6 +233,17 @@ long long atm_last_launch_count(const atm_handle *h);
  * one when a sweep runs in several row/column chunks).
  * *total_ms = summed CUDA-event durations, *launches = sweeps timed. */
 atm_status atm_get_kernel_profile(const atm_handle *h, int which, double *total_ms, long long *launches);
+
+/* Kernels of level `level`'s propagator as chosen at atm_create (the
+ * autotuner's pick on level 0 with ATM_SWEEP_AUTO).  Writes 5 ints:
+ *   cfg[0] kernel: 0 split row + column kernels, 1 fused cluster kernel,
+ *          2 learned network, 3 1D line kernel;
+ *   cfg[1] CTAs per state (fused: cluster size; split: column-kernel CTAs);
+ *   cfg[2] threads per CTA (fused) or per column-kernel CTA (split);
+ *   cfg[3] rows per column segment (fused) or per column-kernel thread (split);
+ *   cfg[4] level 0, split: states per row/column launch pair (0 = all).
+ * The refined mode reports its FP32 inner cycle. */
+atm_status atm_get_sweep_config(const atm_handle *h, int level, int *cfg);
 
 /* Solve several independent problems with one CUDA graph launch on
  * `cuda_stream`: the graph holds, for every handle, its first relaxation pass

@@ -20,6 +20,7 @@ PROP_SPLIT_BE, PROP_PR_ADI, PROP_LEARNED = 0, 1, 2
 REACT_EXACT, REACT_SUBSTEPS = 0, 1
 SEQUENTIAL, MGRIT, AT_MGRIT = 0, 1, 2
 FP64, FP32, FP32_REFINED = 0, 1, 2
+SWEEP_AUTO, SWEEP_SPLIT, SWEEP_FUSED = 0, 1, 2
 STAGE_F_RELAX, STAGE_C_RELAX, STAGE_RESTRICT, STAGE_COARSEST, STAGE_CORRECT = range(5)
 ARRAY_U, ARRAY_V, ARRAY_R, ARRAY_G = range(4)
 MAX_LEVELS = 8
@@ -49,7 +50,8 @@ class SolverDesc(ctypes.Structure):
                 ("coarse_reaction", ctypes.c_int),
                 ("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("precision", ctypes.c_int), ("use_graph", ctypes.c_int),
-                ("profile", ctypes.c_int), ("cpoint_storage_only", ctypes.c_int)]
+                ("profile", ctypes.c_int), ("sweep_kernel", ctypes.c_int),
+                ("cpoint_storage_only", ctypes.c_int)]
 
 
 class TrainCfg(ctypes.Structure):
@@ -78,7 +80,7 @@ EXPORTS = ["atm_workspace_size", "atm_create", "atm_set_initial_condition",
            "atm_last_launch_count", "atm_get_kernel_profile", "atm_apply_propagator_noalloc",
            "atm_nn_param_count", "atm_nn_workspace_size", "atm_nn_apply", "atm_nn_loss_grad",
            "atm_train_learned_coarse", "atm_set_learned_coarse", "atm_batch_solve", "atm_last_error",
-           "atm_destroy"]
+           "atm_get_sweep_config", "atm_destroy"]
 
 _lib = None
 
@@ -115,6 +117,7 @@ def load(build_if_missing: bool = True):
     L.atm_last_launch_count.argtypes = [vp]
     L.atm_last_launch_count.restype = ctypes.c_longlong
     L.atm_get_kernel_profile.argtypes = [vp, i, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_longlong)]
+    L.atm_get_sweep_config.argtypes = [vp, i, ctypes.POINTER(i)]
     L.atm_apply_propagator_noalloc.argtypes = [ctypes.POINTER(Problem), ctypes.POINTER(SolverDesc), i, vp, vp, i, vp]
     L.atm_nn_param_count.restype = i
     L.atm_nn_workspace_size.argtypes = [i, i, i, i, ctypes.POINTER(ctypes.c_size_t)]
@@ -150,7 +153,8 @@ def make_problem(kind, nx, ny=1, lx=1.0, ly=1.0, dt=1e-3, nt_points=65, eps=0.02
 def make_solver(algorithm=AT_MGRIT, m=(8,), k=4, nu=1, fine_prop=PROP_PR_ADI,
                 coarse_prop=PROP_SPLIT_BE, reaction_substeps=None, coarse_reaction=REACT_EXACT,
                 tol=1e-10, max_iter=50,
-                precision=FP64, use_graph=True, profile=False, cpoint_only=False) -> SolverDesc:
+                precision=FP64, use_graph=True, profile=False, cpoint_only=False,
+                sweep_kernel=0) -> SolverDesc:
     s = SolverDesc()
     s.algorithm = algorithm
     s.levels = len(m) + 1
@@ -165,6 +169,7 @@ def make_solver(algorithm=AT_MGRIT, m=(8,), k=4, nu=1, fine_prop=PROP_PR_ADI,
     s.tol, s.max_iter, s.precision, s.use_graph = tol, max_iter, precision, int(use_graph)
     s.profile = int(profile)
     s.cpoint_storage_only = int(cpoint_only)
+    s.sweep_kernel = int(sweep_kernel)
     return s
 
 
@@ -308,6 +313,13 @@ class Solver:
         ms, n = ctypes.c_double(), ctypes.c_longlong()
         _check(load().atm_get_kernel_profile(self.handle, which, ctypes.byref(ms), ctypes.byref(n)))
         return ms.value, n.value
+
+    def sweep_config(self, level=0):
+        """Kernels of a level's propagator: dict(kernel, ctas, threads, rows, chunk)."""
+        cfg = (ctypes.c_int * 5)()
+        _check(load().atm_get_sweep_config(self.handle, level, cfg))
+        names = {0: "split", 1: "fused", 2: "learned", 3: "line1d"}
+        return dict(kernel=names.get(cfg[0], str(cfg[0])), ctas=cfg[1], threads=cfg[2], rows=cfg[3], chunk=cfg[4])
 
     def set_learned_coarse(self, params):
         """Network weights (torch float32 device tensor) for coarse_prop = PROP_LEARNED."""

@@ -199,6 +199,12 @@ atm_status atm_get_kernel_profile(const atm_handle *h, int which, double *total_
     return ATM_OK;
 }
 
+atm_status atm_get_sweep_config(const atm_handle *h, int level, int *cfg)
+{
+    if (!h || !cfg) return atm::fail(ATM_ERR_INVALID_ARG, "invalid argument");
+    return h->p->sweep_config(level, cfg);
+}
+
 atm_status atm_set_learned_coarse(atm_handle *h, const float *d_params)
 {
     if (!h) return atm::fail(ATM_ERR_INVALID_ARG, "null handle");

@@ -1,0 +1,55 @@
+// atm_fused.cu -- instantiations of the fused whole-propagator kernel and
+// their registry (see atm_fused.cuh for the kernel).
+#include "atm_fused.cuh"
+#include "atm_fused.h"
+
+namespace atm {
+
+namespace {
+
+template <int C, int G, int NT, int LS>
+void add_shape(std::vector<FusedShape> &v, bool pr, bool react)
+{
+    FusedShape f;
+    if (pr) f.fn = react ? fused_sweep_kernel<C, G, NT, LS, true, true> : fused_sweep_kernel<C, G, NT, LS, true, false>;
+    else f.fn = react ? fused_sweep_kernel<C, G, NT, LS, false, true> : fused_sweep_kernel<C, G, NT, LS, false, false>;
+    f.G = G;
+    f.NT = NT;
+    f.LS = LS;
+    constexpr int NXP = 16 * C;
+    constexpr int P = NT >= NXP ? NT / NXP : 1;
+    f.smem = fused_smem_bytes(32 * C, P * LS, P);
+    v.push_back(f);
+}
+
+}  // namespace
+
+std::vector<FusedShape> fused_shapes(int nx, int ny, bool pr, bool react)
+{
+    std::vector<FusedShape> v;
+    if (nx == 64 && ny == 64) {
+        add_shape<2, 1, 256, 8>(v, pr, react);
+        add_shape<2, 1, 512, 4>(v, pr, react);
+        add_shape<2, 2, 256, 4>(v, pr, react);
+    }
+    if (nx == 128 && ny == 128) {
+        add_shape<4, 2, 256, 16>(v, pr, react);
+        add_shape<4, 1, 256, 32>(v, pr, react);
+        add_shape<4, 2, 512, 8>(v, pr, react);
+        add_shape<4, 4, 256, 8>(v, pr, react);
+    }
+    if (nx == 256 && ny == 256) {
+        add_shape<8, 4, 256, 32>(v, pr, react);
+        add_shape<8, 2, 512, 32>(v, pr, react);
+        add_shape<8, 8, 256, 16>(v, pr, react);
+        add_shape<8, 4, 512, 16>(v, pr, react);
+    }
+    if (nx == 512 && ny == 512) {
+        add_shape<16, 16, 256, 32>(v, pr, react);
+        add_shape<16, 8, 256, 64>(v, pr, react);
+        add_shape<16, 16, 512, 16>(v, pr, react);
+    }
+    return v;
+}
+
+}  // namespace atm

@@ -1,0 +1,455 @@
+// atm_fused.cuh -- the whole 2D propagator Phi of one state in one kernel: a
+// thread-block cluster of G CTAs holds the state in shared memory (CTA r owns
+// rows [r R, r R + R), R = ny / G), so the row-sweep result never travels
+// through HBM.  Per state: one read of `in` (plus the optional base), one
+// write of `out` -- the algorithmic minimum of 2 S n^2 bytes.
+//
+// Steps (same factorised line operators as the split row/column kernels, see
+// atm_kernels.cuh):
+//   1. load rows r0-1 .. r0+R (periodic halo rows for the PR explicit term),
+//      apply the reaction, store to a swizzled tile;
+//   2. row pass, one warp per pair of rows: rhs = rx0 w + rx1 (w[y-1] + w[y+1]),
+//      line solve along x (warp scan), then the explicit x term of the column
+//      half-step, cy0 v + cy1 (v[x-1] + v[x+1]), formed in registers; rows are
+//      written one tile row up so that later rows still find their inputs;
+//   3. column pass, thread = (pair of columns, segment of LS rows): the two
+//      first-order recurrences run in place in shared memory; segment carries
+//      are combined across the cluster through distributed shared memory (two
+//      exchanges);
+// Pairs of rows and of columns go through packed FP32x2 instructions
+// (FFMA2 / FADD2 / FMUL2), which halves the arithmetic instruction count.
+//   4. epilogue: 16-byte vector stores of val = (+-)Phi + g + h, residual
+//      r = val - sub with its FP64 square sum per CTA.
+// Tile swizzle: float4 index f of a row is stored at f ^ ((f >> 3) & 7), which
+// makes both the row pass (lane = C consecutive values) and the column pass
+// (lane = column) free of bank conflicts without padding.
+#pragma once
+
+#include <cooperative_groups.h>
+
+#include "atm_kernels.cuh"
+
+namespace atm {
+
+namespace cg = cooperative_groups;
+
+__device__ __forceinline__ int fz_swz(int x)
+{
+    return ((((x >> 2) ^ ((x >> 5) & 7)) << 2) | (x & 3));
+}
+
+// C consecutive floats of a tile row starting at x0 (x0 % 4 == 0 or C == 2).
+template <int C>
+__device__ __forceinline__ void fz_load(const float *row, int x0, float (&v)[C])
+{
+    if constexpr (C % 4 == 0) {
+#pragma unroll
+        for (int i = 0; i < C / 4; ++i) {
+            const float4 t = *reinterpret_cast<const float4 *>(row + fz_swz(x0 + 4 * i));
+            v[4 * i] = t.x; v[4 * i + 1] = t.y; v[4 * i + 2] = t.z; v[4 * i + 3] = t.w;
+        }
+    } else {
+        static_assert(C == 2, "C must be 2 or a multiple of 4");
+        const float2 t = *reinterpret_cast<const float2 *>(row + fz_swz(x0));
+        v[0] = t.x; v[1] = t.y;
+    }
+}
+
+template <int C>
+__device__ __forceinline__ void fz_store(float *row, int x0, const float (&v)[C])
+{
+    if constexpr (C % 4 == 0) {
+#pragma unroll
+        for (int i = 0; i < C / 4; ++i)
+            *reinterpret_cast<float4 *>(row + fz_swz(x0 + 4 * i)) = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+    } else {
+        *reinterpret_cast<float2 *>(row + fz_swz(x0)) = make_float2(v[0], v[1]);
+    }
+}
+
+// 16-byte asynchronous copy global -> shared (no register staging, L2 only),
+// and the wait for all of this thread's copies.
+__device__ __forceinline__ void fz_cp_async16(float *smem, const float *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void fz_cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
+__device__ __forceinline__ float4 fz_ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+
+// Epilogue of 4 consecutive values (the addends already loaded).
+template <bool RES>
+__device__ __forceinline__ void fz_epilogue4(const Job<float> &jb, size_t idx, float4 p, int neg, float4 g,
+                                             float4 h, float4 sb, double &acc)
+{
+    float4 v = neg ? make_float4(-p.x, -p.y, -p.z, -p.w) : p;
+    if (jb.g) { v.x += g.x; v.y += g.y; v.z += g.z; v.w += g.w; }
+    if (jb.h) { v.x += h.x; v.y += h.y; v.z += h.z; v.w += h.w; }
+    if (RES) {
+        const float4 r = make_float4(v.x - sb.x, v.y - sb.y, v.z - sb.z, v.w - sb.w);
+        acc = fma((double)r.x, (double)r.x, acc);
+        acc = fma((double)r.y, (double)r.y, acc);
+        acc = fma((double)r.z, (double)r.z, acc);
+        acc = fma((double)r.w, (double)r.w, acc);
+        if (jb.out2) *reinterpret_cast<float4 *>(jb.out2 + idx) = r;
+    }
+    if (jb.out) *reinterpret_cast<float4 *>(jb.out + idx) = v;
+}
+
+// Epilogue over the CTA's R rows in batches of U vectors per thread, every
+// load of a batch issued before its first use.
+template <int NX, int R, int NT, bool RES>
+__device__ __forceinline__ void fz_epilogue(const Job<float> &jb, const float *tile, int r0, int neg, double &acc)
+{
+    constexpr int Q = NX / 4, U = 2;
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int i0 = threadIdx.x; i0 < R * Q; i0 += NT * U) {
+        float4 p[U], g[U], h[U], sb[U];
+        size_t gi[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = i0 + u * NT;
+            const int j = i / Q, x = (i % Q) * 4;
+            gi[u] = (size_t)(r0 + j) * NX + x;
+            const bool in = i < R * Q;
+            p[u] = in ? fz_ld4(tile + (size_t)j * NX + fz_swz(x)) : z4;
+            g[u] = (in && jb.g) ? fz_ld4(jb.g + gi[u]) : z4;
+            h[u] = (in && jb.h) ? fz_ld4(jb.h + gi[u]) : z4;
+            sb[u] = (in && RES) ? fz_ld4(jb.sub + gi[u]) : z4;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (i0 + u * NT < R * Q) fz_epilogue4<RES>(jb, gi[u], p[u], neg, g[u], h[u], sb[u], acc);
+    }
+}
+
+// Shared-memory bytes of a fused launch: the tile of R + 2 rows and the two
+// carry arrays (P segments x nx / 2 column pairs each).
+__host__ __device__ constexpr size_t fused_smem_bytes(int nx, int R, int P)
+{
+    return (size_t)(R + 2) * nx * sizeof(float) + 2 * (size_t)P * nx * sizeof(float);
+}
+
+
+// ---------------------------------------------------------------------------
+// Packed FP32x2 arithmetic (two independent lines per instruction).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 f2s(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+
+__device__ __forceinline__ float2 shfl2(float2 v, int src)
+{
+    return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+__device__ __forceinline__ float2 shfl_up2(float2 v, int d)
+{
+    return make_float2(__shfl_up_sync(0xffffffffu, v.x, d), __shfl_up_sync(0xffffffffu, v.y, d));
+}
+__device__ __forceinline__ float2 shfl_down2(float2 v, int d)
+{
+    return make_float2(__shfl_down_sync(0xffffffffu, v.x, d), __shfl_down_sync(0xffffffffu, v.y, d));
+}
+
+// Reaction of two values (explicit Euler substeps as in react_point, same
+// operation order; the exact flow per element).
+__device__ __forceinline__ float2 react2(float2 w, float c, int nsub)
+{
+    if (nsub < 0) return make_float2(react_point(w.x, c, nsub), react_point(w.y, c, nsub));
+    const float2 c2 = f2s(c);
+    for (int s = 0; s < nsub; ++s) {
+        const float2 w3 = mul2(mul2(w, w), w);
+        w = fma2(c2, add2(w, make_float2(-w3.x, -w3.y)), w);
+    }
+    return w;
+}
+
+// Carry scans of warp_line_solve for two lines at once (see warp_carry_fwd/bwd).
+__device__ __forceinline__ float2 warp_carry_fwd2(float2 E, const TriCoef<float> &c, int lane)
+{
+    float2 S = E;
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+        const int d = 1 << j;
+        const float2 t = shfl_up2(S, d);
+        if (lane >= d) S = fma2(f2s(c.scan[j]), t, S);
+    }
+    float2 excl = shfl_up2(S, 1);
+    if (lane == 0) excl = f2s(0.f);
+    const float2 tot = shfl2(S, 31);
+    return fma2(f2s(c.chunk_pw[lane]), mul2(tot, f2s(c.inv1m)), excl);
+}
+
+__device__ __forceinline__ float2 warp_carry_bwd2(float2 B, const TriCoef<float> &c, int lane)
+{
+    float2 S = B;
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+        const int d = 1 << j;
+        const float2 t = shfl_down2(S, d);
+        if (lane + d < 32) S = fma2(f2s(c.scan[j]), t, S);
+    }
+    float2 excl = shfl_down2(S, 1);
+    if (lane == 31) excl = f2s(0.f);
+    const float2 tot = shfl2(S, 0);
+    return fma2(f2s(c.chunk_pw[31 - lane]), mul2(tot, f2s(c.inv1m)), excl);
+}
+
+// Periodic line solve of two lines held as 32 chunks of C value pairs.
+template <int C>
+__device__ __forceinline__ void warp_line_solve2(float2 (&q)[C], const TriCoef<float> &c, int lane)
+{
+    const float2 rho = f2s(c.rho);
+    float2 z = f2s(0.f);
+#pragma unroll
+    for (int k = 0; k < C; ++k) { z = fma2(rho, z, q[k]); q[k] = z; }
+    const float2 cin = warp_carry_fwd2(z, c, lane);
+#pragma unroll
+    for (int k = 0; k < C; ++k) q[k] = fma2(f2s(c.pw[k + 1]), cin, q[k]);
+    float2 x = f2s(0.f);
+#pragma unroll
+    for (int k = C - 1; k >= 0; --k) { x = fma2(rho, x, q[k]); q[k] = x; }
+    const float2 din = warp_carry_bwd2(x, c, lane);
+#pragma unroll
+    for (int k = 0; k < C; ++k) q[k] = fma2(f2s(c.pw[C - k]), din, q[k]);
+}
+
+// C = nx / 32 values per lane in the row pass; G CTAs per cluster (state);
+// NT threads per CTA; LS rows per column segment.  Work goes in pairs: a warp
+// solves two adjacent rows at once, a thread two adjacent columns, each pair
+// with packed FP32x2 instructions.  R = ny / G rows per CTA; the column pass
+// has P = NT / (nx / 2) segments per CTA (or nx / (2 NT) column pairs per
+// thread, P = 1); R == P * LS.  cy must be built with chunk length LS.
+template <int C, int G, int NT, int LS, bool PR, bool REACT>
+__global__ void __launch_bounds__(NT) fused_sweep_kernel(const __grid_constant__ SweepArgs<float> a)
+{
+    constexpr int NW = NT / 32;
+    constexpr int NX = 32 * C;
+    constexpr int NXP = NX / 2;                 // column pairs
+    constexpr int P = NT >= NXP ? NT / NXP : 1;
+    constexpr int XPT = NT >= NXP ? 1 : NXP / NT;
+    constexpr int R = P * LS;
+    constexpr int S = G * P;                    // segments per column
+    constexpr int V = C >= 4 ? 4 : C;           // values per shared-memory access in the row pass
+    static_assert(R % (2 * NW) == 0, "rows per CTA must be a multiple of twice the warps");
+    static_assert(S <= 32, "at most 32 segments per column");
+    static_assert(LS <= kMaxChunk, "segment longer than the power table");
+
+    extern __shared__ __align__(16) unsigned char fz_smem[];
+    float *tile = reinterpret_cast<float *>(fz_smem);                       // (R + 2) rows of NX
+    float2 *ce = reinterpret_cast<float2 *>(tile + (size_t)(R + 2) * NX);   // [P][NXP] forward carries
+    float2 *cb = ce + (size_t)P * NXP;                                      // [P][NXP] backward carries
+    __shared__ double sh[32];
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int rank = G > 1 ? (int)cg::this_cluster().block_rank() : 0;
+    const int ny = a.ny;
+    const Job<float> jb = a.jobs[blockIdx.y];
+    const int r0 = rank * R;
+
+    // 1. load (with halo rows for PR) and react; tile row t = state row r0 - 1 + t.
+    //    Every 16-byte piece of the CTA's rows is requested before any arrives.
+    {
+        const int t_lo = PR ? 0 : 1, t_hi = PR ? R + 2 : R + 1;
+        const int total = (t_hi - t_lo) * NX;
+        if (!(REACT && jb.base)) {
+            for (int idx = threadIdx.x * 4; idx < total; idx += NT * 4) {
+                const int t = t_lo + idx / NX, x = idx % NX;
+                const int gy = (r0 - 1 + t + ny) % ny;
+                fz_cp_async16(tile + (size_t)t * NX + fz_swz(x), jb.in + (size_t)gy * NX + x);
+            }
+            fz_cp_async_wait_all();
+            if (REACT) {
+                // the same pieces as this thread copied: no barrier needed before
+                for (int idx = threadIdx.x * 4; idx < total; idx += NT * 4) {
+                    const int t = t_lo + idx / NX, x = idx % NX;
+                    float4 *q4 = reinterpret_cast<float4 *>(tile + (size_t)t * NX + fz_swz(x));
+                    const float4 v = *q4;
+                    const float2 lo = react2(make_float2(v.x, v.y), a.react, a.nsub);
+                    const float2 hi = react2(make_float2(v.z, v.w), a.react, a.nsub);
+                    *q4 = make_float4(lo.x, lo.y, hi.x, hi.y);
+                }
+            }
+        } else {
+            // increments around a base: both streams through registers, U pieces in flight
+            constexpr int U = 4;
+            for (int i0 = threadIdx.x * 4; i0 < total; i0 += NT * 4 * U) {
+                float4 v[U], b[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int idx = i0 + u * NT * 4;
+                    if (idx < total) {
+                        const int t = t_lo + idx / NX, x = idx % NX;
+                        const size_t go = (size_t)((r0 - 1 + t + ny) % ny) * NX + x;
+                        v[u] = fz_ld4(jb.in + go);
+                        b[u] = fz_ld4(jb.base + go);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int idx = i0 + u * NT * 4;
+                    if (idx < total) {
+                        const int t = t_lo + idx / NX, x = idx % NX;
+                        const float4 r = make_float4(react_delta(b[u].x, v[u].x, a.react, a.nsub),
+                                                     react_delta(b[u].y, v[u].y, a.react, a.nsub),
+                                                     react_delta(b[u].z, v[u].z, a.react, a.nsub),
+                                                     react_delta(b[u].w, v[u].w, a.react, a.nsub));
+                        *reinterpret_cast<float4 *>(tile + (size_t)t * NX + fz_swz(x)) = r;
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+
+    // 2. row pass: warp w takes tile rows t, t+1 with t = 1 + 2 (g NW + w);
+    //    results go to rows t-1, t (the rows above), read-before-write per group
+    const int x0 = lane * C;
+    const float2 rx0 = f2s(a.rx0), rx1 = f2s(a.rx1), cy0 = f2s(a.cy0), cy1 = f2s(a.cy1);
+#pragma unroll 1
+    for (int g = 0; g < R / (2 * NW); ++g) {
+        const int t = 1 + 2 * (g * NW + warp);
+        float2 q[C];
+#pragma unroll
+        for (int i = 0; i < C; i += V) {
+            float w1[V], w2[V];
+            fz_load<V>(tile + (size_t)t * NX, x0 + i, w1);
+            fz_load<V>(tile + (size_t)(t + 1) * NX, x0 + i, w2);
+            if constexpr (PR) {
+                float w0[V], w3[V];
+                fz_load<V>(tile + (size_t)(t - 1) * NX, x0 + i, w0);
+                fz_load<V>(tile + (size_t)(t + 2) * NX, x0 + i, w3);
+#pragma unroll
+                for (int e = 0; e < V; ++e) {
+                    const float2 s = add2(make_float2(w0[e], w1[e]), make_float2(w2[e], w3[e]));
+                    q[i + e] = fma2(rx1, s, mul2(rx0, make_float2(w1[e], w2[e])));
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < V; ++e) q[i + e] = mul2(rx0, make_float2(w1[e], w2[e]));
+            }
+        }
+        __syncthreads();   // every read of this group precedes its writes
+        warp_line_solve2<C>(q, a.cx, lane);
+        if constexpr (PR) {
+            const float2 left = shfl2(q[C - 1], (lane + 31) & 31);
+            const float2 right = shfl2(q[0], (lane + 1) & 31);
+            float2 prev = left;
+#pragma unroll
+            for (int k = 0; k < C; ++k) {
+                const float2 nxt = k < C - 1 ? q[k + 1] : right;
+                const float2 cur = q[k];
+                q[k] = fma2(cy1, add2(prev, nxt), mul2(cy0, cur));
+                prev = cur;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < C; ++k) q[k] = mul2(cy0, q[k]);
+        }
+#pragma unroll
+        for (int i = 0; i < C; i += V) {
+            float lo[V], hi[V];
+#pragma unroll
+            for (int e = 0; e < V; ++e) { lo[e] = q[i + e].x; hi[e] = q[i + e].y; }
+            fz_store<V>(tile + (size_t)(t - 1) * NX, x0 + i, lo);
+            fz_store<V>(tile + (size_t)t * NX, x0 + i, hi);
+        }
+    }
+    __syncthreads();
+
+    // 3. column pass on pairs of columns: rows [p LS, p LS + LS) of columns
+    //    (x, x + 1), global segment s = rank P + p
+    const TriCoef<float> &c = a.cy;
+    const float2 rho = f2s(c.rho), mls = f2s(c.scan[0]), inv1m = f2s(c.inv1m);
+    const int p = NT >= NXP ? threadIdx.x / NXP : 0;
+    const int xb = NT >= NXP ? threadIdx.x % NXP : threadIdx.x;
+    const int s = rank * P + p;
+    float *col0 = tile + (size_t)(p * LS) * NX;
+#pragma unroll 1
+    for (int xi = 0; xi < XPT; ++xi) {
+        const int xp = xb + xi * NT, xs = fz_swz(2 * xp);
+        float2 z = f2s(0.f);
+#pragma unroll
+        for (int k = 0; k < LS; ++k) {
+            float2 *e = reinterpret_cast<float2 *>(col0 + (size_t)k * NX + xs);
+            z = fma2(rho, z, *e);
+            *e = z;
+        }
+        ce[p * NXP + xp] = z;
+    }
+    if constexpr (G > 1) cg::this_cluster().sync(); else __syncthreads();
+#pragma unroll 1
+    for (int xi = 0; xi < XPT; ++xi) {
+        const int xp = xb + xi * NT, xs = fz_swz(2 * xp);
+        float2 tot = f2s(0.f), pre = f2s(0.f);
+#pragma unroll
+        for (int j = 0; j < S; ++j) {
+            const float2 *src = ce + (j % P) * NXP + xp;
+            if constexpr (G > 1) src = cg::this_cluster().map_shared_rank(const_cast<float2 *>(src), j / P);
+            const float2 ev = *src;
+            if (j == s) pre = tot;
+            tot = fma2(mls, tot, ev);
+        }
+        const float2 cin = fma2(f2s(c.chunk_pw[s]), mul2(tot, inv1m), pre);
+        float2 xv = f2s(0.f);
+#pragma unroll
+        for (int k = LS - 1; k >= 0; --k) {
+            float2 *el = reinterpret_cast<float2 *>(col0 + (size_t)k * NX + xs);
+            const float2 zk = fma2(f2s(c.pw[k + 1]), cin, *el);
+            xv = fma2(rho, xv, zk);
+            *el = xv;
+        }
+        cb[p * NXP + xp] = xv;
+    }
+    if constexpr (G > 1) cg::this_cluster().sync(); else __syncthreads();
+#pragma unroll 1
+    for (int xi = 0; xi < XPT; ++xi) {
+        const int xp = xb + xi * NT, xs = fz_swz(2 * xp);
+        float2 tot = f2s(0.f), pre = f2s(0.f);
+#pragma unroll
+        for (int j = S - 1; j >= 0; --j) {
+            const float2 *src = cb + (j % P) * NXP + xp;
+            if constexpr (G > 1) src = cg::this_cluster().map_shared_rank(const_cast<float2 *>(src), j / P);
+            const float2 ev = *src;
+            if (j == s) pre = tot;
+            tot = fma2(mls, tot, ev);
+        }
+        const float2 din = fma2(f2s(c.chunk_pw[S - 1 - s]), mul2(tot, inv1m), pre);
+#pragma unroll
+        for (int k = 0; k < LS; ++k) {
+            float2 *el = reinterpret_cast<float2 *>(col0 + (size_t)k * NX + xs);
+            *el = fma2(f2s(c.pw[LS - k]), din, *el);
+        }
+    }
+    // no CTA leaves (or reuses its carries) while a peer may still read them
+    if constexpr (G > 1) cg::this_cluster().sync(); else __syncthreads();
+
+    // 4. epilogue: tile row j = state row r0 + j
+    double acc = 0.0;
+    if (!jb.g && !jb.h && !jb.sub && jb.out) {
+        // plain store of (+-)Phi
+        constexpr int Q = NX / 4;
+        for (int i = threadIdx.x; i < R * Q; i += NT) {
+            const int j = i / Q, x = (i % Q) * 4;
+            float4 v = fz_ld4(tile + (size_t)j * NX + fz_swz(x));
+            if (a.neg) v = make_float4(-v.x, -v.y, -v.z, -v.w);
+            *reinterpret_cast<float4 *>(jb.out + (size_t)(r0 + j) * NX + x) = v;
+        }
+    } else if (jb.sub) {
+        fz_epilogue<NX, R, NT, true>(jb, tile, r0, a.neg, acc);
+    } else {
+        fz_epilogue<NX, R, NT, false>(jb, tile, r0, a.neg, acc);
+    }
+    if (a.partials) {
+        const double tsum = block_sum(acc, sh);
+        if (threadIdx.x == 0) a.partials[(size_t)blockIdx.y * G + rank] = tsum;
+    }
+}
+
+}  // namespace atm

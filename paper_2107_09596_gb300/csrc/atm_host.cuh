@@ -14,6 +14,7 @@
 #include "../../include/atm.h"
 #include "atm_common.cuh"
 #include "atm_kernels.cuh"
+#include "atm_fused.h"
 #include "atm_nn.h"
 
 namespace atm {
@@ -122,6 +123,39 @@ inline SweepFn<T> col_kernel(int CY, int W, bool pr)
     return nullptr;
 }
 
+// One launch shape of the fused whole-propagator kernel (FP32, 2D): G CTAs
+// of NT threads per state, LS rows per column segment, and the column-line
+// coefficients built for that segment length.
+template <typename T>
+struct FusedVariant {
+    SweepFn<T> fn = nullptr;
+    int G = 1, NT = 256, LS = 16;
+    size_t smem = 0;
+    TriCoef<T> cy{};
+};
+
+// Fused launch shapes for an nx x ny grid (none in FP64, whose sweeps are
+// bound by the FP64 pipe, not by the intermediate's traffic).  The first
+// entry is the default; the level-0 autotuner times them all.
+template <typename T>
+inline std::vector<FusedVariant<T>> fused_variants(int nx, int ny, bool pr, bool react, double ay)
+{
+    std::vector<FusedVariant<T>> v;
+    if constexpr (sizeof(T) == 4) {
+        for (const FusedShape &f : fused_shapes(nx, ny, pr, react)) {
+            FusedVariant<T> fv;
+            fv.fn = f.fn;
+            fv.G = f.G;
+            fv.NT = f.NT;
+            fv.LS = f.LS;
+            fv.smem = f.smem;
+            fv.cy = to_coef<T>(make_line(ay, ny, true, f.LS), nullptr);
+            v.push_back(fv);
+        }
+    }
+    return v;
+}
+
 }  // namespace atm
 
 namespace atm {
@@ -135,6 +169,7 @@ struct LevelOp {
     size_t row_smem = 0;
     std::vector<double> dir_w;   // 1D: Dirichlet rank-one vector (host copy)
     bool learned = false;        // the level's propagator is the learned Psi_NN
+    std::vector<FusedVariant<T>> fused;   // fused whole-propagator launch shapes (may be empty)
 };
 
 // Build the level-l propagator of (pb, sv): step D = dt * m_0 * .. * m_{l-1};
@@ -213,6 +248,7 @@ inline LevelOp<T> make_level_op(const atm_problem &pb, const atm_solver &sv, int
     // padded tile rows: 16 bytes after every 128 bytes (see row_sweep_kernel)
     const size_t pitch = (size_t)pb.nx + (size_t)(pb.nx * sizeof(T) / 128) * (16 / sizeof(T));
     op.row_smem = pr ? (size_t)(op.rows_per_cta + 2) * pitch * sizeof(T) : 0;
+    if (sv.sweep_kernel != ATM_SWEEP_SPLIT) op.fused = fused_variants<T>(pb.nx, pb.ny, pr, react, ay);
     return op;
 }
 
@@ -259,6 +295,7 @@ struct PlanBase {
     // after the graph ran, collect the result
     virtual atm_status add_loop(cudaGraph_t g) = 0;
     virtual atm_status loop_result(atm_result *res) = 0;
+    virtual atm_status sweep_config(int level, int *cfg) const = 0;
 };
 
 template <typename T>
@@ -273,6 +310,8 @@ struct Level {
     std::vector<double> dir_w_host;
     bool learned = false;
     LevelOp<T> classical;        // learned level: the split-BE ADI operator used after a fallback
+    std::vector<FusedVariant<T>> fused;   // fused launch shapes available on this level
+    int fz = -1;                 // selected fused shape (-1: split row/column kernels)
 };
 
 inline bool pow2_in(int v, int lo, int hi)
@@ -454,6 +493,10 @@ struct Plan : PlanBase {
         Lv.row_smem = op.row_smem;
         Lv.dir_w_host = op.dir_w;
         Lv.learned = op.learned;
+        Lv.fused = op.fused;
+        // fused on coarse levels by default, and on level 0 when asked for
+        // (ATM_SWEEP_AUTO lets the autotuner decide level 0 at create time)
+        Lv.fz = (!Lv.fused.empty() && (l > 0 || sv.sweep_kernel == ATM_SWEEP_FUSED)) ? 0 : -1;
     }
 
     // ---------------- phase builders ----------------
@@ -461,7 +504,15 @@ struct Plan : PlanBase {
     {
         if (is1d) return 1;
         if (l < (int)lv.size() && lv[l].learned) return pb.nx * pb.ny / nn::kNNTile;
+        if (l < (int)lv.size() && lv[l].fz >= 0) return lv[l].fused[lv[l].fz].G;
         return pb.nx / 32;
+    }
+
+    // Partial sums written per job: the largest over the kernels a level may use.
+    int max_blocks_per_job(int l) const
+    {
+        const int b = blocks_per_job(l);
+        return (is1d || b >= pb.nx / 32) ? b : pb.nx / 32;
     }
 
     void add_sweep(Phase &ph, int l, std::vector<Job<T>> &&js, int neg, bool norm)
@@ -475,7 +526,7 @@ struct Plan : PlanBase {
         r.neg = neg;
         if (norm) {
             r.partials = partials;
-            r.npartials = r.njobs * blocks_per_job(l);
+            r.npartials = r.njobs * max_blocks_per_job(l);
             if (r.npartials > npartials_max) npartials_max = r.npartials;
         }
         if (r.njobs > maxbatch) maxbatch = r.njobs;
@@ -494,12 +545,16 @@ struct Plan : PlanBase {
         ph.push_back(r);
     }
 
-    void add_norm(Phase &ph, int count)
+    // Norm of the residual of the preceding sweep of njobs states on level l
+    // (the partial count follows the kernel the level uses at launch time).
+    void add_norm(Phase &ph, int l, int njobs)
     {
         LaunchRec r;
         r.type = L_NORM;
+        r.level = l;
+        r.njobs = njobs;
         r.partials = partials;
-        r.npartials = count;
+        r.npartials = njobs * max_blocks_per_job(l);
         r.norm_out = norm_cur;
         ph.push_back(r);
     }
@@ -550,13 +605,17 @@ struct Plan : PlanBase {
                 if (t < N && (!c0 || full_interval(i)))
                     js.push_back(job(up(l, t - 1), up(l, t), gl(l, t), nullptr, nullptr, nullptr, bp(l, t - 1)));
             }
+            add_sweep(ph, l, std::move(js), 0, false);
             if (c0 && bwork) {
-                // advance the base chain after every increment of this step has read it
+                // advance the base chain once every increment of this step has
+                // read it (a launch of its own: within a launch of the fused
+                // kernel, states are not ordered against each other)
+                std::vector<Job<T>> bs;
                 for (int i = 0; i < NC; ++i)
                     if (full_interval(i))
-                        js.push_back(job(j == 1 ? st_ptr(ubase, i) : st_ptr(bwork, i), st_ptr(bwork, i)));
+                        bs.push_back(job(j == 1 ? st_ptr(ubase, i) : st_ptr(bwork, i), st_ptr(bwork, i)));
+                add_sweep(ph, l, std::move(bs), 0, false);
             }
-            add_sweep(ph, l, std::move(js), 0, false);
         }
         if (resid) {
             std::vector<Job<T>> js;
@@ -567,7 +626,7 @@ struct Plan : PlanBase {
             }
             const int n = (int)js.size();
             add_sweep(ph, l, std::move(js), 0, norm);
-            if (norm) add_norm(ph, n * blocks_per_job(l));
+            if (norm) add_norm(ph, l, n);
         }
     }
 
@@ -696,7 +755,7 @@ struct Plan : PlanBase {
                                  st_ptr(r_full, i)));
             const int n = (int)js.size();
             add_sweep(resid_full, 0, std::move(js), 0, true);
-            add_norm(resid_full, n * blocks_per_job(0));
+            add_norm(resid_full, 0, n);
             add_regen_jobs();
             return;
         }
@@ -708,7 +767,7 @@ struct Plan : PlanBase {
                                  st_ptr(r_full, j)));
             const int n = (int)js.size();
             add_sweep(resid_full, 0, std::move(js), 0, true);
-            add_norm(resid_full, n * blocks_per_job(0));
+            add_norm(resid_full, 0, n);
             return;
         }
         if (role == ROLE_INNER) {
@@ -870,7 +929,7 @@ struct Plan : PlanBase {
         long long n = 0;
         for (const LaunchRec &r : ph) {
             if (r.type != L_SWEEP || is1d) n += 1;
-            else if (lv[r.level].learned) n += sweep_pairs(r.level, r.njobs);
+            else if (lv[r.level].learned || lv[r.level].fz >= 0) n += sweep_pairs(r.level, r.njobs);
             else n += 2 * sweep_pairs(r.level, r.njobs);
         }
         return n;
@@ -909,6 +968,34 @@ struct Plan : PlanBase {
             if (prof) cudaEventRecordWithFlags(pev[4 * slot + 3], st, cudaEventRecordExternal);
             return;
         }
+        if (Lv.fz >= 0) {
+            const FusedVariant<T> &fv = Lv.fused[Lv.fz];
+            a.cy = fv.cy;
+            for (int j0 = 0; j0 < njobs; j0 += 32768) {
+                const int nj = njobs - j0 < 32768 ? njobs - j0 : 32768;
+                a.jobs = djobs + j0;
+                a.partials = part ? part + (size_t)j0 * fv.G : nullptr;
+                cudaLaunchConfig_t cfg = {};
+                cfg.gridDim = dim3(fv.G, nj);
+                cfg.blockDim = dim3(fv.NT);
+                cfg.dynamicSmemBytes = fv.smem;
+                cfg.stream = st;
+                cudaLaunchAttribute at[1];
+                at[0].id = cudaLaunchAttributeClusterDimension;
+                at[0].val.clusterDim.x = fv.G;
+                at[0].val.clusterDim.y = 1;
+                at[0].val.clusterDim.z = 1;
+                cfg.attrs = at;
+                cfg.numAttrs = 1;
+                if (cudaLaunchKernelEx(&cfg, fv.fn, a) != cudaSuccess) launch_failed = true;
+            }
+            if (prof) {
+                cudaEventRecordWithFlags(pev[4 * slot + 1], st, cudaEventRecordExternal);
+                cudaEventRecordWithFlags(pev[4 * slot + 2], st, cudaEventRecordExternal);
+                cudaEventRecordWithFlags(pev[4 * slot + 3], st, cudaEventRecordExternal);
+            }
+            return;
+        }
         const int cs = chunk_size(l, njobs);
         const bool split = cs == njobs;
         for (int j0 = 0; j0 < njobs; j0 += cs) {
@@ -933,6 +1020,7 @@ struct Plan : PlanBase {
             const int ch = maxbatch < nn::kInferChunk ? maxbatch : nn::kInferChunk;
             return 5 * ((njobs + ch - 1) / ch);   // counted as kernels / 2 by kernels_in
         }
+        if (lv[l].fz >= 0) return (njobs + 32767) / 32768;   // counted once by kernels_in
         const int cs = chunk_size(l, njobs);
         return (njobs + cs - 1) / cs;
     }
@@ -963,6 +1051,8 @@ struct Plan : PlanBase {
     // from where a real cycle finds them) for each candidate, with CUDA events
     // over 2 repetitions after a warm-up, and keeps the fastest.  Runs on the
     // state present at create time (zero), for which the sweeps write zeros.
+    // The same timing also chooses, with ATM_SWEEP_AUTO, between the split
+    // row/column kernels (each chunk size) and each fused launch shape.
     atm_status autotune_chunk(const Phase &ph)
     {
         std::vector<const LaunchRec *> recs;
@@ -973,16 +1063,29 @@ struct Plan : PlanBase {
                 if (r.njobs > maxjobs) maxjobs = r.njobs;
             }
         chunk = 0;
-        if (is1d || recs.empty() || maxjobs <= 64) return ATM_OK;
-        const int cands[] = {0, 64, 128, 256, 512};
+        if (is1d || recs.empty() || lv[0].learned) return ATM_OK;
+        struct Cand { int fz, chunk; };
+        std::vector<Cand> cands;
+        const bool tune_fz = sv.sweep_kernel == ATM_SWEEP_AUTO && !lv[0].fused.empty();
+        if (lv[0].fz < 0 || tune_fz) {
+            cands.push_back({-1, 0});
+            if (maxjobs > 64)
+                for (int c : {64, 128, 256, 512})
+                    if (c < maxjobs) cands.push_back({-1, c});
+        }
+        if (tune_fz)
+            for (int k = 0; k < (int)lv[0].fused.size(); ++k) cands.push_back({k, 0});
+        if (cands.empty()) return ATM_OK;   // fused shape fixed by the caller
         float best = 1e30f;
-        int best_c = 0;
+        Cand bc = cands[0];
         cudaEvent_t e0, e1;
         ATM_CK(cudaEventCreate(&e0));
         ATM_CK(cudaEventCreate(&e1));
-        for (int c : cands) {
-            if (c >= maxjobs) continue;
-            chunk = c;
+        for (const Cand &cd : cands) {
+            if (cands.size() == 1) break;
+            lv[0].fz = cd.fz;
+            chunk = cd.chunk;
+            launch_failed = false;
             for (const LaunchRec *r : recs)
                 launch_sweep(0, d_jobs + r->job_index, r->njobs, r->neg, r->partials);
             cudaEventRecord(e0, st);
@@ -993,13 +1096,54 @@ struct Plan : PlanBase {
             cudaEventSynchronize(e1);
             float ms = 0;
             cudaEventElapsedTime(&ms, e0, e1);
-            if (ms < best) { best = ms; best_c = c; }
+            if (launch_failed) {   // a launch shape the device cannot schedule
+                launch_failed = false;
+                cudaGetLastError();
+                continue;
+            }
+            if (ms < best) { best = ms; bc = cd; }
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
-        chunk = best_c;
-        tuned_ms = best / 2;
+        lv[0].fz = bc.fz;
+        chunk = bc.chunk;
+        tuned_ms = best < 1e30f ? best / 2 : 0.f;
         ATM_CK(cudaGetLastError());
+        return ATM_OK;
+    }
+
+    // Shared-memory and cluster-size attributes of the fused kernels; shapes
+    // that cannot be resident on this device are dropped.
+    atm_status prepare_fused(int l)
+    {
+        Level<T> &Lv = lv[l];
+        std::vector<FusedVariant<T>> keep;
+        for (const FusedVariant<T> &fv : Lv.fused) {
+            ATM_CK(cudaFuncSetAttribute((const void *)fv.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fv.smem));
+            // the whole unified L1/shared array as shared memory: room for 3 CTAs of ~70 KB
+            ATM_CK(cudaFuncSetAttribute((const void *)fv.fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+            if (fv.G > 8) ATM_CK(cudaFuncSetAttribute((const void *)fv.fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(fv.G, 1);
+            cfg.blockDim = dim3(fv.NT);
+            cfg.dynamicSmemBytes = fv.smem;
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = fv.G;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            int nclusters = 0;
+            if (cudaOccupancyMaxActiveClusters(&nclusters, (const void *)fv.fn, &cfg) != cudaSuccess) {
+                cudaGetLastError();
+                nclusters = 0;
+            }
+            if (nclusters > 0) keep.push_back(fv);
+        }
+        const bool was = Lv.fz >= 0;
+        Lv.fused = keep;
+        Lv.fz = (was && !keep.empty()) ? 0 : -1;
         return ATM_OK;
     }
 
@@ -1018,7 +1162,8 @@ struct Plan : PlanBase {
             else if (r.type == L_AXPY)
                 launch_axpy(d_ajobs + r.job_index, r.njobs);
             else
-                norm_finalize_kernel<<<1, 1024, 0, st>>>(r.partials, r.npartials, r.norm_out, nullptr);
+                norm_finalize_kernel<<<1, 1024, 0, st>>>(r.partials, r.njobs * blocks_per_job(r.level), r.norm_out,
+                                                         nullptr);
         }
     }
 
@@ -1058,6 +1203,7 @@ struct Plan : PlanBase {
         }
         for (int l = 0; l < L; ++l) {
             if (lv[l].learned) continue;
+            ATM_TRY(prepare_fused(l));
             if (lv[l].row_smem > 48 * 1024)
                 ATM_CK(cudaFuncSetAttribute((const void *)lv[l].row, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)lv[l].row_smem));
@@ -1522,6 +1668,25 @@ struct Plan : PlanBase {
 
     int level_points(int level) const override { return (level >= 0 && level < L) ? lv[level].N : -1; }
 
+    atm_status sweep_config(int level, int *cfg) const override
+    {
+        if (level < 0 || level >= L) return fail(ATM_ERR_INVALID_ARG, "level %d out of range", level);
+        const Level<T> &Lv = lv[level];
+        for (int i = 0; i < 5; ++i) cfg[i] = 0;
+        if (is1d) {
+            cfg[0] = 3; cfg[1] = 1; cfg[2] = 32;
+        } else if (Lv.learned) {
+            cfg[0] = 2;
+        } else if (Lv.fz >= 0) {
+            const FusedVariant<T> &f = Lv.fused[Lv.fz];
+            cfg[0] = 1; cfg[1] = f.G; cfg[2] = f.NT; cfg[3] = f.LS;
+        } else {
+            cfg[0] = 0; cfg[1] = pb.nx / 32; cfg[2] = 32 * Lv.col_warps; cfg[3] = Lv.col_chunk;
+            cfg[4] = level == 0 ? chunk : 0;
+        }
+        return ATM_OK;
+    }
+
     atm_status zero_guess() override
     {
         ATM_CK(cudaMemsetAsync(st_ptr(lv[0].u, 1), 0, (size_t)(ustates() - 1) * nsp * sizeof(T), st));
@@ -1747,6 +1912,7 @@ struct RefinedPlan : PlanBase {
         return inner.level_io(level, array, t0, count, buf, write);
     }
     int level_points(int level) const override { return inner.level_points(level); }
+    atm_status sweep_config(int level, int *cfg) const override { return inner.sweep_config(level, cfg); }
 };
 
 }  // namespace atm

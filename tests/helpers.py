@@ -13,7 +13,8 @@ KIND = {"heat1d": (oracle.HEAT1D, atm.HEAT1D), "heat2d": (oracle.HEAT2D, atm.HEA
 def pair(kind="heat1d", nx=127, ny=1, lx=1.0, ly=1.0, dt=1.0 / 1024, nt=1025, eps=0.02,
          m=(8,), k=4, nu=1, algorithm="at", fine_prop=atm.PROP_PR_ADI,
          coarse_prop=atm.PROP_SPLIT_BE, react_sub=None, coarse_reaction=atm.REACT_EXACT,
-         precision=atm.FP64, tol=0.0, max_iter=10, use_graph=True, cpoint_only=False):
+         precision=atm.FP64, tol=0.0, max_iter=10, use_graph=True, cpoint_only=False,
+         sweep_kernel=atm.SWEEP_AUTO):
     ok, gk = KIND[kind]
     L = len(m) + 1
     prop = [fine_prop if l == 0 else coarse_prop for l in range(L)]
@@ -27,7 +28,8 @@ def pair(kind="heat1d", nx=127, ny=1, lx=1.0, ly=1.0, dt=1.0 / 1024, nt=1025, ep
     gs = atm.make_solver(alg, m=m, k=k, nu=nu, fine_prop=fine_prop, coarse_prop=coarse_prop,
                          reaction_substeps=react_sub, coarse_reaction=coarse_reaction,
                          tol=tol, max_iter=max_iter,
-                         precision=precision, use_graph=use_graph, cpoint_only=cpoint_only)
+                         precision=precision, use_graph=use_graph, cpoint_only=cpoint_only,
+                         sweep_kernel=sweep_kernel)
     return oc, gp, gs
 
 
