@@ -98,3 +98,19 @@ def batch_problem_draws(count: int, seed: int = 0):
             "seed": i,
         })
     return out
+
+
+def conv_net_init(seed: int = 0, channels=(1, 32, 32, 32, 32, 1)):
+    """Seeded initial weights of a stack of 3x3 convolutions: layer l draws
+    uniform(-b, b) with b = sqrt(6 / (9 c_in)) (He-style), the last layer scaled
+    by 0.1 so that u + N(u) starts near the identity; biases zero.  Returns a
+    list of (w [c_out][c_in][3][3], b [c_out]) float64 arrays."""
+    params = []
+    for li in range(len(channels) - 1):
+        ci, co = channels[li], channels[li + 1]
+        bound = np.sqrt(6.0 / (9 * ci))
+        if li == len(channels) - 2:
+            bound *= 0.1
+        w = (2 * uniform01(seed + li, co * ci * 9) - 1).reshape(co, ci, 3, 3) * bound
+        params.append((w, np.zeros(co)))
+    return params

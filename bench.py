@@ -246,7 +246,6 @@ def train_learned(atm, w, device, steps, seeds=(101, 102, 103, 104, 105), batch=
     of fine trajectories from other seeds, produced by the library's sequential
     stepping (the states that F-relaxation generates at convergence), then Adam."""
     import torch
-    from oracle import nn as onn   # parameter initialisation only (seeded draws)
     m0 = w["m"][0]
     prob, desc = make_desc(atm, w, "seq", atm.FP32, profile=False)
     seq = atm.Solver(prob, desc, device=device)
@@ -263,7 +262,7 @@ def train_learned(atm, w, device, steps, seeds=(101, 102, 103, 104, 105), batch=
     targets = torch.cat(outs).contiguous()
     del ins, outs
     net = atm.LearnedCoarse(device=device)
-    flat = np.concatenate([np.concatenate([wt.ravel(), b.ravel()]) for (wt, b) in onn.init_params(7)])
+    flat = np.concatenate([np.concatenate([wt.ravel(), b.ravel()]) for (wt, b) in I.conv_net_init(7)])
     params = torch.as_tensor(flat, dtype=torch.float32, device=device)
     adam = torch.zeros(2 * net.nparams, dtype=torch.float32, device=device)
     perm = torch.randperm(inputs.shape[0], generator=torch.Generator().manual_seed(0)).to(device)

@@ -58,21 +58,11 @@ def gelu_grad(z):
 
 
 def init_params(seed: int = 0, channels=CHANNELS):
-    """He-style uniform init from the shared splitmix64 stream; last layer scaled
-    by 0.1 so that Psi_NN starts near the identity."""
+    """Seeded initial parameters (the shared draw of atm_inputs.conv_net_init:
+    He-style uniform, last layer scaled by 0.1 so that Psi_NN starts near the
+    identity)."""
     import atm_inputs as I
-    params = []
-    s = seed
-    for li in range(len(channels) - 1):
-        ci, co = channels[li], channels[li + 1]
-        bound = math.sqrt(6.0 / (9 * ci))
-        if li == len(channels) - 2:
-            bound *= 0.1
-        w = (2 * I.uniform01(s, co * ci * 9) - 1).reshape(co, ci, 3, 3) * bound
-        b = np.zeros(co)
-        params.append((w, b))
-        s += 1
-    return params
+    return I.conv_net_init(seed, channels)
 
 
 def forward(params, u):
