@@ -124,9 +124,11 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def kernel_source_hash():
-    """Hash of the sweep kernels' source: stored ncu traffic is used only while it matches."""
-    with open(os.path.join(ROOT, "paper_2107_09596_gb300", "csrc", "atm_kernels.cuh"), "rb") as fh:
+def kernel_source_hash(fused=False):
+    """Hash of the timed kernel's source (the split sweep kernels, or the fused
+    kernel): stored ncu traffic is used only while it matches."""
+    name = "atm_fused.cuh" if fused else "atm_kernels.cuh"
+    with open(os.path.join(ROOT, "paper_2107_09596_gb300", "csrc", name), "rb") as fh:
         return hashlib.md5(fh.read()).hexdigest()[:12]
 
 
@@ -273,7 +275,8 @@ def train_learned(atm, w, device, steps, seeds=(101, 102, 103, 104, 105), batch=
                     "train_ms": res["time_ms"]}
 
 
-def make_desc(atm, w, algorithm, precision, profile, coarse="classical", sweep="auto", cpoint=False):
+def make_desc(atm, w, algorithm, precision, profile, coarse="classical", sweep="auto", cpoint=False,
+              inner_cycles=0):
     kind = {"ac": atm.ALLEN_CAHN, "heat1d": atm.HEAT1D}[w["kind"]]
     ny = w["n"] if w["kind"] != "heat1d" else 1
     prob = atm.make_problem(kind, w["n"], ny, dt=w["dt"], nt_points=w["nt"], eps=w["eps"])
@@ -284,7 +287,7 @@ def make_desc(atm, w, algorithm, precision, profile, coarse="classical", sweep="
                            coarse_prop=atm.PROP_LEARNED if coarse == "learned" else atm.PROP_SPLIT_BE,
                            sweep_kernel={"auto": atm.SWEEP_AUTO, "split": atm.SWEEP_SPLIT,
                                          "fused": atm.SWEEP_FUSED}[sweep],
-                           cpoint_only=cpoint)
+                           cpoint_only=cpoint, inner_cycles=inner_cycles)
     return prob, desc
 
 
@@ -294,10 +297,18 @@ def initial_condition(w, seed):
     return I.uniform_field((w["n"], w["n"]), seed)
 
 
+def oracle_cycles(workload, fallback):
+    """The oracle's own cycle count to the workload's tolerance (FP64 AT-MGRIT,
+    written by oracle/make_golden.py)."""
+    gold = load_json(os.path.join(ROOT, "tests", "golden", "oracle_histories.json"), {}) or {}
+    key = {"allen_cahn_256": "cfg2_at_k8", "heat1d_127": "cfg1_at_k4"}.get(workload)
+    return gold.get(key, {}).get("iterations", fallback)
+
+
 def oracle_cycle_sample(w, iterations):
     """CPU baseline: the oracle (as it stands) runs the initial F-relaxation and
-    one V-cycle of the same workload; time-to-solution is scaled to the cycles
-    the solve needs (equal to the GPU's by parity)."""
+    one V-cycle of the same workload; time-to-solution is scaled to the oracle's
+    own FP64 cycle count."""
     import oracle
     kind = {"ac": oracle.ALLEN_CAHN, "heat1d": oracle.HEAT1D}[w["kind"]]
     ny = w["n"] if w["kind"] != "heat1d" else 1
@@ -320,9 +331,7 @@ def run_reference(args, w, world, rank, dist):
     if rank != 0:
         return
     import oracle
-    gold = load_json(os.path.join(ROOT, "tests", "golden", "oracle_histories.json"), {}) or {}
-    key = {"allen_cahn_256": "cfg2_at_k8", "heat1d_127": "cfg1_at_k4"}[args.workload]
-    iters = gold.get(key, {}).get("iterations", 13)
+    iters = oracle_cycles(args.workload, 13)
     kind = {"ac": oracle.ALLEN_CAHN, "heat1d": oracle.HEAT1D}[w["kind"]]
     ny = w["n"] if w["kind"] != "heat1d" else 1
     c = oracle.make_cfg(kind, w["n"], ny, dt=w["dt"], nt=w["nt"], eps=w["eps"], m=w["m"],
@@ -371,7 +380,10 @@ def main():
     ap.add_argument("--train-steps", type=int, default=2500)
     ap.add_argument("--sweep-kernel", choices=["auto", "split", "fused"], default="auto",
                     help="2D propagator kernels (auto: level 0 autotuned at create time)")
-    ap.add_argument("--cpoint", action="store_true", help="C-point-only storage on level 0")
+    ap.add_argument("--storage", choices=["cpoint", "full"], default="cpoint",
+                    help="level-0 storage: C-points only (default) or every time point")
+    ap.add_argument("--inner-cycles", type=int, default=0,
+                    help="fp32r: FP32 V-cycles per FP64 refinement step (0: the library default, 3)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.workload == "batch64":
@@ -395,7 +407,8 @@ def main():
     if args.coarse == "learned":
         nn_params, learned_info = train_learned(atm, w, device, args.train_steps)
     prob, desc = make_desc(atm, w, args.algorithm, prec, profile=True, coarse=args.coarse,
-                           sweep=args.sweep_kernel, cpoint=args.cpoint)
+                           sweep=args.sweep_kernel, cpoint=args.storage == "cpoint",
+                           inner_cycles=args.inner_cycles)
     solver = atm.Solver(prob, desc, device=device)
     if args.coarse == "learned":
         solver.set_learned_coarse(nn_params)
@@ -461,7 +474,7 @@ def main():
     # every interval; in the refined mode the profiled table is the FP64
     # residual of every time point
     jobs = {"allen_cahn_256": 256, "heat1d_127": 128}[args.workload]
-    if args.precision == "fp32r":
+    if args.precision == "fp32r" and args.storage == "full":
         jobs = w["nt"] - 1
     if args.algorithm == "seq":
         jobs = 1
@@ -486,8 +499,9 @@ def main():
     else:
         fpv = FLOPS_PER_VALUE[("row", "pr_react")] + FLOPS_PER_VALUE[("col", "pr")]
     traffic_db = load_json(os.path.join(ROOT, "profiles", "traffic.json"), {}) or {}
-    tr = traffic_db.get(f"{args.workload}:{args.precision}")
-    traffic = tr["bytes_per_launch"] if tr and tr.get("source_hash") == kernel_source_hash() else None
+    tr = traffic_db.get(f"{args.workload}:{args.precision}:{args.storage}")
+    traffic = (tr["bytes_per_launch"] if tr and tr.get("source_hash") == kernel_source_hash(sc["kernel"] == "fused")
+               else None)
     if args.precision in ("fp64", "fp32r"):
         flops = fpv * n_val * jobs
         achieved = flops / (avg_ms / 1e3) / 1e12
@@ -508,7 +522,7 @@ def main():
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
-            cpu = oracle_cycle_sample(w, int(np.median(iters)))
+            cpu = oracle_cycle_sample(w, oracle_cycles(args.workload, int(np.median(iters))))
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -517,8 +531,11 @@ def main():
                 "config": {"workload": args.workload,
                            **{k: (list(v) if isinstance(v, tuple) else v) for k, v in w.items()},
                            "algorithm": args.algorithm, "parallelism": f"{world} independent problems",
-                           "l2": "inputs larger than L2 (space-time array %.2f GB)" % (
-                               w["nt"] * n_val * (8 if args.precision == "fp64" else 4) / 1e9)},
+                           "sweep_kernel": args.sweep_kernel, "storage": args.storage,
+                           "inner_cycles": (args.inner_cycles or 3) if args.precision == "fp32r" else None,
+                           "l2": "working set larger than L2 (workspace %.2f GB; one level-0 launch reads and "
+                                 "writes %.0f MB)" % (atm.workspace_size(prob, desc) / 1e9,
+                                                      2 * jobs * n_val * (4 if args.precision == "fp32" else 8) / 1e6)},
                 "iterations": int(np.median(iters)), "time_to_solution_ms": ms,
                 "final_residual": float(res["final_residual"]),
                 "e2e": {"value": world * (w["nt"] - 1) / (e2e_ms / 1e3), "unit": UNIT,
@@ -529,6 +546,8 @@ def main():
                 "learned": None if learned_info is None else dict(
                     learned_info, fallback_in_timed_steps=sum(f for f, _ in fallbacks),
                     cycles_with_network_before_fallback=[i for _, i in fallbacks]),
+                "kernels_per_level": [solver.sweep_config(l) for l in range(len(w["m"]) + 1)]
+                if args.algorithm != "seq" else [solver.sweep_config(0)],
                 "roofline": roof, "cpu_baseline": cpu, "clocks": clk}
         print(json.dumps(line), flush=True)
     solver.close()

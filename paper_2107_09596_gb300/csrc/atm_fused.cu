@@ -31,18 +31,21 @@ std::vector<FusedShape> fused_shapes(int nx, int ny, bool pr, bool react)
         add_shape<2, 1, 256, 8>(v, pr, react);
         add_shape<2, 1, 512, 4>(v, pr, react);
         add_shape<2, 2, 256, 4>(v, pr, react);
+        add_shape<2, 4, 256, 2>(v, pr, react);
     }
     if (nx == 128 && ny == 128) {
         add_shape<4, 2, 256, 16>(v, pr, react);
         add_shape<4, 1, 256, 32>(v, pr, react);
         add_shape<4, 2, 512, 8>(v, pr, react);
         add_shape<4, 4, 256, 8>(v, pr, react);
+        add_shape<4, 8, 256, 4>(v, pr, react);
     }
     if (nx == 256 && ny == 256) {
         add_shape<8, 4, 256, 32>(v, pr, react);
         add_shape<8, 2, 512, 32>(v, pr, react);
         add_shape<8, 8, 256, 16>(v, pr, react);
         add_shape<8, 4, 512, 16>(v, pr, react);
+        add_shape<8, 16, 256, 8>(v, pr, react);
     }
     if (nx == 512 && ny == 512) {
         add_shape<16, 16, 256, 32>(v, pr, react);

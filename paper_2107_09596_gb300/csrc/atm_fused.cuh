@@ -101,38 +101,56 @@ __device__ __forceinline__ void fz_epilogue4(const Job<float> &jb, size_t idx, f
     if (jb.out) *reinterpret_cast<float4 *>(jb.out + idx) = v;
 }
 
-// Epilogue over the CTA's R rows in batches of U vectors per thread, every
-// load of a batch issued before its first use.
-template <int NX, int R, int NT, bool RES>
-__device__ __forceinline__ void fz_epilogue(const Job<float> &jb, const float *tile, int r0, int neg, double &acc)
+// Final value of 4 consecutive columns px..px+3 of tile row j: the stored
+// backward recurrence plus rho^(LS-k) times the segment's backward carry.
+template <int NX, int NXP, int LS>
+__device__ __forceinline__ float4 fz_col_final(const float *tile, const float2 *dn, const TriCoef<float> &c, int j,
+                                               int px, int pxs)
 {
-    constexpr int Q = NX / 4, U = 2;
+    const int p = j / LS, k = j % LS;
+    const float4 v = fz_ld4(tile + (size_t)j * NX + pxs);
+    const float4 d = *reinterpret_cast<const float4 *>(dn + p * NXP + px / 2);
+    const float2 w = make_float2(c.pw[LS - k], c.pw[LS - k]);
+    const float2 lo = __ffma2_rn(w, make_float2(d.x, d.y), make_float2(v.x, v.y));
+    const float2 hi = __ffma2_rn(w, make_float2(d.z, d.w), make_float2(v.z, v.w));
+    return make_float4(lo.x, lo.y, hi.x, hi.y);
+}
+
+// Epilogue over the CTA's R rows (this thread: columns px..px+3 of rows
+// prow, prow + RPI, ...) in batches of U rows, every load of a batch issued
+// before its first use.
+template <int NX, int NXP, int R, int LS, int RPI, bool RES>
+__device__ __forceinline__ void fz_epilogue(const Job<float> &jb, const float *tile, const float2 *dn,
+                                            const TriCoef<float> &c, int r0, int prow, int px, int pxs, int neg,
+                                            double &acc)
+{
+    constexpr int U = 2;
     const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int i0 = threadIdx.x; i0 < R * Q; i0 += NT * U) {
+    for (int j0 = prow; j0 < R; j0 += RPI * U) {
         float4 p[U], g[U], h[U], sb[U];
         size_t gi[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            const int i = i0 + u * NT;
-            const int j = i / Q, x = (i % Q) * 4;
-            gi[u] = (size_t)(r0 + j) * NX + x;
-            const bool in = i < R * Q;
-            p[u] = in ? fz_ld4(tile + (size_t)j * NX + fz_swz(x)) : z4;
+            const int j = j0 + u * RPI;
+            const bool in = j < R;
+            gi[u] = (size_t)(r0 + j) * NX + px;
+            p[u] = in ? fz_col_final<NX, NXP, LS>(tile, dn, c, j, px, pxs) : z4;
             g[u] = (in && jb.g) ? fz_ld4(jb.g + gi[u]) : z4;
             h[u] = (in && jb.h) ? fz_ld4(jb.h + gi[u]) : z4;
             sb[u] = (in && RES) ? fz_ld4(jb.sub + gi[u]) : z4;
         }
 #pragma unroll
         for (int u = 0; u < U; ++u)
-            if (i0 + u * NT < R * Q) fz_epilogue4<RES>(jb, gi[u], p[u], neg, g[u], h[u], sb[u], acc);
+            if (j0 + u * RPI < R) fz_epilogue4<RES>(jb, gi[u], p[u], neg, g[u], h[u], sb[u], acc);
     }
 }
 
 // Shared-memory bytes of a fused launch: the tile of R + 2 rows and the two
-// carry arrays (P segments x nx / 2 column pairs each).
+// carry arrays and the final backward carries (P segments x nx / 2 column
+// pairs each).
 __host__ __device__ constexpr size_t fused_smem_bytes(int nx, int R, int P)
 {
-    return (size_t)(R + 2) * nx * sizeof(float) + 2 * (size_t)P * nx * sizeof(float);
+    return (size_t)(R + 2) * nx * sizeof(float) + 3 * (size_t)P * nx * sizeof(float);
 }
 
 
@@ -159,14 +177,18 @@ __device__ __forceinline__ float2 shfl_down2(float2 v, int d)
 
 // Reaction of two values (explicit Euler substeps as in react_point, same
 // operation order; the exact flow per element).
+__device__ __forceinline__ float2 react2_step(float2 w, float2 c2)
+{
+    const float2 w3 = mul2(mul2(w, w), w);
+    return fma2(c2, add2(w, make_float2(-w3.x, -w3.y)), w);
+}
+
 __device__ __forceinline__ float2 react2(float2 w, float c, int nsub)
 {
+    if (nsub == 1) return react2_step(w, f2s(c));
     if (nsub < 0) return make_float2(react_point(w.x, c, nsub), react_point(w.y, c, nsub));
     const float2 c2 = f2s(c);
-    for (int s = 0; s < nsub; ++s) {
-        const float2 w3 = mul2(mul2(w, w), w);
-        w = fma2(c2, add2(w, make_float2(-w3.x, -w3.y)), w);
-    }
+    for (int s = 0; s < nsub; ++s) w = react2_step(w, c2);
     return w;
 }
 
@@ -237,7 +259,10 @@ __global__ void __launch_bounds__(NT) fused_sweep_kernel(const __grid_constant__
     constexpr int R = P * LS;
     constexpr int S = G * P;                    // segments per column
     constexpr int V = C >= 4 ? 4 : C;           // values per shared-memory access in the row pass
+    constexpr int NY = G * R;
+    constexpr int RPI = NT * 4 / NX;            // rows per pass of the CTA over 16-byte pieces
     static_assert(R % (2 * NW) == 0, "rows per CTA must be a multiple of twice the warps");
+    static_assert((NT * 4) % NX == 0 && (NY & (NY - 1)) == 0, "whole rows per pass, power-of-two ny");
     static_assert(S <= 32, "at most 32 segments per column");
     static_assert(LS <= kMaxChunk, "segment longer than the power table");
 
@@ -245,31 +270,30 @@ __global__ void __launch_bounds__(NT) fused_sweep_kernel(const __grid_constant__
     float *tile = reinterpret_cast<float *>(fz_smem);                       // (R + 2) rows of NX
     float2 *ce = reinterpret_cast<float2 *>(tile + (size_t)(R + 2) * NX);   // [P][NXP] forward carries
     float2 *cb = ce + (size_t)P * NXP;                                      // [P][NXP] backward carries
+    float2 *dn = cb + (size_t)P * NXP;                                      // [P][NXP] final backward carries
     __shared__ double sh[32];
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int rank = G > 1 ? (int)cg::this_cluster().block_rank() : 0;
-    const int ny = a.ny;
     const Job<float> jb = a.jobs[blockIdx.y];
     const int r0 = rank * R;
+    // this thread's 16-byte column piece in every pass over rows
+    const int px = (threadIdx.x * 4) % NX, prow = (threadIdx.x * 4) / NX, pxs = fz_swz(px);
 
     // 1. load (with halo rows for PR) and react; tile row t = state row r0 - 1 + t.
     //    Every 16-byte piece of the CTA's rows is requested before any arrives.
     {
         const int t_lo = PR ? 0 : 1, t_hi = PR ? R + 2 : R + 1;
-        const int total = (t_hi - t_lo) * NX;
         if (!(REACT && jb.base)) {
-            for (int idx = threadIdx.x * 4; idx < total; idx += NT * 4) {
-                const int t = t_lo + idx / NX, x = idx % NX;
-                const int gy = (r0 - 1 + t + ny) % ny;
-                fz_cp_async16(tile + (size_t)t * NX + fz_swz(x), jb.in + (size_t)gy * NX + x);
+            for (int t = t_lo + prow; t < t_hi; t += RPI) {
+                const int gy = (r0 - 1 + t) & (NY - 1);
+                fz_cp_async16(tile + (size_t)t * NX + pxs, jb.in + (size_t)gy * NX + px);
             }
             fz_cp_async_wait_all();
             if (REACT) {
                 // the same pieces as this thread copied: no barrier needed before
-                for (int idx = threadIdx.x * 4; idx < total; idx += NT * 4) {
-                    const int t = t_lo + idx / NX, x = idx % NX;
-                    float4 *q4 = reinterpret_cast<float4 *>(tile + (size_t)t * NX + fz_swz(x));
+                for (int t = t_lo + prow; t < t_hi; t += RPI) {
+                    float4 *q4 = reinterpret_cast<float4 *>(tile + (size_t)t * NX + pxs);
                     const float4 v = *q4;
                     const float2 lo = react2(make_float2(v.x, v.y), a.react, a.nsub);
                     const float2 hi = react2(make_float2(v.z, v.w), a.react, a.nsub);
@@ -279,28 +303,26 @@ __global__ void __launch_bounds__(NT) fused_sweep_kernel(const __grid_constant__
         } else {
             // increments around a base: both streams through registers, U pieces in flight
             constexpr int U = 4;
-            for (int i0 = threadIdx.x * 4; i0 < total; i0 += NT * 4 * U) {
+            for (int t0 = t_lo + prow; t0 < t_hi; t0 += RPI * U) {
                 float4 v[U], b[U];
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
-                    const int idx = i0 + u * NT * 4;
-                    if (idx < total) {
-                        const int t = t_lo + idx / NX, x = idx % NX;
-                        const size_t go = (size_t)((r0 - 1 + t + ny) % ny) * NX + x;
+                    const int t = t0 + u * RPI;
+                    if (t < t_hi) {
+                        const size_t go = (size_t)((r0 - 1 + t) & (NY - 1)) * NX + px;
                         v[u] = fz_ld4(jb.in + go);
                         b[u] = fz_ld4(jb.base + go);
                     }
                 }
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
-                    const int idx = i0 + u * NT * 4;
-                    if (idx < total) {
-                        const int t = t_lo + idx / NX, x = idx % NX;
+                    const int t = t0 + u * RPI;
+                    if (t < t_hi) {
                         const float4 r = make_float4(react_delta(b[u].x, v[u].x, a.react, a.nsub),
                                                      react_delta(b[u].y, v[u].y, a.react, a.nsub),
                                                      react_delta(b[u].z, v[u].z, a.react, a.nsub),
                                                      react_delta(b[u].w, v[u].w, a.react, a.nsub));
-                        *reinterpret_cast<float4 *>(tile + (size_t)t * NX + fz_swz(x)) = r;
+                        *reinterpret_cast<float4 *>(tile + (size_t)t * NX + pxs) = r;
                     }
                 }
             }
@@ -420,31 +442,26 @@ __global__ void __launch_bounds__(NT) fused_sweep_kernel(const __grid_constant__
             if (j == s) pre = tot;
             tot = fma2(mls, tot, ev);
         }
-        const float2 din = fma2(f2s(c.chunk_pw[S - 1 - s]), mul2(tot, inv1m), pre);
-#pragma unroll
-        for (int k = 0; k < LS; ++k) {
-            float2 *el = reinterpret_cast<float2 *>(col0 + (size_t)k * NX + xs);
-            *el = fma2(f2s(c.pw[LS - k]), din, *el);
-        }
+        // the fix-up x += rho^(LS-k) din is applied in the epilogue
+        dn[p * NXP + xp] = fma2(f2s(c.chunk_pw[S - 1 - s]), mul2(tot, inv1m), pre);
     }
     // no CTA leaves (or reuses its carries) while a peer may still read them
     if constexpr (G > 1) cg::this_cluster().sync(); else __syncthreads();
 
-    // 4. epilogue: tile row j = state row r0 + j
+    // 4. epilogue: tile row j = state row r0 + j, finished with the last
+    //    column fix-up rho^(LS-k) din (k = row within its segment)
     double acc = 0.0;
     if (!jb.g && !jb.h && !jb.sub && jb.out) {
         // plain store of (+-)Phi
-        constexpr int Q = NX / 4;
-        for (int i = threadIdx.x; i < R * Q; i += NT) {
-            const int j = i / Q, x = (i % Q) * 4;
-            float4 v = fz_ld4(tile + (size_t)j * NX + fz_swz(x));
-            if (a.neg) v = make_float4(-v.x, -v.y, -v.z, -v.w);
-            *reinterpret_cast<float4 *>(jb.out + (size_t)(r0 + j) * NX + x) = v;
+        for (int j = prow; j < R; j += RPI) {
+            const float4 v = fz_col_final<NX, NXP, LS>(tile, dn, c, j, px, pxs);
+            const float4 o = a.neg ? make_float4(-v.x, -v.y, -v.z, -v.w) : v;
+            *reinterpret_cast<float4 *>(jb.out + (size_t)(r0 + j) * NX + px) = o;
         }
     } else if (jb.sub) {
-        fz_epilogue<NX, R, NT, true>(jb, tile, r0, a.neg, acc);
+        fz_epilogue<NX, NXP, R, LS, RPI, true>(jb, tile, dn, c, r0, prow, px, pxs, a.neg, acc);
     } else {
-        fz_epilogue<NX, R, NT, false>(jb, tile, r0, a.neg, acc);
+        fz_epilogue<NX, NXP, R, LS, RPI, false>(jb, tile, dn, c, r0, prow, px, pxs, a.neg, acc);
     }
     if (a.partials) {
         const double tsum = block_sum(acc, sh);

@@ -8,6 +8,8 @@
 #include <cstdio>
 #include <cstring>
 #include <cmath>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -250,6 +252,20 @@ inline LevelOp<T> make_level_op(const atm_problem &pb, const atm_solver &sv, int
     op.row_smem = pr ? (size_t)(op.rows_per_cta + 2) * pitch * sizeof(T) : 0;
     if (sv.sweep_kernel != ATM_SWEEP_SPLIT) op.fused = fused_variants<T>(pb.nx, pb.ny, pr, react, ay);
     return op;
+}
+
+// Autotuner results shared by every handle of the process: handles with the
+// same configuration run the same kernels (identical results) and pay the
+// tuning once.  Value: level-0 chunk, then the fused shape index per level.
+struct TuneCache {
+    std::mutex mu;
+    std::map<std::string, std::vector<int>> choice;
+};
+
+inline TuneCache &tune_cache()
+{
+    static TuneCache c;
+    return c;
 }
 
 enum { L_SWEEP = 0, L_AXPY = 1, L_NORM = 2 };
@@ -508,11 +524,17 @@ struct Plan : PlanBase {
         return pb.nx / 32;
     }
 
-    // Partial sums written per job: the largest over the kernels a level may use.
+    // Partial sums written per job: the largest over every kernel a level may
+    // use (the autotuner tries each fused shape, with its own cluster size).
     int max_blocks_per_job(int l) const
     {
-        const int b = blocks_per_job(l);
-        return (is1d || b >= pb.nx / 32) ? b : pb.nx / 32;
+        int b = blocks_per_job(l);
+        if (is1d || (l < (int)lv.size() && lv[l].learned)) return b;
+        if (b < pb.nx / 32) b = pb.nx / 32;
+        if (l < (int)lv.size())
+            for (const FusedVariant<T> &f : lv[l].fused)
+                if (f.G > b) b = f.G;
+        return b;
     }
 
     void add_sweep(Phase &ph, int l, std::vector<Job<T>> &&js, int neg, bool norm)
@@ -1112,6 +1134,68 @@ struct Plan : PlanBase {
         return ATM_OK;
     }
 
+    // Key of the autotuner cache: everything that decides the timed launches
+    // (device, precision, role, grid, problem kind, time grid, levels, kernels).
+    std::string tune_key() const
+    {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        char b[512];
+        int n = std::snprintf(b, sizeof(b), "d%d T%zu r%d k%d %dx%d nt%d alg%d L%d nu%d k%d fp%d cp%d sk%d cr%d cpo%d m",
+                              dev, sizeof(T), role, pb.kind, pb.nx, pb.ny, pb.nt_points, sv.algorithm, L, sv.nu, sv.k,
+                              sv.fine_prop, sv.coarse_prop, sv.sweep_kernel, sv.coarse_reaction, (int)cpo);
+        for (int l = 0; l + 1 < L && n < (int)sizeof(b) - 8; ++l) n += std::snprintf(b + n, sizeof(b) - n, "_%d", sv.m[l]);
+        for (int l = 0; l < L && n < (int)sizeof(b) - 8; ++l)
+            n += std::snprintf(b + n, sizeof(b) - n, "/%d", sv.reaction_substeps[l]);
+        return std::string(b);
+    }
+
+    // Coarse-level kernel choice (ATM_SWEEP_AUTO): for each level l >= 1 with
+    // fused shapes, time the level's sweeps of `ph` with the split kernels and
+    // with each fused shape (warm-up, then three repetitions) and keep the fastest.
+    // The coarse launches are short and latency-bound, so the shape with the
+    // most CTAs per state often wins there.
+    atm_status autotune_coarse(const Phase &ph)
+    {
+        if (is1d || sv.sweep_kernel != ATM_SWEEP_AUTO) return ATM_OK;
+        cudaEvent_t e0, e1;
+        ATM_CK(cudaEventCreate(&e0));
+        ATM_CK(cudaEventCreate(&e1));
+        for (int l = 1; l < L; ++l) {
+            if (lv[l].learned || lv[l].fused.empty()) continue;
+            std::vector<const LaunchRec *> recs;
+            for (const LaunchRec &r : ph)
+                if (r.type == L_SWEEP && r.level == l) recs.push_back(&r);
+            if (recs.empty()) continue;
+            float best = 1e30f;
+            int bk = lv[l].fz;
+            for (int k = -1; k < (int)lv[l].fused.size(); ++k) {
+                lv[l].fz = k;
+                launch_failed = false;
+                for (const LaunchRec *r : recs) launch_sweep(l, d_jobs + r->job_index, r->njobs, r->neg, r->partials);
+                cudaEventRecord(e0, st);
+                for (int rep = 0; rep < 3; ++rep)
+                    for (const LaunchRec *r : recs)
+                        launch_sweep(l, d_jobs + r->job_index, r->njobs, r->neg, r->partials);
+                cudaEventRecord(e1, st);
+                cudaEventSynchronize(e1);
+                float ms = 0;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (launch_failed) {
+                    launch_failed = false;
+                    cudaGetLastError();
+                    continue;
+                }
+                if (ms < best) { best = ms; bk = k; }
+            }
+            lv[l].fz = bk;
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        ATM_CK(cudaGetLastError());
+        return ATM_OK;
+    }
+
     // Shared-memory and cluster-size attributes of the fused kernels; shapes
     // that cannot be resident on this device are dropped.
     atm_status prepare_fused(int l)
@@ -1230,8 +1314,34 @@ struct Plan : PlanBase {
         ATM_CK(cudaEventCreate(&ev1));
         pev.assign(4 * (size_t)nprof, nullptr);
         for (cudaEvent_t &e : pev) ATM_CK(cudaEventCreate(&e));
-        if (sv.algorithm != ATM_SEQUENTIAL || role == ROLE_OUTER)
-            ATM_TRY(autotune_chunk(role == ROLE_OUTER ? resid_full : role == ROLE_INNER ? inner_cycle : passA));
+        const std::string tkey = tune_key();
+        bool cached = false;
+        {
+            std::lock_guard<std::mutex> lk(tune_cache().mu);
+            auto it = tune_cache().choice.find(tkey);
+            if (it != tune_cache().choice.end() && (int)it->second.size() == L + 1) {
+                chunk = it->second[0];
+                for (int l = 0; l < L; ++l) lv[l].fz = it->second[1 + l];
+                cached = true;
+            }
+        }
+        if (!cached) {
+            if (sv.algorithm != ATM_SEQUENTIAL || role == ROLE_OUTER)
+                ATM_TRY(autotune_chunk(role == ROLE_OUTER ? resid_full : role == ROLE_INNER ? inner_cycle : passA));
+            if (L > 1 && role != ROLE_OUTER) {
+                // coarse arrays hold whatever the workspace held: zero them before timing
+                for (int l = 1; l < L; ++l) {
+                    T *arrs[4] = {lv[l].u, lv[l].v, lv[l].r, lv[l].g};
+                    for (int q = 0; q < 4; ++q)
+                        ATM_CK(cudaMemsetAsync(arrs[q], 0, (size_t)lv[l].N * nsp * sizeof(T), st));
+                }
+                ATM_TRY(autotune_coarse(role == ROLE_INNER ? inner_cycle : rest));
+            }
+            std::vector<int> ch(1, chunk);
+            for (int l = 0; l < L; ++l) ch.push_back(lv[l].fz);
+            std::lock_guard<std::mutex> lk(tune_cache().mu);
+            tune_cache().choice[tkey] = ch;
+        }
         ATM_CK(cudaMemsetAsync(lv[0].u, 0, n0, st));
         ATM_CK(cudaStreamSynchronize(st));
         if (sv.use_graph && st != nullptr && role == ROLE_NORMAL) {
@@ -1788,7 +1898,7 @@ struct RefinedPlan : PlanBase {
         outer.convert_to_T_other(outer.lv[0].u, inner.ubase, n);
         outer.convert_to_T_other(outer.r_full, inner.lv[0].g, n);
         cudaMemsetAsync(inner.lv[0].u, 0, n * sizeof(float), st);
-        inner.run(inner.inner_cycle);
+        for (int c = 0; c < inner_cycles(); ++c) inner.run(inner.inner_cycle);
         int blocks = (int)((n + 255) / 256);
         if (blocks > 4096) blocks = 4096;
         refine_update_kernel<<<blocks, 256, 0, st>>>(outer.lv[0].u, inner.lv[0].u, n);
@@ -1826,8 +1936,10 @@ struct RefinedPlan : PlanBase {
     long long kernels_outer() const { return outer.kernels_in(outer.resid_full); }
     long long kernels_inner() const
     {
-        return 3 + inner.kernels_in(inner.inner_cycle);
+        return 3 + inner_cycles() * inner.kernels_in(inner.inner_cycle);
     }
+
+    int inner_cycles() const { return sv.refine_inner_cycles > 0 ? sv.refine_inner_cycles : 3; }
 
     atm_status solve(atm_result *res) override
     {

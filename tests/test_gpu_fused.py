@@ -124,3 +124,24 @@ def test_fused_residual_norm_matches_split(torch):
         s.solve()
         hs.append(s.residual_history())
     np.testing.assert_allclose(hs[0], hs[1], rtol=1e-3)
+
+
+@pytest.mark.parametrize("inner", [2, 3])
+def test_refined_with_several_inner_cycles(torch, inner):
+    """Several FP32 V-cycles on the correction per FP64 residual: the same FP64
+    fixed point (<= 1e-7 against the oracle) with fewer FP64 residual passes."""
+    kw = dict(kind="ac", nx=64, ny=64, dt=1e-4, nt=257, m=(4, 4), k=4, nu=1, tol=1e-9, max_iter=60,
+              precision=atm.FP32_REFINED)
+    u0 = I.uniform_field((64, 64), 15)
+    res = {}
+    for ic in (1, inner):
+        oc, gp, gs = pair(**kw)
+        gs.refine_inner_cycles = ic
+        s = atm.Solver(gp, gs)
+        s.set_initial_condition(dev(torch, u0))
+        r = s.solve()
+        assert r["converged"], (ic, r)
+        res[ic] = (r, s.solution().cpu().numpy())
+    seq = oracle.sequential(oc, u0)
+    assert rel_l2(res[inner][1], seq) <= 1e-7
+    assert res[inner][0]["iterations"] < res[1][0]["iterations"], (res[1][0], res[inner][0])

@@ -284,6 +284,9 @@ def test_fp32_refined_reaches_fp64_accuracy(torch, case):
     err = rel_l2(res[atm.FP32_REFINED][1], seq)
     assert err <= 1e-7, err
     assert res[atm.FP32_REFINED][0]["iterations"] <= res[atm.FP64][0]["iterations"] + 3
-    # the refined history is the FP64 residual of every point: check its last entry
-    full = oracle.full_residual_norm(oc, np.ascontiguousarray(res[atm.FP32_REFINED][1]))
-    assert abs(full - res[atm.FP32_REFINED][2][-1]) <= 1e-3 * full + 1e-14
+    # the refined history is the FP64 residual of every point: check its last entry,
+    # up to the rounding floor of evaluating a residual in FP64 (a few eps_64 per value)
+    u = res[atm.FP32_REFINED][1]
+    full = oracle.full_residual_norm(oc, np.ascontiguousarray(u))
+    floor = 4 * 2.2e-16 * np.sqrt(u.size) * np.abs(u).max()
+    assert abs(full - res[atm.FP32_REFINED][2][-1]) <= 1e-3 * full + floor
