@@ -276,12 +276,12 @@ def train_learned(atm, w, device, steps, seeds=(101, 102, 103, 104, 105), batch=
 
 
 def make_desc(atm, w, algorithm, precision, profile, coarse="classical", sweep="auto", cpoint=False,
-              inner_cycles=0):
+              inner_cycles=0, nu=None):
     kind = {"ac": atm.ALLEN_CAHN, "heat1d": atm.HEAT1D}[w["kind"]]
     ny = w["n"] if w["kind"] != "heat1d" else 1
     prob = atm.make_problem(kind, w["n"], ny, dt=w["dt"], nt_points=w["nt"], eps=w["eps"])
     alg = {"at": atm.AT_MGRIT, "mgrit": atm.MGRIT, "seq": atm.SEQUENTIAL}[algorithm]
-    desc = atm.make_solver(alg, m=w["m"], k=w["k"], nu=w["nu"], tol=w["tol"],
+    desc = atm.make_solver(alg, m=w["m"], k=w["k"], nu=w["nu"] if nu is None else nu, tol=w["tol"],
                            max_iter=w["max_iter"], precision=precision, use_graph=True,
                            profile=profile,
                            coarse_prop=atm.PROP_LEARNED if coarse == "learned" else atm.PROP_SPLIT_BE,
@@ -382,8 +382,10 @@ def main():
                     help="2D propagator kernels (auto: level 0 autotuned at create time)")
     ap.add_argument("--storage", choices=["cpoint", "full"], default="cpoint",
                     help="level-0 storage: C-points only (default) or every time point")
+    ap.add_argument("--nu", type=int, choices=[0, 1], default=None,
+                    help="relaxation: 0 F, 1 FCF (default: the workload's); in fp32r it shapes the inner cycles")
     ap.add_argument("--inner-cycles", type=int, default=0,
-                    help="fp32r: FP32 V-cycles per FP64 refinement step (0: the library default, 3)")
+                    help="fp32r: FP32 V-cycles per FP64 refinement step (0: the library default, 4)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.workload == "batch64":
@@ -408,7 +410,7 @@ def main():
         nn_params, learned_info = train_learned(atm, w, device, args.train_steps)
     prob, desc = make_desc(atm, w, args.algorithm, prec, profile=True, coarse=args.coarse,
                            sweep=args.sweep_kernel, cpoint=args.storage == "cpoint",
-                           inner_cycles=args.inner_cycles)
+                           inner_cycles=args.inner_cycles, nu=args.nu)
     solver = atm.Solver(prob, desc, device=device)
     if args.coarse == "learned":
         solver.set_learned_coarse(nn_params)
@@ -530,9 +532,10 @@ def main():
                 "data": "synthetic",
                 "config": {"workload": args.workload,
                            **{k: (list(v) if isinstance(v, tuple) else v) for k, v in w.items()},
+                           **({"nu": args.nu} if args.nu is not None else {}),
                            "algorithm": args.algorithm, "parallelism": f"{world} independent problems",
                            "sweep_kernel": args.sweep_kernel, "storage": args.storage,
-                           "inner_cycles": (args.inner_cycles or 3) if args.precision == "fp32r" else None,
+                           "inner_cycles": (args.inner_cycles or 4) if args.precision == "fp32r" else None,
                            "l2": "working set larger than L2 (workspace %.2f GB; one level-0 launch reads and "
                                  "writes %.0f MB)" % (atm.workspace_size(prob, desc) / 1e9,
                                                       2 * jobs * n_val * (4 if args.precision == "fp32" else 8) / 1e6)},

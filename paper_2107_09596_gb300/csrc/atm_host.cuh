@@ -357,6 +357,8 @@ struct Plan : PlanBase {
     bool cpo = false;       // level 0 stores C-points only (u holds them, `work` the F-chains)
     T *work = nullptr;      // cpo: one working state per interval (the latest F-point)
     T *bwork = nullptr;     // cpo, inner role: the base chain of each interval (latest F-point)
+    float *base_store = nullptr;  // cpo, inner role: stored FP32 base of every point (no regeneration)
+    float *fp32_out = nullptr;    // cpo, outer role: FP32 copies of the F-chains written here
     size_t regen_index = 0; // cpo: jobs u[i] -> work[i] (NC), then work[i] -> work[i] (NC)
     T *mid = nullptr;       // row-sweep results, maxbatch states
     T *sin = nullptr, *sout = nullptr;   // FP64 <-> T staging for atm_apply_propagator
@@ -585,7 +587,7 @@ struct Plan : PlanBase {
                       const T *sub = nullptr, T *out2 = nullptr, const T *base = nullptr)
     {
         Job<T> j;
-        j.in = in; j.out = out; j.g = g; j.h = h; j.sub = sub; j.out2 = out2; j.base = base;
+        j.in = in; j.out = out; j.g = g; j.h = h; j.sub = sub; j.out2 = out2; j.base = base; j.outf = nullptr;
         return j;
     }
 
@@ -597,9 +599,11 @@ struct Plan : PlanBase {
         size_t f = (size_t)t;
         for (int j = 0; j < l; ++j) f *= (size_t)sv.m[j];
         if (cpo) {
-            // C-point storage: ubase holds the C-points, bwork the regenerated base chain
+            // C-point storage: ubase holds the C-points, base_store (or the
+            // regenerated chain in bwork) the F-points
             const size_t m0 = (size_t)lv[0].m;
-            return (f % m0 == 0) ? ubase + (f / m0) * nsp : bwork + (f / m0) * nsp;
+            if (f % m0 == 0) return ubase + (f / m0) * nsp;
+            return base_store ? reinterpret_cast<const T *>(base_store) + f * nsp : bwork + (f / m0) * nsp;
         }
         return ubase + f * nsp;
     }
@@ -624,8 +628,11 @@ struct Plan : PlanBase {
             std::vector<Job<T>> js;
             for (int i = 0; i < NC; ++i) {
                 const int t = i * m + j;
-                if (t < N && (!c0 || full_interval(i)))
+                if (t < N && (!c0 || full_interval(i))) {
                     js.push_back(job(up(l, t - 1), up(l, t), gl(l, t), nullptr, nullptr, nullptr, bp(l, t - 1)));
+                    // the FP64 outer pass leaves fp32(u_t) for the inner cycles' base
+                    if (c0 && fp32_out) js.back().outf = fp32_out + (size_t)t * nsp;
+                }
             }
             add_sweep(ph, l, std::move(js), 0, false);
             if (c0 && bwork) {
@@ -872,7 +879,7 @@ struct Plan : PlanBase {
         if (role == ROLE_INNER) {
             lv[0].g = take<T>(n0);
             ubase = take<T>(n0);
-            if (cpo) bwork = take<T>(n0);
+            if (cpo && !base_store) bwork = take<T>(n0);
         }
         if (L > 1 && sv.nu == 1 && role == ROLE_NORMAL) yC = take<T>((size_t)lv[0].NC * nsp);
         for (int l = 1; l < L; ++l) {
@@ -1143,7 +1150,8 @@ struct Plan : PlanBase {
         char b[512];
         int n = std::snprintf(b, sizeof(b), "d%d T%zu r%d k%d %dx%d nt%d alg%d L%d nu%d k%d fp%d cp%d sk%d cr%d cpo%d m",
                               dev, sizeof(T), role, pb.kind, pb.nx, pb.ny, pb.nt_points, sv.algorithm, L, sv.nu, sv.k,
-                              sv.fine_prop, sv.coarse_prop, sv.sweep_kernel, sv.coarse_reaction, (int)cpo);
+                              sv.fine_prop, sv.coarse_prop, sv.sweep_kernel, sv.coarse_reaction,
+                              (int)cpo + 2 * (base_store != nullptr) + 4 * (fp32_out != nullptr));
         for (int l = 0; l + 1 < L && n < (int)sizeof(b) - 8; ++l) n += std::snprintf(b + n, sizeof(b) - n, "_%d", sv.m[l]);
         for (int l = 0; l < L && n < (int)sizeof(b) - 8; ++l)
             n += std::snprintf(b + n, sizeof(b) - n, "/%d", sv.reaction_substeps[l]);
@@ -1840,6 +1848,11 @@ struct RefinedPlan : PlanBase {
     cudaGraphExec_t gA = nullptr, gIter = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     size_t off = 0;
+    // C-point storage: the FP64 pass writes fp32(u) of every F-point (the base
+    // of the inner cycles' increments) when that array fits in 16 GiB;
+    // otherwise the inner cycles regenerate the base chain themselves
+    bool store_base = false;
+    size_t base_bytes = 0;
 
     ~RefinedPlan() override
     {
@@ -1865,6 +1878,13 @@ struct RefinedPlan : PlanBase {
         inner.sv.profile = 0;
         inner.role = ROLE_INNER;
         inner.st = stream;
+        const size_t nsp = (p.kind == ATM_HEAT1D) ? (size_t)p.nx : (size_t)p.nx * p.ny;
+        base_bytes = (((size_t)p.nt_points * nsp * sizeof(float)) + 255) & ~(size_t)255;
+        store_base = s.cpoint_storage_only && base_bytes <= ((size_t)16 << 30);
+        // placeholder address while sizes are measured (the layout sets the real one)
+        float *ph = store_base ? reinterpret_cast<float *>((uintptr_t)256) : nullptr;
+        outer.fp32_out = ph;
+        inner.base_store = ph;
     }
 
     size_t measure(atm_status *s)
@@ -1877,15 +1897,20 @@ struct RefinedPlan : PlanBase {
         if (*s != ATM_OK) return 0;
         size_t b = inner.measure(s);
         if (*s != ATM_OK) return 0;
-        return a + b;
+        return (store_base ? base_bytes : 0) + a + b;
     }
 
     atm_status layout(uintptr_t ws)
     {
-        ATM_TRY(outer.layout(ws, outer.maxbatch, outer.npartials_max));
+        const size_t sb = store_base ? base_bytes : 0;
+        if (store_base) {
+            outer.fp32_out = reinterpret_cast<float *>(ws);
+            inner.base_store = reinterpret_cast<float *>(ws);
+        }
+        ATM_TRY(outer.layout(ws + sb, outer.maxbatch, outer.npartials_max));
         const size_t a = outer.off;
-        ATM_TRY(inner.layout(ws + a, inner.maxbatch, inner.npartials_max));
-        off = a + inner.off;
+        ATM_TRY(inner.layout(ws + sb + a, inner.maxbatch, inner.npartials_max));
+        off = sb + a + inner.off;
         return ATM_OK;
     }
 
@@ -1939,7 +1964,7 @@ struct RefinedPlan : PlanBase {
         return 3 + inner_cycles() * inner.kernels_in(inner.inner_cycle);
     }
 
-    int inner_cycles() const { return sv.refine_inner_cycles > 0 ? sv.refine_inner_cycles : 3; }
+    int inner_cycles() const { return sv.refine_inner_cycles > 0 ? sv.refine_inner_cycles : 4; }
 
     atm_status solve(atm_result *res) override
     {

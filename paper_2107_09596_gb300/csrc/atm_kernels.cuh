@@ -53,7 +53,7 @@ struct TriCoef {
 //   P = Phi(base + in) - Phi(base),
 // evaluated without cancellation (the reaction increment is formed
 // algebraically; the diffusion part is linear), so that a small `in` keeps its
-// relative precision.
+// relative precision.  outf (split kernels): FP32 copy of `out`.
 template <typename T>
 struct Job {
     const T *in;
@@ -63,6 +63,7 @@ struct Job {
     const T *sub;
     T *out2;
     const T *base;
+    float *outf;
 };
 
 template <typename T>
@@ -272,6 +273,7 @@ __device__ __forceinline__ void apply_epilogue(const Job<T> &jb, size_t idx, T p
         if (jb.out2) jb.out2[idx] = r;
     }
     if (jb.out) jb.out[idx] = val;
+    if (jb.outf) jb.outf[idx] = (float)val;
 }
 
 // Deterministic CTA sum of one double per thread; thread 0 gets the total.
