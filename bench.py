@@ -41,6 +41,10 @@ WORKLOADS = {
                            tol=1e-8, max_iter=60),
     "heat1d_127": dict(kind="heat1d", n=127, nt=1025, dt=1 / 1024, eps=0.0, m=(8,), k=4, nu=1,
                        tol=1e-10, max_iter=60),
+    # 1024^2 x 65537 with m = (32, 4, 4), k = 16: FP32 with C-point storage (the FP64
+    # kernels stop at 512); tol = RMS 2e-7 per C-point value, near the FP32 floor
+    "allen_cahn_1024": dict(kind="ac", n=1024, nt=65537, dt=2.5e-5, eps=0.02, m=(32, 4, 4), k=16, nu=1,
+                            tol=1e-2, max_iter=30),
 }
 
 # Textbook flops per grid value of one sweep kernel:
@@ -132,12 +136,13 @@ def kernel_source_hash(fused=False):
         return hashlib.md5(fh.read()).hexdigest()[:12]
 
 
-def batch_descs(atm, count=64, seed=0):
+def batch_descs(atm, count=64, seed=0, precision="fp32r", storage="cpoint"):
     """The batched workload: `count` problems drawn by atm_inputs.batch_problem_draws
     (kind in {heat2d, Allen-Cahn}, n in {64..512}, nt in {1025, 4097, 16385},
     m in {8, 16}); AT-MGRIT FCF with two coarsenings when the coarse grid allows,
-    k = ceil(N_c / 4); FP32 propagation; stop at an RMS residual of 1e-6 per
-    space-time value (tol = 1e-6 sqrt(nt n^2)); dt = 1e-4, eps = 0.02."""
+    k = ceil(N_c / 4); dt = 1e-4, eps = 0.02.  fp32r (FP32 propagation, FP64
+    residual): stop at an RMS C-point residual of 1e-10 per value; fp32: at an
+    RMS residual of 1e-6 (the FP32 floor is near 1e-7)."""
     out = []
     for d in I.batch_problem_draws(count, seed):
         kind = atm.ALLEN_CAHN if d["kind"] == "allen_cahn" else atm.HEAT2D
@@ -147,8 +152,11 @@ def batch_descs(atm, count=64, seed=0):
         ms = (m, m) if (nc - 1) // m + 1 >= 3 else (m,)
         nco = ((nc - 1) // m + 1) if len(ms) == 2 else nc
         k = max(2, (nco + 3) // 4)
-        desc = atm.make_solver(atm.AT_MGRIT, m=ms, k=k, nu=1, tol=1e-6 * np.sqrt(nt * n * n),
-                               max_iter=40, precision=atm.FP32, use_graph=2)
+        rms = 1e-10 if precision == "fp32r" else 1e-6
+        pts = nc if storage == "cpoint" else nt
+        desc = atm.make_solver(atm.AT_MGRIT, m=ms, k=k, nu=1, tol=rms * np.sqrt(pts * n * n),
+                               max_iter=40, precision=atm.FP32_REFINED if precision == "fp32r" else atm.FP32,
+                               use_graph=2, cpoint_only=storage == "cpoint")
         out.append((d, prob, desc))
     return out
 
@@ -160,7 +168,7 @@ def run_batch(args):
     import paper_2107_09596_gb300 as atm
     device = torch.device("cuda", 0)
     atm._build.build()
-    descs = batch_descs(atm)
+    descs = batch_descs(atm, precision="fp32r" if args.precision == "fp32r" else "fp32", storage=args.storage)
     budget = 240e9
     groups, cur, used = [], [], 0
     for item in descs:
@@ -204,8 +212,9 @@ def run_batch(args):
     value = total_steps / t_batch
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 0,
             "ms_per_step": t_batch * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32", "data": "synthetic",
+            "dtype": "f32+f64" if args.precision == "fp32r" else "f32", "data": "synthetic",
             "config": {"workload": "batch64", "problems": len(descs), "groups": len(groups),
+                       "precision": args.precision, "storage": args.storage,
                        "memory_budget_gb_per_group": budget / 1e9, "l2": "inputs larger than L2"},
             "one_at_a_time": {"value": total_steps / t_single, "ms": t_single * 1e3},
             "batched_speedup": t_single / t_batch,
@@ -386,12 +395,15 @@ def main():
                     help="relaxation: 0 F, 1 FCF (default: the workload's); in fp32r it shapes the inner cycles")
     ap.add_argument("--inner-cycles", type=int, default=0,
                     help="fp32r: FP32 V-cycles per FP64 refinement step (0: the library default, 4)")
+    ap.add_argument("--max-iter", type=int, default=None, help="override the workload's cycle cap")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.workload == "batch64":
         run_batch(args)
         return
-    w = WORKLOADS[args.workload]
+    w = dict(WORKLOADS[args.workload])
+    if args.max_iter is not None:
+        w["max_iter"] = args.max_iter
     world, rank, local, dist = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, w, world, rank, dist)
@@ -475,7 +487,7 @@ def main():
     # states per profiled launch table: the level-0 relaxation launches cover
     # every interval; in the refined mode the profiled table is the FP64
     # residual of every time point
-    jobs = {"allen_cahn_256": 256, "heat1d_127": 128}[args.workload]
+    jobs = {"allen_cahn_256": 256, "heat1d_127": 128, "allen_cahn_1024": 2048}[args.workload]
     if args.precision == "fp32r" and args.storage == "full":
         jobs = w["nt"] - 1
     if args.algorithm == "seq":
@@ -541,6 +553,7 @@ def main():
                                                       2 * jobs * n_val * (4 if args.precision == "fp32" else 8) / 1e6)},
                 "iterations": int(np.median(iters)), "time_to_solution_ms": ms,
                 "final_residual": float(res["final_residual"]),
+                "residual_history": [float(v) for v in solver.residual_history()][:64],
                 "e2e": {"value": world * (w["nt"] - 1) / (e2e_ms / 1e3), "unit": UNIT,
                         "h2d_bytes_per_step": state_bytes,
                         "d2h_bytes_per_step": state_bytes + 8 * len(hist)},

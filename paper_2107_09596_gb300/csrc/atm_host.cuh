@@ -1853,9 +1853,11 @@ struct RefinedPlan : PlanBase {
     // otherwise the inner cycles regenerate the base chain themselves
     bool store_base = false;
     size_t base_bytes = 0;
+    cudaGraphExec_t gLoop = nullptr;   // use_graph = 2: the whole refinement loop, one launch
 
     ~RefinedPlan() override
     {
+        if (gLoop) cudaGraphExecDestroy(gLoop);
         if (gA) cudaGraphExecDestroy(gA);
         if (gIter) cudaGraphExecDestroy(gIter);
         if (ev0) cudaEventDestroy(ev0);
@@ -1954,6 +1956,15 @@ struct RefinedPlan : PlanBase {
             ATM_TRY(capture(false, &gA));
             ATM_TRY(capture(true, &gIter));
         }
+        if (sv.use_graph == 2 && st != nullptr) {
+            cudaGraph_t g = nullptr;
+            ATM_CK(cudaGraphCreate(&g, 0));
+            atm_status s = add_loop(g);
+            if (s == ATM_OK && cudaGraphInstantiate(&gLoop, g, 0) != cudaSuccess)
+                s = fail(ATM_ERR_CUDA, "instantiating the refinement loop failed");
+            cudaGraphDestroy(g);
+            ATM_TRY(s);
+        }
         outer.launches = inner.launches = launches = 0;
         return ATM_OK;
     }
@@ -1973,6 +1984,18 @@ struct RefinedPlan : PlanBase {
         hist.clear();
         launches = outer.launches = inner.launches = 0;
         long long counted = 0;
+        if (gLoop) {
+            ATM_CK(cudaEventRecord(ev0, st));
+            ATM_CK(cudaGraphLaunch(gLoop, st));
+            ATM_CK(cudaEventRecord(ev1, st));
+            ATM_CK(cudaEventSynchronize(ev1));
+            float ms = 0;
+            ATM_CK(cudaEventElapsedTime(&ms, ev0, ev1));
+            atm_status s = loop_result(&R);
+            R.time_ms = ms;
+            if (res) *res = R;
+            return s;
+        }
         ATM_CK(cudaEventRecord(ev0, st));
         if (gA) { ATM_CK(cudaGraphLaunch(gA, st)); counted += kernels_outer(); }
         else ATM_TRY(outer.run(outer.resid_full));
@@ -2030,11 +2053,77 @@ struct RefinedPlan : PlanBase {
     {
         return fail(ATM_ERR_UNSUPPORTED, "the learned propagator is not available in the refined mode");
     }
-    atm_status add_loop(cudaGraph_t) override
+    // Device-side refinement loop: FP64 residual, then while a kernel finds it
+    // above tol (and under max_iter, not diverging): FP32 inner cycles, update,
+    // FP64 residual.  Added to g as a conditional WHILE node (atm_batch_solve
+    // puts several handles' loops in one graph).
+    atm_status add_loop(cudaGraph_t g) override
     {
-        return fail(ATM_ERR_UNSUPPORTED, "device-side loops are not available in the refined mode");
+        if (st == nullptr) return fail(ATM_ERR_INVALID_ARG, "device-side loops need a non-default stream");
+        cudaGraphConditionalHandle h;
+        ATM_CK(cudaGraphConditionalHandleCreate(&h, g, 0, 0));
+        outer.no_events = inner.no_events = true;
+        cudaError_t e = cudaStreamBeginCaptureToGraph(st, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) {
+            outer.no_events = inner.no_events = false;
+            return fail(ATM_ERR_CUDA, "capture failed: %s", cudaGetErrorString(e));
+        }
+        outer.enqueue(outer.resid_full);
+        loop_decide_kernel<<<1, 1, 0, st>>>(outer.norm_cur, outer.loop_hist, outer.loop_state, sv.max_iter, sv.tol, h, 1);
+        cudaStreamCaptureStatus cs;
+        const cudaGraphNode_t *deps = nullptr;
+        size_t nd = 0;
+        cudaGraph_t cgr = nullptr;
+        e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &cgr, &deps, nullptr, &nd);
+        cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t node;
+        if (e == cudaSuccess) e = cudaGraphAddNode(&node, g, deps, nullptr, nd, &cp);
+        cudaGraph_t tmp = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(st, &tmp);
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+            outer.no_events = inner.no_events = false;
+            return fail(ATM_ERR_CUDA, "building the loop failed: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+        }
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        e = cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            enqueue_inner();
+            outer.enqueue(outer.resid_full);
+            loop_decide_kernel<<<1, 1, 0, st>>>(outer.norm_cur, outer.loop_hist, outer.loop_state, sv.max_iter, sv.tol,
+                                                h, 0);
+            e = cudaStreamEndCapture(st, &tmp);
+        }
+        outer.no_events = inner.no_events = false;
+        if (e != cudaSuccess) return fail(ATM_ERR_CUDA, "capturing the loop body failed: %s", cudaGetErrorString(e));
+        if (outer.launch_failed || inner.launch_failed) return fail(ATM_ERR_CUDA, "a launch failed while building the loop");
+        return ATM_OK;
     }
-    atm_status loop_result(atm_result *) override { return fail(ATM_ERR_UNSUPPORTED, "refined mode"); }
+
+    atm_status loop_result(atm_result *res) override
+    {
+        double stv[4];
+        ATM_CK(cudaMemcpy(stv, outer.loop_state, sizeof(stv), cudaMemcpyDeviceToHost));
+        const int it = (int)stv[0];
+        hist.assign((size_t)it + 1, 0.0);
+        ATM_CK(cudaMemcpy(hist.data(), outer.loop_hist, sizeof(double) * (it + 1), cudaMemcpyDeviceToHost));
+        launches = kernels_outer() + 1 + (long long)it * (kernels_inner() + kernels_outer() + 1);
+        atm_result R;
+        std::memset(&R, 0, sizeof(R));
+        R.iterations = it;
+        R.initial_residual = hist.front();
+        R.final_residual = hist.back();
+        R.converged = hist.back() <= sv.tol;
+        atm_status status = ATM_OK;
+        if (!std::isfinite(hist.back()) || (int)stv[1] >= 3)
+            status = fail(ATM_ERR_DIVERGED, "residual diverged (%g after %d cycles)", hist.back(), it);
+        else if (!R.converged)
+            status = fail(ATM_ERR_NOT_CONVERGED, "residual %g > tol %g after %d cycles", hist.back(), sv.tol, it);
+        if (res) *res = R;
+        return status;
+    }
     atm_status apply_prop(int level, const double *in, double *o, int n) override
     {
         return inner.apply_prop(level, in, o, n);

@@ -40,6 +40,12 @@ CASES = [
     dict(kind="ac", nx=64, ny=64, dt=1e-4, nt=300, m=(4, 2, 2), k=5, nu=1, tol=1e-9, max_iter=60,
          algorithm="mgrit"),
     dict(kind="heat2d", nx=64, ny=64, dt=1e-3, nt=257, m=(16,), k=2, nu=1, tol=1e-30, max_iter=3),
+    dict(kind="ac", nx=64, ny=64, dt=1e-4, nt=257, m=(4, 4), k=4, nu=1, tol=1e-9, max_iter=40,
+         precision=atm.FP32_REFINED),
+    dict(kind="ac", nx=128, ny=128, dt=1e-4, nt=257, m=(4, 4), k=4, nu=1, tol=1e-9, max_iter=40,
+         precision=atm.FP32_REFINED, cpoint_only=True),
+    dict(kind="heat1d", nx=127, dt=1 / 1024, nt=1025, m=(8,), k=4, nu=1, tol=1e-10, max_iter=40,
+         precision=atm.FP32_REFINED, cpoint_only=True),
 ]
 
 

@@ -290,3 +290,38 @@ def test_fp32_refined_reaches_fp64_accuracy(torch, case):
     full = oracle.full_residual_norm(oc, np.ascontiguousarray(u))
     floor = 4 * 2.2e-16 * np.sqrt(u.size) * np.abs(u).max()
     assert abs(full - res[atm.FP32_REFINED][2][-1]) <= 1e-3 * full + floor
+
+
+def test_fp32_propagators_1024(torch):
+    """The 1024^2 kernels (FP32 only): row lines of 32 values per lane, column
+    chunks of 64 rows; every level of the large configuration's hierarchy
+    (m = (32, 4, 4)), against the oracle at the FP32 bar scaled by the line
+    condition number 1 + 4a (a = 13 on the fine level)."""
+    kw = dict(kind="ac", nx=1024, ny=1024, dt=2.5e-5, nt=129, m=(32, 2))
+    oc, gp, gs = pair(precision=atm.FP32, **kw)
+    s = atm.Solver(gp, gs)
+    x = I.uniform_field((2, 1024, 1024), 21, -1.0, 1.0)
+    for level, a in [(0, 0.5 * 2.5e-5 * 1024 ** 2), (1, 32 * 2.5e-5 * 1024 ** 2), (2, 64 * 2.5e-5 * 1024 ** 2)]:
+        want = oracle.apply_prop(oc, level, x)
+        got = s.apply_propagator(level, dev(torch, x)).cpu().numpy()
+        tol = max(3e-6, 2.5e-7 * (1 + 4 * a))
+        for j in range(2):
+            assert rel_l2(got[j], want[j]) <= tol, (level, j, rel_l2(got[j], want[j]), tol)
+
+
+def test_fp32_solve_1024_reaches_the_fixed_point(torch):
+    """AT-MGRIT at 1024^2 (FP32, C-point storage, the large configuration's
+    coarsening m = (32, 4), k = 3) converges to the FP64 sequential solution."""
+    kw = dict(kind="ac", nx=1024, ny=1024, dt=2.5e-5, nt=257, m=(32, 4), k=3, nu=1, tol=1e-2, max_iter=20,
+              precision=atm.FP32, cpoint_only=True)
+    oc, gp, gs = pair(**kw)
+    s = atm.Solver(gp, gs)
+    u0 = I.uniform_field((1024, 1024), 22)
+    s.set_initial_condition(dev(torch, u0))
+    r = s.solve()
+    h = s.residual_history()
+    print("\n1024^2 residual history:", " ".join(f"{v:.3e}" for v in h))
+    assert r["converged"], r
+    seq = oracle.sequential(oc, u0)
+    got = s.solution(256, 1).cpu().numpy()[0]
+    assert rel_l2(got, seq[256]) <= 1e-4
