@@ -394,7 +394,7 @@ def main():
     ap.add_argument("--nu", type=int, choices=[0, 1], default=None,
                     help="relaxation: 0 F, 1 FCF (default: the workload's); in fp32r it shapes the inner cycles")
     ap.add_argument("--inner-cycles", type=int, default=0,
-                    help="fp32r: FP32 V-cycles per FP64 refinement step (0: the library default, 4)")
+                    help="fp32r: FP32 V-cycles per FP64 refinement step (0: the library default, 5)")
     ap.add_argument("--max-iter", type=int, default=None, help="override the workload's cycle cap")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -547,7 +547,7 @@ def main():
                            **({"nu": args.nu} if args.nu is not None else {}),
                            "algorithm": args.algorithm, "parallelism": f"{world} independent problems",
                            "sweep_kernel": args.sweep_kernel, "storage": args.storage,
-                           "inner_cycles": (args.inner_cycles or 4) if args.precision == "fp32r" else None,
+                           "inner_cycles": (args.inner_cycles or 5) if args.precision == "fp32r" else None,
                            "l2": "working set larger than L2 (workspace %.2f GB; one level-0 launch reads and "
                                  "writes %.0f MB)" % (atm.workspace_size(prob, desc) / 1e9,
                                                       2 * jobs * n_val * (4 if args.precision == "fp32" else 8) / 1e6)},

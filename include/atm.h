@@ -123,10 +123,10 @@ typedef struct {
                                          shared memory; FP32 on 64^2, 128^2, 256^2, 512^2 grids,
                                          split kernels elsewhere) */
     int refine_inner_cycles;          /* ATM_FP32_REFINED: FP32 V-cycles on the correction per FP64
-                                         residual, 1..16 (0: 4).  More cycles trade FP64 residual
+                                         residual, 1..16 (0: 5).  More cycles trade FP64 residual
                                          passes for FP32 cycles while the inner iteration still
                                          contracts (256^2 Allen-Cahn to 1e-8: 14 FP64 passes with
-                                         one inner cycle, 6 with three, 5 with four) */
+                                         one inner cycle, 6 with three, 4 with five) */
     int cpoint_storage_only;          /* 1: level 0 keeps only its C-points (t = i m_0) and one
                                          working state per C-interval, about 3 N_t / m_0 states
                                          instead of N_t + N_t / m_0 (Sec. 2.1: the F-points of an

@@ -1975,7 +1975,7 @@ struct RefinedPlan : PlanBase {
         return 3 + inner_cycles() * inner.kernels_in(inner.inner_cycle);
     }
 
-    int inner_cycles() const { return sv.refine_inner_cycles > 0 ? sv.refine_inner_cycles : 4; }
+    int inner_cycles() const { return sv.refine_inner_cycles > 0 ? sv.refine_inner_cycles : 5; }
 
     atm_status solve(atm_result *res) override
     {

@@ -261,7 +261,7 @@ __device__ __forceinline__ void warp_line_solve(T (&q)[C], const TriCoef<T> &c, 
 // stored to out; with a residual (jb.sub), r = val - sub is stored to out2 and
 // r^2 added to acc (FP64).  The caller tests jb.sub once per job, so jobs
 // without a residual issue no FP64 work.
-template <typename T, bool RES>
+template <typename T, bool RES, bool OUTF = false>
 __device__ __forceinline__ void apply_epilogue(const Job<T> &jb, size_t idx, T phi, int neg, double &acc)
 {
     T val = neg ? -phi : phi;
@@ -273,7 +273,7 @@ __device__ __forceinline__ void apply_epilogue(const Job<T> &jb, size_t idx, T p
         if (jb.out2) jb.out2[idx] = r;
     }
     if (jb.out) jb.out[idx] = val;
-    if (jb.outf) jb.outf[idx] = (float)val;
+    if (OUTF) jb.outf[idx] = (float)val;
 }
 
 // Deterministic CTA sum of one double per thread; thread 0 gets the total.
@@ -387,7 +387,10 @@ __global__ void __launch_bounds__(256) row_sweep_kernel(const __grid_constant__ 
         } else {
 #pragma unroll
             for (int k = 0; k < C; ++k)
-                if (k < valid) apply_epilogue<T, false>(jb, row_off + x0 + k, q[k], a.neg, acc);
+                if (k < valid) {
+                    if (jb.outf) apply_epilogue<T, false, true>(jb, row_off + x0 + k, q[k], a.neg, acc);
+                    else apply_epilogue<T, false>(jb, row_off + x0 + k, q[k], a.neg, acc);
+                }
         }
         if (a.partials) {
             __shared__ double sh[32];
@@ -486,6 +489,10 @@ __global__ void __launch_bounds__(W * 32, 1024 / (W * 32)) col_sweep_kernel(cons
     if (jb.sub) {
 #pragma unroll
         for (int k = 0; k < CY; ++k) apply_epilogue<T, true>(jb, (size_t)(y0 + k) * nx + x, q[k], a.neg, acc);
+    } else if (jb.outf) {
+#pragma unroll
+        for (int k = 0; k < CY; ++k)
+            apply_epilogue<T, false, true>(jb, (size_t)(y0 + k) * nx + x, q[k], a.neg, acc);
     } else {
 #pragma unroll
         for (int k = 0; k < CY; ++k) apply_epilogue<T, false>(jb, (size_t)(y0 + k) * nx + x, q[k], a.neg, acc);
