@@ -64,8 +64,12 @@ enum {
 enum {
     ATM_PROP_SPLIT_BE = 0, /* (I - D Lx) y = w, (I - D Ly) u' = y */
     ATM_PROP_PR_ADI = 1,   /* (I - D/2 Lx) u* = (I + D/2 Ly) w, (I - D/2 Ly) u' = (I + D/2 Lx) u* */
-    ATM_PROP_LEARNED = 2   /* coarse_prop only: level 1 uses the learned Psi_NN (weights from
+    ATM_PROP_LEARNED = 2,  /* coarse_prop only: level 1 uses the learned Psi_NN (weights from
                               atm_set_learned_coarse), deeper levels split-BE ADI */
+    ATM_PROP_LEARNED_CORRECTION = 3  /* coarse_prop only: level 1 uses split-BE ADI plus the learned
+                              network's correction, Psi(u) = Psi_split(u) + N(u), where the network
+                              computes u + N(u) (train it on targets Phi^m(u) - Psi_split(u) + u);
+                              deeper levels split-BE ADI */
 };
 
 /* Reaction part of the coarse Allen-Cahn propagators (levels >= 1, step D):

@@ -16,7 +16,7 @@ import numpy as np
 from . import build as _build
 
 HEAT1D, HEAT2D, ALLEN_CAHN = 0, 1, 2
-PROP_SPLIT_BE, PROP_PR_ADI, PROP_LEARNED = 0, 1, 2
+PROP_SPLIT_BE, PROP_PR_ADI, PROP_LEARNED, PROP_LEARNED_CORRECTION = 0, 1, 2, 3
 REACT_EXACT, REACT_SUBSTEPS = 0, 1
 SEQUENTIAL, MGRIT, AT_MGRIT = 0, 1, 2
 FP64, FP32, FP32_REFINED = 0, 1, 2
@@ -323,7 +323,8 @@ class Solver:
         return dict(kernel=names.get(cfg[0], str(cfg[0])), ctas=cfg[1], threads=cfg[2], rows=cfg[3], chunk=cfg[4])
 
     def set_learned_coarse(self, params):
-        """Network weights (torch float32 device tensor) for coarse_prop = PROP_LEARNED."""
+        """Network weights (torch float32 device tensor) for coarse_prop = PROP_LEARNED or
+        PROP_LEARNED_CORRECTION."""
         params = params.to(device=self.device, dtype=self.torch.float32).contiguous()
         self._enter()
         _check(load().atm_set_learned_coarse(self.handle, ctypes.c_void_p(params.data_ptr())))

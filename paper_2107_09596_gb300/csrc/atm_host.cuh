@@ -203,13 +203,13 @@ inline LevelOp<T> make_level_op(const atm_problem &pb, const atm_solver &sv, int
         return op;
     }
     a.ny = pb.ny;
-    if (l == 1 && sv.coarse_prop == ATM_PROP_LEARNED) {
+    if (l == 1 && (sv.coarse_prop == ATM_PROP_LEARNED || sv.coarse_prop == ATM_PROP_LEARNED_CORRECTION)) {
         op.learned = true;
         return op;
     }
     const double dx = pb.lx / pb.nx, dy = pb.ly / pb.ny;
     int prop = (l == 0) ? sv.fine_prop : sv.coarse_prop;
-    if (prop == ATM_PROP_LEARNED) prop = ATM_PROP_SPLIT_BE;
+    if (prop == ATM_PROP_LEARNED || prop == ATM_PROP_LEARNED_CORRECTION) prop = ATM_PROP_SPLIT_BE;
     const bool pr = (prop == ATM_PROP_PR_ADI);
     const double f = pr ? 0.5 * D : D;
     const double ax = f / (dx * dx), ay = f / (dy * dy);
@@ -281,6 +281,8 @@ struct LaunchRec {
     int npartials = 0;
     double *norm_out = nullptr;
     int prof_slot = -1;   // >= 0: time this sweep's kernels with event slot prof_slot
+    bool has_pre = false; // learned correction: classical pass over the jobs at pre_index first
+    size_t pre_index = 0;
 };
 
 using Phase = std::vector<LaunchRec>;
@@ -373,6 +375,8 @@ struct Plan : PlanBase {
     Job<T> *d_dyn = nullptr;             // jobs of atm_apply_propagator
     // learned propagator (level 1 when coarse_prop = ATM_PROP_LEARNED)
     bool any_learned = false;
+    bool hybrid = false;                 // ATM_PROP_LEARNED_CORRECTION: classical Psi plus the network's N(u)
+    T *hyb = nullptr;                    // hybrid: the classical Psi of each job's input (maxbatch states)
     bool net_ready = false;
     bool launch_failed = false;          // a launch helper reported an error
     bool no_events = false;              // capturing a conditional body: no event nodes
@@ -479,12 +483,12 @@ struct Plan : PlanBase {
         if (sv.coarse_reaction != ATM_REACT_EXACT && sv.coarse_reaction != ATM_REACT_SUBSTEPS)
             return fail(ATM_ERR_INVALID_ARG, "unknown coarse_reaction %d", sv.coarse_reaction);
         if (!is1d) {
-            if (sv.fine_prop < 0 || sv.fine_prop > 1 || sv.coarse_prop < 0 || sv.coarse_prop > 2)
+            if (sv.fine_prop < 0 || sv.fine_prop > 1 || sv.coarse_prop < 0 || sv.coarse_prop > 3)
                 return fail(ATM_ERR_INVALID_ARG, "unknown propagator");
         }
         if (sv.cpoint_storage_only && sv.algorithm == ATM_SEQUENTIAL && sv.m[0] == 1)
             return fail(ATM_ERR_INVALID_ARG, "C-point storage needs m[0] >= 2 (or 0 for the default 16)");
-        if (sv.coarse_prop == ATM_PROP_LEARNED) {
+        if (sv.coarse_prop == ATM_PROP_LEARNED || sv.coarse_prop == ATM_PROP_LEARNED_CORRECTION) {
             if (is1d) return fail(ATM_ERR_INVALID_ARG, "the learned propagator is for the 2D problems");
             if (sv.algorithm == ATM_SEQUENTIAL) return fail(ATM_ERR_INVALID_ARG, "the learned propagator needs levels >= 2");
             if (((size_t)pb.nx * pb.ny) % 2048 != 0) return fail(ATM_ERR_INVALID_ARG, "the learned propagator needs nx*ny % 2048 == 0");
@@ -554,7 +558,15 @@ struct Plan : PlanBase {
             if (r.npartials > npartials_max) npartials_max = r.npartials;
         }
         if (r.njobs > maxbatch) maxbatch = r.njobs;
+        std::vector<Job<T>> pre;
+        if (hybrid && l < (int)lv.size() && lv[l].learned)
+            for (int k = 0; k < r.njobs; ++k) pre.push_back(job(js[k].in, hyb ? st_ptr(hyb, k) : nullptr));
         jobs.insert(jobs.end(), js.begin(), js.end());
+        if (!pre.empty()) {
+            r.has_pre = true;
+            r.pre_index = jobs.size();
+            jobs.insert(jobs.end(), pre.begin(), pre.end());
+        }
         ph.push_back(r);
     }
 
@@ -908,7 +920,9 @@ struct Plan : PlanBase {
         norm_cur = take<double>(1);
         loop_hist = take<double>((size_t)(sv.max_iter > 0 ? sv.max_iter : 0) + 2);
         loop_state = take<double>(4);
-        any_learned = !is1d && L > 1 && sv.coarse_prop == ATM_PROP_LEARNED;
+        any_learned = !is1d && L > 1 &&
+                      (sv.coarse_prop == ATM_PROP_LEARNED || sv.coarse_prop == ATM_PROP_LEARNED_CORRECTION);
+        hybrid = any_learned && sv.coarse_prop == ATM_PROP_LEARNED_CORRECTION;
         if (any_learned) {
             nn_params = take<float>((size_t)nn::param_count());
             nn_packed = take<unsigned char>(nn::packed_bytes());
@@ -916,6 +930,7 @@ struct Plan : PlanBase {
             nn_scratch = take<unsigned char>(nn::infer_scratch_bytes(ch, pb.ny, pb.nx));
             nn_err = take<int>(1);
             snapshot = take<T>(n0);
+            if (hybrid) hyb = take<T>((size_t)maxbatch * nsp);
         }
         for (int l = 0; l < L; ++l) {
             if (is1d) lv[l].dir_w = take<T>((size_t)pb.nx);
@@ -932,7 +947,7 @@ struct Plan : PlanBase {
         }
         d_jobs = take<Job<T>>(jobs.size() + 1);
         d_ajobs = take<AxpyJob<T>>(ajobs.size() + 1);
-        d_dyn = take<Job<T>>((size_t)midcap);
+        d_dyn = take<Job<T>>((size_t)2 * midcap);   // jobs, then (learned correction) their classical pass
         off = (off + 255) & ~(size_t)255;
         return ATM_OK;
     }
@@ -958,7 +973,10 @@ struct Plan : PlanBase {
         long long n = 0;
         for (const LaunchRec &r : ph) {
             if (r.type != L_SWEEP || is1d) n += 1;
-            else if (lv[r.level].learned || lv[r.level].fz >= 0) n += sweep_pairs(r.level, r.njobs);
+            else if (lv[r.level].learned || lv[r.level].fz >= 0) {
+                n += sweep_pairs(r.level, r.njobs);
+                if (lv[r.level].learned && hybrid) n += 2 * ((r.njobs + midcap - 1) / midcap);
+            }
             else n += 2 * sweep_pairs(r.level, r.njobs);
         }
         return n;
@@ -976,12 +994,33 @@ struct Plan : PlanBase {
         return cs > midcap ? midcap : cs;
     }
 
-    void launch_sweep(int l, const Job<T> *djobs, int njobs, int neg, double *part, int slot = -1)
+    // The classical operator of a learned level on `djobs` (the split row and
+    // column kernels), chunked to the intermediate.
+    void launch_classical(int l, const Job<T> *djobs, int njobs)
+    {
+        const LevelOp<T> &op = lv[l].classical;
+        SweepArgs<T> a = op.args;
+        a.neg = 0;
+        a.mid = mid;
+        a.partials = nullptr;
+        for (int j0 = 0; j0 < njobs; j0 += midcap) {
+            const int nj = njobs - j0 < midcap ? njobs - j0 : midcap;
+            a.jobs = djobs + j0;
+            op.row<<<dim3(pb.ny / op.rows_per_cta, nj), 32 * op.rows_per_cta, op.row_smem, st>>>(a);
+            op.col<<<dim3(pb.nx / 32, nj), 32 * op.col_warps, 0, st>>>(a);
+        }
+    }
+
+    void launch_sweep(int l, const Job<T> *djobs, int njobs, int neg, double *part, int slot = -1,
+                      const Job<T> *pre = nullptr)
     {
         const Level<T> &Lv = lv[l];
         if (Lv.learned) {
             const int ch = maxbatch < nn::kInferChunk ? maxbatch : nn::kInferChunk;
-            if (nn::infer_jobs<T>(net, djobs, njobs, neg, part, pb.ny, pb.nx, nn_scratch, ch, nn_err, st) != ATM_OK)
+            // learned correction: Psi_split(in) into hyb first, then out = hyb + N(in)
+            if (hybrid && pre) launch_classical(l, pre, njobs);
+            if (nn::infer_jobs<T>(net, djobs, njobs, neg, part, pb.ny, pb.nx, nn_scratch, ch, nn_err, st,
+                                  (hybrid && pre) ? hyb : nullptr) != ATM_OK)
                 launch_failed = true;
             return;
         }
@@ -1250,7 +1289,8 @@ struct Plan : PlanBase {
     {
         for (const LaunchRec &r : ph) {
             if (r.type == L_SWEEP)
-                launch_sweep(r.level, d_jobs + r.job_index, r.njobs, r.neg, r.partials, r.prof_slot);
+                launch_sweep(r.level, d_jobs + r.job_index, r.njobs, r.neg, r.partials, r.prof_slot,
+                             r.has_pre ? d_jobs + r.pre_index : nullptr);
             else if (r.type == L_AXPY)
                 launch_axpy(d_ajobs + r.job_index, r.njobs);
             else
@@ -1737,8 +1777,13 @@ struct Plan : PlanBase {
             T *po = f64 ? reinterpret_cast<T *>(out) + (size_t)s * nsp : sout + (size_t)s * nsp;
             js.push_back(job(pi, po));
         }
-        ATM_CK(cudaMemcpyAsync(d_dyn, js.data(), js.size() * sizeof(Job<T>), cudaMemcpyHostToDevice, st));
-        launch_sweep(level, d_dyn, n, 0, nullptr);
+        const bool pre = lv[level].learned && hybrid;
+        if (pre)
+            for (int s2 = 0; s2 < n; ++s2) js.push_back(job(js[s2].in, st_ptr(hyb, s2)));
+        ATM_CK(cudaMemcpyAsync(d_dyn, js.data(), (size_t)n * sizeof(Job<T>), cudaMemcpyHostToDevice, st));
+        if (pre)
+            ATM_CK(cudaMemcpyAsync(d_dyn + midcap, js.data() + n, (size_t)n * sizeof(Job<T>), cudaMemcpyHostToDevice, st));
+        launch_sweep(level, d_dyn, n, 0, nullptr, -1, pre ? d_dyn + midcap : nullptr);
         if (!f64) convert_from_T(sout, out, (size_t)n * nsp);
         ATM_CK(cudaGetLastError());
         ATM_CK(cudaStreamSynchronize(st));
@@ -1813,7 +1858,8 @@ struct Plan : PlanBase {
 
     atm_status set_learned(const float *d_params) override
     {
-        if (!any_learned) return fail(ATM_ERR_INVALID_ARG, "the handle was not created with coarse_prop = ATM_PROP_LEARNED");
+        if (!any_learned)
+            return fail(ATM_ERR_INVALID_ARG, "the handle was not created with a learned coarse propagator");
         if (!d_params) return fail(ATM_ERR_INVALID_ARG, "null parameters");
         ATM_CK(cudaMemcpyAsync(nn_params, d_params, (size_t)nn::param_count() * sizeof(float), cudaMemcpyDeviceToDevice, st));
         ATM_TRY(nn::pack(nn_params, &net, st));

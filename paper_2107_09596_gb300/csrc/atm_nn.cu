@@ -103,7 +103,7 @@ size_t infer_scratch_bytes(int chunk, int H, int W)
 
 template <typename T>
 atm_status infer_jobs(const Net &net, const Job<T> *d_jobs, int njobs, int neg, double *partials, int H, int W,
-                      void *scratch, int chunk, int *d_err, cudaStream_t st)
+                      void *scratch, int chunk, int *d_err, cudaStream_t st, const T *skip)
 {
     ATM_TRY(check_grid(H, W));
     const size_t P = (size_t)H * W;
@@ -141,6 +141,7 @@ atm_status infer_jobs(const Net &net, const Job<T> *d_jobs, int njobs, int neg, 
         a.bias = bias_of(net.params, kLayers - 1);
         a.neg = neg;
         a.partials = partials ? partials + (size_t)j0 * tiles : nullptr;
+        a.skip = skip ? skip + (size_t)j0 * P : nullptr;
         ATM_TRY((launch_conv<T, IN_BF16, 16, EPI_LAST>(a, nj, st)));
     }
     ATM_CK(cudaGetLastError());
@@ -160,9 +161,9 @@ template atm_status prepare<float>();
 template atm_status prepare<double>();
 
 template atm_status infer_jobs<float>(const Net &, const Job<float> *, int, int, double *, int, int, void *, int, int *,
-                                      cudaStream_t);
+                                      cudaStream_t, const float *);
 template atm_status infer_jobs<double>(const Net &, const Job<double> *, int, int, double *, int, int, void *, int,
-                                       int *, cudaStream_t);
+                                       int *, cudaStream_t, const double *);
 
 // ---------------------------------------------------------------------------
 // Training buffers for a batch of B images

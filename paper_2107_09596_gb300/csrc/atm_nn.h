@@ -34,9 +34,11 @@ atm_status pack(const float *d_params, Net *net, cudaStream_t st);
 template <typename T>
 atm_status prepare();
 
+// skip (may be null): per-job states [njobs][H W] used in place of the job's
+// input as the skip term, out = skip + N(in) (the learned correction form).
 template <typename T>
 atm_status infer_jobs(const Net &net, const Job<T> *d_jobs, int njobs, int neg, double *partials, int H, int W,
-                      void *scratch, int chunk, int *d_err, cudaStream_t st);
+                      void *scratch, int chunk, int *d_err, cudaStream_t st, const T *skip = nullptr);
 
 constexpr int kInferChunk = 32;
 constexpr int kNNTile = 128;       // pixels per tensor-core tile (partial sums per image = nx*ny/128)

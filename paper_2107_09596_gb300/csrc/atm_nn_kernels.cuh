@@ -95,6 +95,7 @@ struct ConvArgs {
     float *out_f32;                  // EPI_LAST without jobs: u + z [img][p]
     const float *u_f32;              // EPI_LAST without jobs: the network input u [img][p]
     const Job<T> *jobs;              // EPI_LAST with jobs: the propagator epilogue per image
+    const T *skip;                   // EPI_LAST with jobs: skip term per image [img][p] (null: the job's input)
     int neg;
     double *partials;                // EPI_LAST with jobs and residuals: per-CTA sums of r^2
     int *err;                        // set to 1 when an MMA wait times out
@@ -264,7 +265,7 @@ __global__ void __launch_bounds__(kTile) conv_umma_kernel(const __grid_constant_
         const size_t q = (size_t)p;
         if (a.jobs) {
             const Job<T> jb = a.jobs[img];
-            const T phi = jb.in[q] + (T)z;
+            const T phi = (a.skip ? a.skip[(size_t)img * a.H * a.W + q] : jb.in[q]) + (T)z;
             double r2 = 0.0;
             if (jb.sub) apply_epilogue<T, true>(jb, q, phi, a.neg, r2);
             else apply_epilogue<T, false>(jb, q, phi, a.neg, r2);
