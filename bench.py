@@ -252,10 +252,12 @@ def max_over_ranks(dist, value, device=None):
     return float(t.item())
 
 
-def train_learned(atm, w, device, steps, seeds=(101, 102, 103, 104, 105), batch=8):
+def train_learned(atm, w, device, steps, seeds=(101, 102, 103, 104, 105), batch=8, correction=False):
     """Psi_NN for the workload's level-1 step (m_0 fine steps): pairs (u_t, u_{t+m_0})
     of fine trajectories from other seeds, produced by the library's sequential
-    stepping (the states that F-relaxation generates at convergence), then Adam."""
+    stepping (the states that F-relaxation generates at convergence), then Adam.
+    correction: train the network on Phi^m0(u) - Psi_split(u) + u, for the
+    corrected propagator Psi_split(u) + N(u)."""
     import torch
     m0 = w["m"][0]
     prob, desc = make_desc(atm, w, "seq", atm.FP32, profile=False)
@@ -272,6 +274,13 @@ def train_learned(atm, w, device, steps, seeds=(101, 102, 103, 104, 105), batch=
     inputs = torch.cat(ins).contiguous()
     targets = torch.cat(outs).contiguous()
     del ins, outs
+    if correction:
+        prob, desc = make_desc(atm, w, "at", atm.FP64, profile=False)
+        cl = atm.Solver(prob, desc, device=device)
+        for i in range(0, inputs.shape[0], 64):
+            x = inputs[i:i + 64].to(torch.float64)
+            targets[i:i + 64] -= (cl.apply_propagator(1, x) - x).to(torch.float32)
+        cl.close()
     net = atm.LearnedCoarse(device=device)
     flat = np.concatenate([np.concatenate([wt.ravel(), b.ravel()]) for (wt, b) in I.conv_net_init(7)])
     params = torch.as_tensor(flat, dtype=torch.float32, device=device)
@@ -293,7 +302,8 @@ def make_desc(atm, w, algorithm, precision, profile, coarse="classical", sweep="
     desc = atm.make_solver(alg, m=w["m"], k=w["k"], nu=w["nu"] if nu is None else nu, tol=w["tol"],
                            max_iter=w["max_iter"], precision=precision, use_graph=True,
                            profile=profile,
-                           coarse_prop=atm.PROP_LEARNED if coarse == "learned" else atm.PROP_SPLIT_BE,
+                           coarse_prop={"learned": atm.PROP_LEARNED, "correction": atm.PROP_LEARNED_CORRECTION}.get(
+                               coarse, atm.PROP_SPLIT_BE),
                            sweep_kernel={"auto": atm.SWEEP_AUTO, "split": atm.SWEEP_SPLIT,
                                          "fused": atm.SWEEP_FUSED}[sweep],
                            cpoint_only=cpoint, inner_cycles=inner_cycles)
@@ -384,8 +394,9 @@ def main():
     ap.add_argument("--algorithm", choices=["at", "mgrit", "seq"], default="at")
     ap.add_argument("--precision", choices=["fp64", "fp32", "fp32r"], default="fp32r",
                     help="fp32r: FP32 propagation with FP64 refinement (the fastest form that reaches 1e-8)")
-    ap.add_argument("--coarse", choices=["classical", "learned"], default="classical",
-                    help="level-1 coarse propagator; 'learned' trains Psi_NN first (untimed)")
+    ap.add_argument("--coarse", choices=["classical", "learned", "correction"], default="classical",
+                    help="level-1 coarse propagator; 'learned' trains Psi_NN, 'correction' the network of "
+                         "Psi_split + N first (untimed)")
     ap.add_argument("--train-steps", type=int, default=2500)
     ap.add_argument("--sweep-kernel", choices=["auto", "split", "fused"], default="auto",
                     help="2D propagator kernels (auto: level 0 autotuned at create time)")
@@ -418,13 +429,14 @@ def main():
     atm._build.build()
     prec = {"fp64": atm.FP64, "fp32": atm.FP32, "fp32r": atm.FP32_REFINED}[args.precision]
     learned_info = None
-    if args.coarse == "learned":
-        nn_params, learned_info = train_learned(atm, w, device, args.train_steps)
+    if args.coarse in ("learned", "correction"):
+        nn_params, learned_info = train_learned(atm, w, device, args.train_steps,
+                                                correction=args.coarse == "correction")
     prob, desc = make_desc(atm, w, args.algorithm, prec, profile=True, coarse=args.coarse,
                            sweep=args.sweep_kernel, cpoint=args.storage == "cpoint",
                            inner_cycles=args.inner_cycles, nu=args.nu)
     solver = atm.Solver(prob, desc, device=device)
-    if args.coarse == "learned":
+    if args.coarse in ("learned", "correction"):
         solver.set_learned_coarse(nn_params)
     shape = solver.state_shape
     u0 = torch.as_tensor(initial_condition(w, rank), dtype=torch.float64, device=device)
