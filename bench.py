@@ -305,7 +305,7 @@ def make_desc(atm, w, algorithm, precision, profile, coarse="classical", sweep="
                            coarse_prop={"learned": atm.PROP_LEARNED, "correction": atm.PROP_LEARNED_CORRECTION}.get(
                                coarse, atm.PROP_SPLIT_BE),
                            sweep_kernel={"auto": atm.SWEEP_AUTO, "split": atm.SWEEP_SPLIT,
-                                         "fused": atm.SWEEP_FUSED}[sweep],
+                                         "fused": atm.SWEEP_FUSED, "chain": atm.SWEEP_CHAIN}[sweep],
                            cpoint_only=cpoint, inner_cycles=inner_cycles)
     return prob, desc
 
@@ -398,7 +398,7 @@ def main():
                     help="level-1 coarse propagator; 'learned' trains Psi_NN, 'correction' the network of "
                          "Psi_split + N first (untimed)")
     ap.add_argument("--train-steps", type=int, default=2500)
-    ap.add_argument("--sweep-kernel", choices=["auto", "split", "fused"], default="auto",
+    ap.add_argument("--sweep-kernel", choices=["auto", "split", "fused", "chain"], default="auto",
                     help="2D propagator kernels (auto: level 0 autotuned at create time)")
     ap.add_argument("--storage", choices=["cpoint", "full"], default="cpoint",
                     help="level-0 storage: C-points only (default) or every time point")

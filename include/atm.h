@@ -87,7 +87,7 @@ enum { ATM_SEQUENTIAL = 0, ATM_MGRIT = 1, ATM_AT_MGRIT = 2 };
 enum { ATM_FP64 = 0, ATM_FP32 = 1, ATM_FP32_REFINED = 2 };
 
 /* 2D propagator kernels (atm_solver.sweep_kernel). */
-enum { ATM_SWEEP_AUTO = 0, ATM_SWEEP_SPLIT = 1, ATM_SWEEP_FUSED = 2 };
+enum { ATM_SWEEP_AUTO = 0, ATM_SWEEP_SPLIT = 1, ATM_SWEEP_FUSED = 2, ATM_SWEEP_CHAIN = 3 };
 
 #define ATM_MAX_LEVELS 8
 
@@ -125,7 +125,10 @@ typedef struct {
                                          column kernel through an HBM intermediate), ATM_SWEEP_FUSED
                                          (one cluster kernel per application, the state held in
                                          shared memory; FP32 on 64^2, 128^2, 256^2, 512^2 grids,
-                                         split kernels elsewhere) */
+                                         split kernels elsewhere), ATM_SWEEP_CHAIN (as FUSED, and
+                                         every F-relaxation runs as one launch in which a cluster
+                                         applies an interval's m-1 steps to its state in shared
+                                         memory) */
     int refine_inner_cycles;          /* ATM_FP32_REFINED: FP32 V-cycles on the correction per FP64
                                          residual, 1..16 (0: 5).  More cycles trade FP64 residual
                                          passes for FP32 cycles while the inner iteration still
@@ -248,7 +251,7 @@ atm_status atm_get_kernel_profile(const atm_handle *h, int which, double *total_
 /* Kernels of level `level`'s propagator as chosen at atm_create (the
  * autotuner's pick on level 0 with ATM_SWEEP_AUTO).  Writes 5 ints:
  *   cfg[0] kernel: 0 split row + column kernels, 1 fused cluster kernel,
- *          2 learned network, 3 1D line kernel;
+ *          2 learned network, 3 1D line kernel, 4 chain kernel (F-relaxations);
  *   cfg[1] CTAs per state (fused: cluster size; split: column-kernel CTAs);
  *   cfg[2] threads per CTA (fused) or per column-kernel CTA (split);
  *   cfg[3] rows per column segment (fused) or per column-kernel thread (split);

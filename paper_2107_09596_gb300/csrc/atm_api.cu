@@ -86,7 +86,7 @@ atm_status check_args(const atm_problem *pb, const atm_solver *sv)
     if (!pb || !sv) return atm::fail(ATM_ERR_INVALID_ARG, "null problem or solver");
     if (sv->precision != ATM_FP64 && sv->precision != ATM_FP32 && sv->precision != ATM_FP32_REFINED)
         return atm::fail(ATM_ERR_INVALID_ARG, "unknown precision %d", sv->precision);
-    if (sv->sweep_kernel < ATM_SWEEP_AUTO || sv->sweep_kernel > ATM_SWEEP_FUSED)
+    if (sv->sweep_kernel < ATM_SWEEP_AUTO || sv->sweep_kernel > ATM_SWEEP_CHAIN)
         return atm::fail(ATM_ERR_INVALID_ARG, "unknown sweep_kernel %d", sv->sweep_kernel);
     if (sv->refine_inner_cycles < 0 || sv->refine_inner_cycles > 16)
         return atm::fail(ATM_ERR_INVALID_ARG, "refine_inner_cycles must be in [0, 16]");

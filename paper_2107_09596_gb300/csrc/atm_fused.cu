@@ -22,7 +22,47 @@ void add_shape(std::vector<FusedShape> &v, bool pr, bool react)
     v.push_back(f);
 }
 
+template <int C, int G, int NT, int LS>
+void add_chain(std::vector<FusedShape> &v, bool pr, bool react)
+{
+    FusedShape f;
+    if (pr) f.cfn = react ? fused_chain_kernel<C, G, NT, LS, true, true> : fused_chain_kernel<C, G, NT, LS, true, false>;
+    else f.cfn = react ? fused_chain_kernel<C, G, NT, LS, false, true> : fused_chain_kernel<C, G, NT, LS, false, false>;
+    f.G = G;
+    f.NT = NT;
+    f.LS = LS;
+    constexpr int NXP = 16 * C;
+    constexpr int P = NT >= NXP ? NT / NXP : 1;
+    f.smem = chain_smem_bytes(32 * C, P * LS, P);
+    v.push_back(f);
+}
+
 }  // namespace
+
+std::vector<FusedShape> chain_shapes(int nx, int ny, bool pr, bool react)
+{
+    std::vector<FusedShape> v;
+    if (nx == 64 && ny == 64) {
+        add_chain<2, 2, 256, 4>(v, pr, react);
+        add_chain<2, 1, 256, 8>(v, pr, react);
+        add_chain<2, 4, 256, 2>(v, pr, react);
+    }
+    if (nx == 128 && ny == 128) {
+        add_chain<4, 4, 256, 8>(v, pr, react);
+        add_chain<4, 2, 256, 16>(v, pr, react);
+        add_chain<4, 8, 256, 4>(v, pr, react);
+    }
+    if (nx == 256 && ny == 256) {
+        add_chain<8, 8, 256, 16>(v, pr, react);
+        add_chain<8, 16, 256, 8>(v, pr, react);
+        add_chain<8, 4, 256, 32>(v, pr, react);
+    }
+    if (nx == 512 && ny == 512) {
+        add_chain<16, 16, 256, 32>(v, pr, react);
+        add_chain<16, 16, 512, 16>(v, pr, react);
+    }
+    return v;
+}
 
 std::vector<FusedShape> fused_shapes(int nx, int ny, bool pr, bool react)
 {

@@ -470,3 +470,276 @@ __global__ void __launch_bounds__(NT) fused_sweep_kernel(const __grid_constant__
 }
 
 }  // namespace atm
+
+namespace atm {
+
+// A peer CTA's copy of a shared-memory location (32-bit shared::cluster
+// window address) and an 8-byte load from it; volatile so that the
+// translations stay inside the step loop instead of being hoisted (and held
+// in registers) across steps.
+__device__ __forceinline__ uint32_t fz_peer(const void *p, int rank)
+{
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+
+__device__ __forceinline__ float2 fz_ld_peer2(uint32_t addr)
+{
+    float2 v;
+    asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ float4 fz_ld_peer4(uint32_t addr)
+{
+    float4 v;
+    asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(addr) : "memory");
+    return v;
+}
+
+// Shared-memory bytes of a chain launch: two tiles (ping-pong) of R + 2 rows,
+// the carry arrays, and the two edge rows a CTA hands to its neighbours.
+__host__ __device__ constexpr size_t chain_smem_bytes(int nx, int R, int P)
+{
+    return 2 * (size_t)(R + 2) * nx * sizeof(float) + 3 * (size_t)P * nx * sizeof(float) +
+           2 * (size_t)nx * sizeof(float);
+}
+
+// S propagator applications in a row on one state per cluster (an interval's
+// F-relaxation chain, Sec. 2.1): step s applies job c S + s, whose input is
+// step s-1's value (in shared memory; only step 0 reads its input from
+// memory).  Each step: reaction on the resident tile (increments around the
+// job's base when it has one), row pass from one tile into the other (no
+// in-place hazard, no per-group barriers), column pass as in
+// fused_sweep_kernel, epilogue: val = (+-)Phi + g + h back into the tile and
+// to the job's output unless the next step writes the same state.  For PR
+// the CTAs exchange their edge rows through distributed shared memory before
+// the next step.  Jobs carry no residual (sub = null).
+template <int C, int G, int NT, int LS, bool PR, bool REACT>
+__global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1) fused_chain_kernel(const __grid_constant__ SweepArgs<float> a,
+                                                                          int S)
+{
+    constexpr int NW = NT / 32;
+    constexpr int NX = 32 * C;
+    constexpr int NXP = NX / 2;
+    constexpr int P = NT >= NXP ? NT / NXP : 1;
+    constexpr int XPT = NT >= NXP ? 1 : NXP / NT;
+    constexpr int R = P * LS;
+    constexpr int SEG = G * P;
+    constexpr int V = C >= 4 ? 4 : C;
+    constexpr int NY = G * R;
+    constexpr int RPI = NT * 4 / NX;
+    constexpr size_t TILE = (size_t)(R + 2) * NX;
+    static_assert(R % (2 * NW) == 0, "rows per CTA must be a multiple of twice the warps");
+    static_assert((NT * 4) % NX == 0 && (NY & (NY - 1)) == 0, "whole rows per pass, power-of-two ny");
+    static_assert(SEG <= 32 && LS <= kMaxChunk, "segment table sizes");
+
+    extern __shared__ __align__(16) unsigned char fz_smem[];
+    float *tA = reinterpret_cast<float *>(fz_smem);
+    float *tB = tA + TILE;
+    float2 *ce = reinterpret_cast<float2 *>(tB + TILE);
+    float2 *cb = ce + (size_t)P * NXP;
+    float2 *dn = cb + (size_t)P * NXP;
+    float *edge = reinterpret_cast<float *>(dn + (size_t)P * NXP);   // [2][NX]: own rows r0, r0 + R - 1
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int rank = G > 1 ? (int)cg::this_cluster().block_rank() : 0;
+    const int r0 = rank * R;
+    const Job<float> *cj = a.jobs + (size_t)blockIdx.y * S;
+    const int px = (threadIdx.x * 4) % NX, prow = (threadIdx.x * 4) / NX, pxs = fz_swz(px);
+    const int t_lo = PR ? 0 : 1, t_hi = PR ? R + 2 : R + 1;
+
+    // step 0's input (tile row t = state row r0 - 1 + t)
+    for (int t = t_lo + prow; t < t_hi; t += RPI)
+        fz_cp_async16(tA + (size_t)t * NX + pxs, cj[0].in + (size_t)((r0 - 1 + t) & (NY - 1)) * NX + px);
+    fz_cp_async_wait_all();
+
+    float *cur = tA, *nxt = tB;
+    const float2 rx0 = f2s(a.rx0), rx1 = f2s(a.rx1), cy0 = f2s(a.cy0), cy1 = f2s(a.cy1);
+    const TriCoef<float> &c = a.cy;
+    const float2 rho = f2s(c.rho), mls = f2s(c.scan[0]), inv1m = f2s(c.inv1m);
+    const int p = NT >= NXP ? threadIdx.x / NXP : 0;
+    const int xb = NT >= NXP ? threadIdx.x % NXP : threadIdx.x;
+    const int sg = rank * P + p;
+
+#pragma unroll 1
+    for (int s = 0; s < S; ++s) {
+        const Job<float> jb = cj[s];
+        // reaction of the resident rows (this thread's own pieces)
+        if (REACT) {
+            if (jb.base) {
+                for (int t = t_lo + prow; t < t_hi; t += RPI) {
+                    float4 *q4 = reinterpret_cast<float4 *>(cur + (size_t)t * NX + pxs);
+                    const float4 b = fz_ld4(jb.base + (size_t)((r0 - 1 + t) & (NY - 1)) * NX + px);
+                    const float4 v = *q4;
+                    *q4 = make_float4(react_delta(b.x, v.x, a.react, a.nsub), react_delta(b.y, v.y, a.react, a.nsub),
+                                      react_delta(b.z, v.z, a.react, a.nsub), react_delta(b.w, v.w, a.react, a.nsub));
+                }
+            } else {
+                for (int t = t_lo + prow; t < t_hi; t += RPI) {
+                    float4 *q4 = reinterpret_cast<float4 *>(cur + (size_t)t * NX + pxs);
+                    const float4 v = *q4;
+                    const float2 lo = react2(make_float2(v.x, v.y), a.react, a.nsub);
+                    const float2 hi = react2(make_float2(v.z, v.w), a.react, a.nsub);
+                    *q4 = make_float4(lo.x, lo.y, hi.x, hi.y);
+                }
+            }
+        }
+        __syncthreads();
+
+        // row pass: cur rows t-1 .. t+2 -> nxt rows t, t+1
+        const int x0 = lane * C;
+#pragma unroll 1
+        for (int g = 0; g < R / (2 * NW); ++g) {
+            const int t = 1 + 2 * (g * NW + warp);
+            float2 q[C];
+#pragma unroll
+            for (int i = 0; i < C; i += V) {
+                float w1[V], w2[V];
+                fz_load<V>(cur + (size_t)t * NX, x0 + i, w1);
+                fz_load<V>(cur + (size_t)(t + 1) * NX, x0 + i, w2);
+                if constexpr (PR) {
+                    float w0[V], w3[V];
+                    fz_load<V>(cur + (size_t)(t - 1) * NX, x0 + i, w0);
+                    fz_load<V>(cur + (size_t)(t + 2) * NX, x0 + i, w3);
+#pragma unroll
+                    for (int e = 0; e < V; ++e) {
+                        const float2 sm = add2(make_float2(w0[e], w1[e]), make_float2(w2[e], w3[e]));
+                        q[i + e] = fma2(rx1, sm, mul2(rx0, make_float2(w1[e], w2[e])));
+                    }
+                } else {
+#pragma unroll
+                    for (int e = 0; e < V; ++e) q[i + e] = mul2(rx0, make_float2(w1[e], w2[e]));
+                }
+            }
+            warp_line_solve2<C>(q, a.cx, lane);
+            if constexpr (PR) {
+                const float2 left = shfl2(q[C - 1], (lane + 31) & 31);
+                const float2 right = shfl2(q[0], (lane + 1) & 31);
+                float2 prev = left;
+#pragma unroll
+                for (int k = 0; k < C; ++k) {
+                    const float2 nx2 = k < C - 1 ? q[k + 1] : right;
+                    const float2 cu = q[k];
+                    q[k] = fma2(cy1, add2(prev, nx2), mul2(cy0, cu));
+                    prev = cu;
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < C; ++k) q[k] = mul2(cy0, q[k]);
+            }
+#pragma unroll
+            for (int i = 0; i < C; i += V) {
+                float lo[V], hi[V];
+#pragma unroll
+                for (int e = 0; e < V; ++e) { lo[e] = q[i + e].x; hi[e] = q[i + e].y; }
+                fz_store<V>(nxt + (size_t)t * NX, x0 + i, lo);
+                fz_store<V>(nxt + (size_t)(t + 1) * NX, x0 + i, hi);
+            }
+        }
+        __syncthreads();
+
+        // column pass on nxt rows 1 .. R
+        float *col0 = nxt + (size_t)(1 + p * LS) * NX;
+#pragma unroll 1
+        for (int xi = 0; xi < XPT; ++xi) {
+            const int xp = xb + xi * NT, xs = fz_swz(2 * xp);
+            float2 z = f2s(0.f);
+#pragma unroll
+            for (int k = 0; k < LS; ++k) {
+                float2 *e = reinterpret_cast<float2 *>(col0 + (size_t)k * NX + xs);
+                z = fma2(rho, z, *e);
+                *e = z;
+            }
+            ce[p * NXP + xp] = z;
+        }
+        if constexpr (G > 1) cg::this_cluster().sync(); else __syncthreads();
+#pragma unroll 1
+        for (int xi = 0; xi < XPT; ++xi) {
+            const int xp = xb + xi * NT, xs = fz_swz(2 * xp);
+            float2 tot = f2s(0.f), pre = f2s(0.f);
+#pragma unroll
+            for (int j = 0; j < SEG; ++j) {
+                const float2 *src = ce + (j % P) * NXP + xp;
+                float2 ev;
+                if constexpr (G > 1) ev = fz_ld_peer2(fz_peer(src, j / P));
+                else ev = *src;
+                if (j == sg) pre = tot;
+                tot = fma2(mls, tot, ev);
+            }
+            const float2 cin = fma2(f2s(c.chunk_pw[sg]), mul2(tot, inv1m), pre);
+            float2 xv = f2s(0.f);
+#pragma unroll
+            for (int k = LS - 1; k >= 0; --k) {
+                float2 *el = reinterpret_cast<float2 *>(col0 + (size_t)k * NX + xs);
+                const float2 zk = fma2(f2s(c.pw[k + 1]), cin, *el);
+                xv = fma2(rho, xv, zk);
+                *el = xv;
+            }
+            cb[p * NXP + xp] = xv;
+        }
+        if constexpr (G > 1) cg::this_cluster().sync(); else __syncthreads();
+#pragma unroll 1
+        for (int xi = 0; xi < XPT; ++xi) {
+            const int xp = xb + xi * NT;
+            float2 tot = f2s(0.f), pre = f2s(0.f);
+#pragma unroll
+            for (int j = SEG - 1; j >= 0; --j) {
+                const float2 *src = cb + (j % P) * NXP + xp;
+                float2 ev;
+                if constexpr (G > 1) ev = fz_ld_peer2(fz_peer(src, j / P));
+                else ev = *src;
+                if (j == sg) pre = tot;
+                tot = fma2(mls, tot, ev);
+            }
+            dn[p * NXP + xp] = fma2(f2s(c.chunk_pw[SEG - 1 - sg]), mul2(tot, inv1m), pre);
+        }
+        if constexpr (G > 1) cg::this_cluster().sync(); else __syncthreads();
+
+        // epilogue: val into nxt (the next step's input) and, unless the next
+        // step writes the same state, to the job's output; edge rows for PR
+        const bool write = jb.out && (s == S - 1 || cj[s + 1].out != jb.out);
+        const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int j = prow; j < R; j += RPI) {
+            float4 v = fz_col_final<NX, NXP, LS>(nxt + NX, dn, c, j, px, pxs);
+            if (a.neg) v = make_float4(-v.x, -v.y, -v.z, -v.w);
+            const size_t gi = (size_t)(r0 + j) * NX + px;
+            const float4 gg = jb.g ? fz_ld4(jb.g + gi) : z4;
+            const float4 hh = jb.h ? fz_ld4(jb.h + gi) : z4;
+            v = make_float4(v.x + gg.x + hh.x, v.y + gg.y + hh.y, v.z + gg.z + hh.z, v.w + gg.w + hh.w);
+            *reinterpret_cast<float4 *>(nxt + (size_t)(j + 1) * NX + pxs) = v;
+            if (write) *reinterpret_cast<float4 *>(jb.out + gi) = v;
+            if (PR && j == 0) *reinterpret_cast<float4 *>(edge + px) = v;
+            if (PR && j == R - 1) *reinterpret_cast<float4 *>(edge + NX + px) = v;
+        }
+        if (s + 1 < S && PR) {
+            // halo rows of the next step: state rows r0 - 1 and r0 + R from the
+            // neighbouring CTAs' edge rows (own rows when the cluster is one CTA)
+            if constexpr (G > 1) cg::this_cluster().sync(); else __syncthreads();
+            for (int x = threadIdx.x * 4; x < NX; x += NT * 4) {
+                float4 vu, vd;
+                if constexpr (G > 1) {
+                    vu = fz_ld_peer4(fz_peer(edge + NX + x, (rank + G - 1) % G));
+                    vd = fz_ld_peer4(fz_peer(edge + x, (rank + 1) % G));
+                } else {
+                    vu = fz_ld4(edge + NX + x);
+                    vd = fz_ld4(edge + x);
+                }
+                *reinterpret_cast<float4 *>(nxt + fz_swz(x)) = vu;
+                *reinterpret_cast<float4 *>(nxt + (size_t)(R + 1) * NX + fz_swz(x)) = vd;
+            }
+        }
+        // the edges are rewritten only after the next step's cluster barriers;
+        // nxt becomes the input
+        if constexpr (G > 1) { if (s + 1 == S) cg::this_cluster().sync(); }
+        __syncthreads();
+        float *tmp = cur;
+        cur = nxt;
+        nxt = tmp;
+    }
+}
+
+}  // namespace atm

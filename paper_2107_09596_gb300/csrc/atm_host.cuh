@@ -131,6 +131,7 @@ inline SweepFn<T> col_kernel(int CY, int W, bool pr)
 template <typename T>
 struct FusedVariant {
     SweepFn<T> fn = nullptr;
+    void (*cfn)(SweepArgs<T>, int) = nullptr;   // chain kernel (chain shapes only)
     int G = 1, NT = 256, LS = 16;
     size_t smem = 0;
     TriCoef<T> cy{};
@@ -140,13 +141,14 @@ struct FusedVariant {
 // bound by the FP64 pipe, not by the intermediate's traffic).  The first
 // entry is the default; the level-0 autotuner times them all.
 template <typename T>
-inline std::vector<FusedVariant<T>> fused_variants(int nx, int ny, bool pr, bool react, double ay)
+inline std::vector<FusedVariant<T>> fused_variants(int nx, int ny, bool pr, bool react, double ay, bool chains = false)
 {
     std::vector<FusedVariant<T>> v;
     if constexpr (sizeof(T) == 4) {
-        for (const FusedShape &f : fused_shapes(nx, ny, pr, react)) {
+        for (const FusedShape &f : chains ? chain_shapes(nx, ny, pr, react) : fused_shapes(nx, ny, pr, react)) {
             FusedVariant<T> fv;
             fv.fn = f.fn;
+            fv.cfn = f.cfn;
             fv.G = f.G;
             fv.NT = f.NT;
             fv.LS = f.LS;
@@ -172,6 +174,7 @@ struct LevelOp {
     std::vector<double> dir_w;   // 1D: Dirichlet rank-one vector (host copy)
     bool learned = false;        // the level's propagator is the learned Psi_NN
     std::vector<FusedVariant<T>> fused;   // fused whole-propagator launch shapes (may be empty)
+    std::vector<FusedVariant<T>> chains;  // chain-kernel shapes (ATM_SWEEP_CHAIN)
 };
 
 // Build the level-l propagator of (pb, sv): step D = dt * m_0 * .. * m_{l-1};
@@ -251,6 +254,7 @@ inline LevelOp<T> make_level_op(const atm_problem &pb, const atm_solver &sv, int
     const size_t pitch = (size_t)pb.nx + (size_t)(pb.nx * sizeof(T) / 128) * (16 / sizeof(T));
     op.row_smem = pr ? (size_t)(op.rows_per_cta + 2) * pitch * sizeof(T) : 0;
     if (sv.sweep_kernel != ATM_SWEEP_SPLIT) op.fused = fused_variants<T>(pb.nx, pb.ny, pr, react, ay);
+    if (sv.sweep_kernel == ATM_SWEEP_CHAIN) op.chains = fused_variants<T>(pb.nx, pb.ny, pr, react, ay, true);
     return op;
 }
 
@@ -268,7 +272,7 @@ inline TuneCache &tune_cache()
     return c;
 }
 
-enum { L_SWEEP = 0, L_AXPY = 1, L_NORM = 2 };
+enum { L_SWEEP = 0, L_AXPY = 1, L_NORM = 2, L_CHAIN = 3 };
 
 // One kernel launch (a sweep is one launch in 1D, two in 2D) of a phase.
 struct LaunchRec {
@@ -281,6 +285,7 @@ struct LaunchRec {
     int npartials = 0;
     double *norm_out = nullptr;
     int prof_slot = -1;   // >= 0: time this sweep's kernels with event slot prof_slot
+    int steps = 0;        // L_CHAIN: steps per chain (jobs chain-major)
     bool has_pre = false; // learned correction: classical pass over the jobs at pre_index first
     size_t pre_index = 0;
 };
@@ -330,6 +335,8 @@ struct Level {
     LevelOp<T> classical;        // learned level: the split-BE ADI operator used after a fallback
     std::vector<FusedVariant<T>> fused;   // fused launch shapes available on this level
     int fz = -1;                 // selected fused shape (-1: split row/column kernels)
+    std::vector<FusedVariant<T>> chains;  // chain-kernel shapes
+    int chz = -1;                // selected chain shape (-1: F-relaxation step by step)
 };
 
 inline bool pow2_in(int v, int lo, int hi)
@@ -516,9 +523,12 @@ struct Plan : PlanBase {
         Lv.dir_w_host = op.dir_w;
         Lv.learned = op.learned;
         Lv.fused = op.fused;
+        Lv.chains = op.chains;
+        Lv.chz = Lv.chains.empty() ? -1 : 0;
         // fused on coarse levels by default, and on level 0 when asked for
         // (ATM_SWEEP_AUTO lets the autotuner decide level 0 at create time)
-        Lv.fz = (!Lv.fused.empty() && (l > 0 || sv.sweep_kernel == ATM_SWEEP_FUSED)) ? 0 : -1;
+        Lv.fz = (!Lv.fused.empty() && (l > 0 || sv.sweep_kernel == ATM_SWEEP_FUSED || sv.sweep_kernel == ATM_SWEEP_CHAIN))
+                    ? 0 : -1;
     }
 
     // ---------------- phase builders ----------------
@@ -567,6 +577,20 @@ struct Plan : PlanBase {
             r.pre_index = jobs.size();
             jobs.insert(jobs.end(), pre.begin(), pre.end());
         }
+        ph.push_back(r);
+    }
+
+    // nch chains of S steps (jobs chain-major: chain c, step s at c S + s).
+    void add_chain(Phase &ph, int l, std::vector<Job<T>> &&js, int nch, int S)
+    {
+        if (nch == 0) return;
+        LaunchRec r;
+        r.type = L_CHAIN;
+        r.level = l;
+        r.job_index = jobs.size();
+        r.njobs = nch;
+        r.steps = S;
+        jobs.insert(jobs.end(), js.begin(), js.end());
         ph.push_back(r);
     }
 
@@ -636,7 +660,32 @@ struct Plan : PlanBase {
         Level<T> &Lv = lv[l];
         const int N = Lv.N, m = Lv.m, NC = Lv.NC;
         const bool c0 = cpo && l == 0;
-        for (int j = 1; j < m; ++j) {
+        // chain kernel: one launch, each interval's m-1 steps on its state in
+        // shared memory (not with a regenerated base chain, whose states are
+        // not kept per step)
+        const bool chain = Lv.chz >= 0 && m > 1 && !(c0 && bwork);
+        if (chain) {
+            std::vector<Job<T>> cj;
+            int nch = 0;
+            for (int i = 0; i < NC; ++i) {
+                if (i * m + m - 1 > N - 1 || (c0 && !full_interval(i))) continue;
+                for (int j = 1; j < m; ++j) {
+                    const int t = i * m + j;
+                    cj.push_back(job(up(l, t - 1), up(l, t), gl(l, t), nullptr, nullptr, nullptr, bp(l, t - 1)));
+                }
+                ++nch;
+            }
+            add_chain(ph, l, std::move(cj), nch, m - 1);
+            // a ragged last interval (full storage) goes step by step
+            const int it = N - 1 - ((N - 1) / m) * m > 0 && !c0 ? (N - 1) / m : -1;
+            if (it >= 0)
+                for (int j = 1; it * m + j < N; ++j) {
+                    const int t = it * m + j;
+                    add_sweep(ph, l, {job(up(l, t - 1), up(l, t), gl(l, t), nullptr, nullptr, nullptr, bp(l, t - 1))},
+                              0, false);
+                }
+        }
+        for (int j = 1; j < m && !chain; ++j) {
             std::vector<Job<T>> js;
             for (int i = 0; i < NC; ++i) {
                 const int t = i * m + j;
@@ -972,7 +1021,8 @@ struct Plan : PlanBase {
     {
         long long n = 0;
         for (const LaunchRec &r : ph) {
-            if (r.type != L_SWEEP || is1d) n += 1;
+            if (r.type == L_CHAIN) n += (r.njobs + 32767) / 32768;
+            else if (r.type != L_SWEEP || is1d) n += 1;
             else if (lv[r.level].learned || lv[r.level].fz >= 0) {
                 n += sweep_pairs(r.level, r.njobs);
                 if (lv[r.level].learned && hybrid) n += 2 * ((r.njobs + midcap - 1) / midcap);
@@ -1008,6 +1058,39 @@ struct Plan : PlanBase {
             a.jobs = djobs + j0;
             op.row<<<dim3(pb.ny / op.rows_per_cta, nj), 32 * op.rows_per_cta, op.row_smem, st>>>(a);
             op.col<<<dim3(pb.nx / 32, nj), 32 * op.col_warps, 0, st>>>(a);
+        }
+    }
+
+    // nch chains of S propagator applications, one cluster per chain.
+    void launch_chain(int l, const Job<T> *djobs, int nch, int S)
+    {
+        if constexpr (sizeof(T) == 4) {
+            const Level<T> &Lv = lv[l];
+            const FusedVariant<T> &fv = Lv.chains[Lv.chz];
+            SweepArgs<T> a = Lv.args;
+            a.cy = fv.cy;
+            a.neg = 0;
+            a.mid = nullptr;
+            a.partials = nullptr;
+            for (int c0 = 0; c0 < nch; c0 += 32768) {
+                const int nc = nch - c0 < 32768 ? nch - c0 : 32768;
+                a.jobs = djobs + (size_t)c0 * S;
+                cudaLaunchConfig_t cfg = {};
+                cfg.gridDim = dim3(fv.G, nc);
+                cfg.blockDim = dim3(fv.NT);
+                cfg.dynamicSmemBytes = fv.smem;
+                cfg.stream = st;
+                cudaLaunchAttribute at[1];
+                at[0].id = cudaLaunchAttributeClusterDimension;
+                at[0].val.clusterDim.x = fv.G;
+                at[0].val.clusterDim.y = 1;
+                at[0].val.clusterDim.z = 1;
+                cfg.attrs = at;
+                cfg.numAttrs = 1;
+                if (cudaLaunchKernelEx(&cfg, fv.cfn, a, S) != cudaSuccess) launch_failed = true;
+            }
+        } else {
+            launch_failed = true;   // no chain kernels in FP64
         }
     }
 
@@ -1243,17 +1326,67 @@ struct Plan : PlanBase {
         return ATM_OK;
     }
 
+    // Chain-shape choice: for each level with chain records in `ph`, time them
+    // with every chain shape (warm-up, then two repetitions) and keep the fastest.
+    atm_status autotune_chains(const Phase &ph)
+    {
+        cudaEvent_t e0, e1;
+        ATM_CK(cudaEventCreate(&e0));
+        ATM_CK(cudaEventCreate(&e1));
+        for (int l = 0; l < L; ++l) {
+            if (lv[l].chains.size() < 2) continue;
+            std::vector<const LaunchRec *> recs;
+            for (const LaunchRec &r : ph)
+                if (r.type == L_CHAIN && r.level == l) recs.push_back(&r);
+            if (recs.empty()) continue;
+            float best = 1e30f;
+            int bk = lv[l].chz;
+            for (int k = 0; k < (int)lv[l].chains.size(); ++k) {
+                lv[l].chz = k;
+                launch_failed = false;
+                for (const LaunchRec *r : recs) launch_chain(l, d_jobs + r->job_index, r->njobs, r->steps);
+                cudaEventRecord(e0, st);
+                for (int rep = 0; rep < 2; ++rep)
+                    for (const LaunchRec *r : recs) launch_chain(l, d_jobs + r->job_index, r->njobs, r->steps);
+                cudaEventRecord(e1, st);
+                cudaEventSynchronize(e1);
+                float ms = 0;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (launch_failed) {
+                    launch_failed = false;
+                    cudaGetLastError();
+                    continue;
+                }
+                if (ms < best) { best = ms; bk = k; }
+            }
+            lv[l].chz = bk;
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        ATM_CK(cudaGetLastError());
+        return ATM_OK;
+    }
+
     // Shared-memory and cluster-size attributes of the fused kernels; shapes
     // that cannot be resident on this device are dropped.
     atm_status prepare_fused(int l)
     {
         Level<T> &Lv = lv[l];
+        ATM_TRY(prepare_shapes(Lv.chains, true));
+        Lv.chz = Lv.chains.empty() ? -1 : (Lv.chz >= 0 ? 0 : -1);
+        return prepare_shapes(Lv.fused, false, &Lv.fz);
+    }
+
+    // Attributes of each shape's kernel; drop shapes that cannot be resident.
+    atm_status prepare_shapes(std::vector<FusedVariant<T>> &shapes, bool chain, int *fz = nullptr)
+    {
         std::vector<FusedVariant<T>> keep;
-        for (const FusedVariant<T> &fv : Lv.fused) {
-            ATM_CK(cudaFuncSetAttribute((const void *)fv.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fv.smem));
+        for (const FusedVariant<T> &fv : shapes) {
+            const void *fn = chain ? (const void *)fv.cfn : (const void *)fv.fn;
+            ATM_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fv.smem));
             // the whole unified L1/shared array as shared memory: room for 3 CTAs of ~70 KB
-            ATM_CK(cudaFuncSetAttribute((const void *)fv.fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
-            if (fv.G > 8) ATM_CK(cudaFuncSetAttribute((const void *)fv.fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+            ATM_CK(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+            if (fv.G > 8) ATM_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
             cudaLaunchConfig_t cfg = {};
             cfg.gridDim = dim3(fv.G, 1);
             cfg.blockDim = dim3(fv.NT);
@@ -1266,15 +1399,14 @@ struct Plan : PlanBase {
             cfg.attrs = at;
             cfg.numAttrs = 1;
             int nclusters = 0;
-            if (cudaOccupancyMaxActiveClusters(&nclusters, (const void *)fv.fn, &cfg) != cudaSuccess) {
+            if (cudaOccupancyMaxActiveClusters(&nclusters, fn, &cfg) != cudaSuccess) {
                 cudaGetLastError();
                 nclusters = 0;
             }
             if (nclusters > 0) keep.push_back(fv);
         }
-        const bool was = Lv.fz >= 0;
-        Lv.fused = keep;
-        Lv.fz = (was && !keep.empty()) ? 0 : -1;
+        shapes = keep;
+        if (fz) *fz = (*fz >= 0 && !keep.empty()) ? 0 : -1;
         return ATM_OK;
     }
 
@@ -1291,6 +1423,8 @@ struct Plan : PlanBase {
             if (r.type == L_SWEEP)
                 launch_sweep(r.level, d_jobs + r.job_index, r.njobs, r.neg, r.partials, r.prof_slot,
                              r.has_pre ? d_jobs + r.pre_index : nullptr);
+            else if (r.type == L_CHAIN)
+                launch_chain(r.level, d_jobs + r.job_index, r.njobs, r.steps);
             else if (r.type == L_AXPY)
                 launch_axpy(d_ajobs + r.job_index, r.njobs);
             else
@@ -1367,9 +1501,10 @@ struct Plan : PlanBase {
         {
             std::lock_guard<std::mutex> lk(tune_cache().mu);
             auto it = tune_cache().choice.find(tkey);
-            if (it != tune_cache().choice.end() && (int)it->second.size() == L + 1) {
+            if (it != tune_cache().choice.end() && (int)it->second.size() == 2 * L + 1) {
                 chunk = it->second[0];
                 for (int l = 0; l < L; ++l) lv[l].fz = it->second[1 + l];
+                for (int l = 0; l < L; ++l) lv[l].chz = it->second[1 + L + l];
                 cached = true;
             }
         }
@@ -1385,8 +1520,13 @@ struct Plan : PlanBase {
                 }
                 ATM_TRY(autotune_coarse(role == ROLE_INNER ? inner_cycle : rest));
             }
+            if (sv.sweep_kernel == ATM_SWEEP_CHAIN && role != ROLE_OUTER) {
+                ATM_TRY(autotune_chains(role == ROLE_INNER ? inner_cycle : passA));
+                if (L > 1 && role == ROLE_NORMAL) ATM_TRY(autotune_chains(rest));
+            }
             std::vector<int> ch(1, chunk);
             for (int l = 0; l < L; ++l) ch.push_back(lv[l].fz);
+            for (int l = 0; l < L; ++l) ch.push_back(lv[l].chz);
             std::lock_guard<std::mutex> lk(tune_cache().mu);
             tune_cache().choice[tkey] = ch;
         }
@@ -1840,6 +1980,9 @@ struct Plan : PlanBase {
             cfg[0] = 3; cfg[1] = 1; cfg[2] = 32;
         } else if (Lv.learned) {
             cfg[0] = 2;
+        } else if (Lv.chz >= 0) {
+            const FusedVariant<T> &f = Lv.chains[Lv.chz];
+            cfg[0] = 4; cfg[1] = f.G; cfg[2] = f.NT; cfg[3] = f.LS;
         } else if (Lv.fz >= 0) {
             const FusedVariant<T> &f = Lv.fused[Lv.fz];
             cfg[0] = 1; cfg[1] = f.G; cfg[2] = f.NT; cfg[3] = f.LS;

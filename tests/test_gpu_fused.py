@@ -145,3 +145,47 @@ def test_refined_with_several_inner_cycles(torch, inner):
     seq = oracle.sequential(oc, u0)
     assert rel_l2(res[inner][1], seq) <= 1e-7
     assert res[inner][0]["iterations"] < res[1][0]["iterations"], (res[1][0], res[inner][0])
+
+
+CHAIN_CASES = {
+    "ac64_ragged_full": dict(kind="ac", nx=64, ny=64, dt=1e-4, nt=300, m=(4, 4), k=3, nu=1),
+    "ac128_cpoint": dict(kind="ac", nx=128, ny=128, dt=1e-4, nt=257, m=(8, 4), k=4, nu=1, cpoint_only=True),
+    "heat256_f": dict(kind="heat2d", nx=256, ny=256, dt=2e-4, nt=257, m=(16,), k=4, nu=0),
+    "ac256_3lvl": dict(kind="ac", nx=256, ny=256, dt=1e-4, nt=513, m=(16, 4), k=4, nu=1),
+}
+
+
+@pytest.mark.parametrize("case", sorted(CHAIN_CASES))
+def test_chain_kernel_solves_like_the_fused_kernel(torch, case):
+    """F-relaxations as chains (one launch; each interval's steps on its state
+    in shared memory) reach the same FP32 fixed point as step-by-step fused
+    launches and the FP64 sequential solution within the FP32 bar."""
+    kw = dict(CHAIN_CASES[case], precision=atm.FP32, tol=0.0, max_iter=6)
+    n = kw["nx"]
+    u0 = I.uniform_field((n, n), 31)
+    sols = {}
+    for sk in (atm.SWEEP_CHAIN, atm.SWEEP_FUSED):
+        oc, gp, gs = pair(sweep_kernel=sk, **kw)
+        s = atm.Solver(gp, gs)
+        s.set_initial_condition(dev(torch, u0))
+        s.solve()
+        sols[sk] = (s.solution().cpu().numpy(), s.residual_history())
+    assert rel_l2(sols[atm.SWEEP_CHAIN][0], sols[atm.SWEEP_FUSED][0]) <= 1e-5
+    np.testing.assert_allclose(sols[atm.SWEEP_CHAIN][1], sols[atm.SWEEP_FUSED][1], rtol=1e-3)
+    # after 6 cycles both sit at the same iterate; the FP64 oracle after 6 cycles agrees to FP32
+    want = np.zeros_like(sols[atm.SWEEP_CHAIN][0])
+    want[0] = u0
+    oracle.solve(oc, want, 6, 0.0)
+    assert rel_l2(sols[atm.SWEEP_CHAIN][0], want) <= 1e-4
+
+
+def test_chain_kernel_in_the_refined_inner_cycles(torch):
+    kw = dict(kind="ac", nx=128, ny=128, dt=1e-4, nt=257, m=(4, 4), k=4, nu=1, tol=1e-9, max_iter=40,
+              precision=atm.FP32_REFINED, sweep_kernel=atm.SWEEP_CHAIN, cpoint_only=True)
+    oc, gp, gs = pair(**kw)
+    s = atm.Solver(gp, gs)
+    u0 = I.uniform_field((128, 128), 32)
+    s.set_initial_condition(dev(torch, u0))
+    r = s.solve()
+    assert r["converged"], r
+    assert rel_l2(s.solution().cpu().numpy(), oracle.sequential(oc, u0)) <= 1e-7
