@@ -81,6 +81,8 @@ def lib():
         L.or_solve.restype = ctypes.c_int
         L.or_cpoint_residual_norm.argtypes = [P, dp, dp]
         L.or_cpoint_residual_norm.restype = ctypes.c_double
+        L.or_nested_guess.argtypes = [P, dp]
+        L.or_nested_guess.restype = None
         L.or_full_residual_norm.argtypes = [P, dp, dp]
         L.or_full_residual_norm.restype = ctypes.c_double
         L.or_frelax_level.argtypes = [P, ctypes.c_int, dp, dp]
@@ -164,6 +166,14 @@ def solve(c: OrCfg, u: np.ndarray, max_iter: int, tol: float = 0.0,
     if it < 0:
         raise ValueError("invalid oracle configuration")
     return it, hist[: it + 1].copy()
+
+
+def nested_guess(c: OrCfg, u: np.ndarray) -> None:
+    """Nested iteration: overwrite the level-0 C-points i >= 1 of ``u`` with the
+    coarse hierarchy's values (coarsest level stepped sequentially, injection
+    and F-relaxation on each finer coarse level)."""
+    assert u.dtype == np.float64 and u.flags["C_CONTIGUOUS"]
+    lib().or_nested_guess(ctypes.byref(c), _ptr(u))
 
 
 def cpoint_residual_norm(c: OrCfg, u: np.ndarray, g=None) -> float:

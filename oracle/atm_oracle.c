@@ -533,6 +533,41 @@ int or_solve(const or_cfg *c, double *g, double *u, int max_iter, double tol, do
     return it;
 }
 
+/* Nested iteration: the initial iterate of a multilevel solve built from its
+ * coarse hierarchy.  Every coarse level l carries the rediscretised problem
+ * w_0 = u0, w_i = Phi_l(w_{i-1}); the coarsest level is stepped sequentially;
+ * each finer level l >= 1 takes the coarser values at its C-points
+ * (w^l_{i m_l} = w^{l+1}_i) and F-relaxes; level 0 receives its C-points
+ * i >= 1.  u[0] (the initial condition) and the level-0 F-points are left as
+ * they are.  u: nt states. */
+void or_nested_guess(const or_cfg *c, double *u)
+{
+    const int n = nspace(c), L = c->levels;
+    if (L < 2 || L > OR_MAXLEV) return;
+    double *ws = (double *)malloc(sizeof(double) * or_prop_workspace(c));
+    double *w[OR_MAXLEV];
+    int N[OR_MAXLEV];
+    for (int l = 1; l < L; ++l) {
+        N[l] = or_level_points(c, l);
+        w[l] = (double *)malloc(sizeof(double) * (size_t)N[l] * n);
+    }
+    memcpy(w[L - 1], u, sizeof(double) * n);
+    for (int j = 1; j < N[L - 1]; ++j)
+        or_apply_prop_ws(c, L - 1, w[L - 1] + (size_t)(j - 1) * n, w[L - 1] + (size_t)j * n, ws);
+    for (int l = L - 2; l >= 1; --l) {
+        const int m = c->m[l];
+        for (int i = 0; i < N[l + 1]; ++i)
+            memcpy(w[l] + (size_t)i * m * n, w[l + 1] + (size_t)i * n, sizeof(double) * n);
+        for (int i = 0; i < N[l + 1]; ++i)
+            for (int t = i * m + 1; t <= i * m + m - 1 && t < N[l]; ++t)
+                or_apply_prop_ws(c, l, w[l] + (size_t)(t - 1) * n, w[l] + (size_t)t * n, ws);
+    }
+    for (int i = 1; i < N[1]; ++i)
+        memcpy(u + (size_t)i * c->m[0] * n, w[1] + (size_t)i * n, sizeof(double) * n);
+    for (int l = 1; l < L; ++l) free(w[l]);
+    free(ws);
+}
+
 /* C-point residual norm of a level-0 iterate (F-points taken as stored). */
 double or_cpoint_residual_norm(const or_cfg *c, double *g, double *u)
 {
