@@ -134,6 +134,11 @@ typedef struct {
                                          passes for FP32 cycles while the inner iteration still
                                          contracts (256^2 Allen-Cahn to 1e-8: 14 FP64 passes with
                                          one inner cycle, 6 with three, 4 with five) */
+    int nested_iteration;             /* 1: nested iteration -- every solve starts from the coarsest
+                                         level's sequential solution (u_0 = the initial condition),
+                                         interpolated down the hierarchy by injection and
+                                         F-relaxation on each level; it replaces the initial guess
+                                         (MGRIT / AT-MGRIT with levels >= 2) */
     int cpoint_storage_only;          /* 1: level 0 keeps only its C-points (t = i m_0) and one
                                          working state per C-interval, about 3 N_t / m_0 states
                                          instead of N_t + N_t / m_0 (Sec. 2.1: the F-points of an

@@ -399,6 +399,8 @@ struct Plan : PlanBase {
     cudaGraphExec_t gA_nn = nullptr, gIter_nn = nullptr, gA_cl = nullptr, gIter_cl = nullptr;
     nn::Net net;
     Phase passA, rest, seq;
+    Phase nested;          // nested iteration: the initial iterate from the coarse hierarchy
+    Phase passA0;          // first pass of a solve: nested (if on) + passA
     T *r_full = nullptr;   // ROLE_OUTER: residual of every point
     T *ubase = nullptr;    // ROLE_INNER: FP32 copy of the outer iterate (base of the increments)
     Phase resid_full;      // ROLE_OUTER: residual of every point + norm
@@ -798,6 +800,33 @@ struct Plan : PlanBase {
         }
     }
 
+    // Nested iteration down to level `lowest`: each level l >= 1 holds the
+    // rediscretised problem u_0 = u0, u_i = Psi_l(u_{i-1}) (g = u0 at 0, zero
+    // elsewhere; the caller provides g^1_0 when lowest >= 1); the coarsest is
+    // solved sequentially, and each finer level takes the coarser values at its
+    // C-points (injection) and F-relaxes.  Level 0 gets its C-points i >= 1.
+    void add_nested(Phase &ph, int lowest)
+    {
+        for (int l = 1; l < L; ++l) {
+            std::vector<AxpyJob<T>> z;
+            for (int i = 1; i < lv[l].N; ++i) z.push_back(ajob(st_ptr(lv[l].g, i), nullptr));
+            if (lowest == 0) z.push_back(ajob(lv[l].g, up(0, 0)));
+            else if (l >= 2) z.push_back(ajob(lv[l].g, lv[1].g));
+            add_axpy(ph, std::move(z));
+        }
+        Level<T> &C = lv[L - 1];
+        add_axpy(ph, {ajob(C.u, C.g)});
+        for (int j = 1; j < C.N; ++j)
+            add_sweep(ph, L - 1, {job(st_ptr(C.u, j - 1), st_ptr(C.u, j), st_ptr(C.g, j))}, 0, false);
+        for (int l = L - 2; l >= lowest; --l) {
+            std::vector<AxpyJob<T>> cp;
+            for (int i = (l == 0 ? 1 : 0); i < lv[l + 1].N; ++i)
+                cp.push_back(ajob(up(l, i * lv[l].m), st_ptr(lv[l + 1].u, i)));
+            add_axpy(ph, std::move(cp));
+            if (l >= 1) add_frelax(ph, l, 0, false);
+        }
+    }
+
     // u^l_C += u^{l+1} - v^{l+1}
     void add_correct(Phase &ph, int l)
     {
@@ -834,7 +863,7 @@ struct Plan : PlanBase {
         ajobs.clear();
         passA.clear(); rest.clear(); seq.clear(); st_coarse.clear();
         st_f.assign(L, Phase()); st_c.assign(L, Phase()); st_r.assign(L, Phase()); st_corr.assign(L, Phase());
-        resid_full.clear(); inner_cycle.clear();
+        resid_full.clear(); inner_cycle.clear(); nested.clear(); passA0.clear();
         if (role == ROLE_OUTER && cpo) {
             // C-point storage: the F-points are the F-chains of the C-points, so the
             // residual is zero there; r_i = Phi(u_{im-1}) - u_im at the C-points i >= 1
@@ -865,6 +894,9 @@ struct Plan : PlanBase {
             // e_0 = r_0 = 0: its right-hand side is r itself (staged in g by the
             // caller), its iterate starts at zero
             add_level_cycle(inner_cycle, 0);
+            // nested iteration of the refined mode: the coarse hierarchy of the
+            // original problem in FP32, down to level 1 (the caller stages u0)
+            if (sv.nested_iteration && L > 1) add_nested(nested, 1);
             return;
         }
         if (sv.algorithm == ATM_SEQUENTIAL) {
@@ -884,6 +916,9 @@ struct Plan : PlanBase {
         add_restrict(rest, 0);
         add_level_cycle(rest, 1);
         add_correct(rest, 0);
+        if (sv.nested_iteration) add_nested(nested, 0);
+        passA0 = nested;
+        passA0.insert(passA0.end(), passA.begin(), passA.end());
         // building blocks for atm_run_stage
         for (int l = 0; l < L; ++l) {
             if (l + 1 < L) {
@@ -1536,7 +1571,7 @@ struct Plan : PlanBase {
             if (sv.algorithm == ATM_SEQUENTIAL) {
                 ATM_TRY(capture({&seq}, &gSeq));
             } else {
-                ATM_TRY(capture({&passA}, &gA));
+                ATM_TRY(capture({&passA0}, &gA));
                 ATM_TRY(capture({&rest, &passA}, &gIter));
             }
         }
@@ -1574,7 +1609,7 @@ struct Plan : PlanBase {
         any_learned = on;
         if (sv.use_graph && st != nullptr) {
             if (!on && !gA_cl) {
-                ATM_TRY(capture({&passA}, &gA_cl));
+                ATM_TRY(capture({&passA0}, &gA_cl));
                 ATM_TRY(capture({&rest, &passA}, &gIter_cl));
             }
             gA = on ? gA_nn : gA_cl;
@@ -1596,7 +1631,7 @@ struct Plan : PlanBase {
         no_events = true;
         cudaError_t e = cudaStreamBeginCaptureToGraph(st, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) { no_events = false; return fail(ATM_ERR_CUDA, "capture failed: %s", cudaGetErrorString(e)); }
-        enqueue(passA);
+        enqueue(passA0);
         loop_decide_kernel<<<1, 1, 0, st>>>(norm_cur, loop_hist, loop_state, sv.max_iter, sv.tol, h, 1);
         cudaStreamCaptureStatus cs;
         const cudaGraphNode_t *deps = nullptr;
@@ -1636,7 +1671,7 @@ struct Plan : PlanBase {
         const int it = (int)stv[0];
         hist.assign((size_t)it + 1, 0.0);
         ATM_CK(cudaMemcpy(hist.data(), loop_hist, sizeof(double) * (it + 1), cudaMemcpyDeviceToHost));
-        launches = (long long)kernels_in(passA) + 1 + (long long)it * (kernels_in(rest) + kernels_in(passA) + 1);
+        launches = (long long)kernels_in(passA0) + 1 + (long long)it * (kernels_in(rest) + kernels_in(passA) + 1);
         atm_result R;
         std::memset(&R, 0, sizeof(R));
         R.iterations = it;
@@ -1729,8 +1764,8 @@ struct Plan : PlanBase {
             }
             R.converged = 1;
         } else {
-            if (gA) { ATM_CK(cudaGraphLaunch(gA, st)); launches += kernels_in(passA); }
-            else ATM_TRY(run(passA));
+            if (gA) { ATM_CK(cudaGraphLaunch(gA, st)); launches += kernels_in(passA0); }
+            else ATM_TRY(run(passA0));
             double r0 = 0;
             ATM_TRY(read_norm(&r0));
             if (nprof) collect_profile();
@@ -2121,11 +2156,38 @@ struct RefinedPlan : PlanBase {
         launches += 3;
     }
 
+    // Nested iteration (refined mode): the coarse hierarchy solved in FP32 by
+    // the inner plan (u0 staged into g^1_0), its level-1 values become the
+    // outer iterate's C-points (FP64).
+    void enqueue_nested()
+    {
+        if (inner.nested.empty()) return;
+        const size_t nsp = (size_t)outer.nsp;
+        outer.convert_to_T_other(outer.lv[0].u, inner.lv[1].g, nsp);
+        inner.enqueue(inner.nested);
+        const int N1 = inner.lv[1].N;
+        if (outer.cpo) {
+            inner.convert_from_T(inner.lv[1].u + nsp, outer.lv[0].u + nsp, (size_t)(N1 - 1) * nsp);
+        } else {
+            const size_t m0 = (size_t)sv.m[0];
+            for (int i = 1; i < N1; ++i)
+                inner.convert_from_T(inner.lv[1].u + (size_t)i * nsp, outer.lv[0].u + (size_t)i * m0 * nsp, nsp);
+        }
+        launches += 1 + inner.kernels_in(inner.nested) + (outer.cpo ? 1 : N1 - 1);
+    }
+
+    long long kernels_nested() const
+    {
+        if (inner.nested.empty()) return 0;
+        return 1 + inner.kernels_in(inner.nested) + (outer.cpo ? 1 : inner.lv[1].N - 1);
+    }
+
     atm_status capture(bool with_inner, cudaGraphExec_t *out)
     {
         cudaGraph_t g = nullptr;
         ATM_CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
         if (with_inner) enqueue_inner();
+        else enqueue_nested();
         outer.run(outer.resid_full);
         cudaError_t e = cudaStreamEndCapture(st, &g);
         if (e != cudaSuccess) return fail(ATM_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
@@ -2186,8 +2248,11 @@ struct RefinedPlan : PlanBase {
             return s;
         }
         ATM_CK(cudaEventRecord(ev0, st));
-        if (gA) { ATM_CK(cudaGraphLaunch(gA, st)); counted += kernels_outer(); }
-        else ATM_TRY(outer.run(outer.resid_full));
+        if (gA) { ATM_CK(cudaGraphLaunch(gA, st)); counted += kernels_nested() + kernels_outer(); }
+        else {
+            enqueue_nested();
+            ATM_TRY(outer.run(outer.resid_full));
+        }
         double r0 = 0;
         ATM_TRY(outer.read_norm(&r0));
         if (outer.nprof) outer.collect_profile();
@@ -2257,6 +2322,7 @@ struct RefinedPlan : PlanBase {
             outer.no_events = inner.no_events = false;
             return fail(ATM_ERR_CUDA, "capture failed: %s", cudaGetErrorString(e));
         }
+        enqueue_nested();
         outer.enqueue(outer.resid_full);
         loop_decide_kernel<<<1, 1, 0, st>>>(outer.norm_cur, outer.loop_hist, outer.loop_state, sv.max_iter, sv.tol, h, 1);
         cudaStreamCaptureStatus cs;
@@ -2298,7 +2364,7 @@ struct RefinedPlan : PlanBase {
         const int it = (int)stv[0];
         hist.assign((size_t)it + 1, 0.0);
         ATM_CK(cudaMemcpy(hist.data(), outer.loop_hist, sizeof(double) * (it + 1), cudaMemcpyDeviceToHost));
-        launches = kernels_outer() + 1 + (long long)it * (kernels_inner() + kernels_outer() + 1);
+        launches = kernels_nested() + kernels_outer() + 1 + (long long)it * (kernels_inner() + kernels_outer() + 1);
         atm_result R;
         std::memset(&R, 0, sizeof(R));
         R.iterations = it;
