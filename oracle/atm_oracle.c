@@ -533,39 +533,45 @@ int or_solve(const or_cfg *c, double *g, double *u, int max_iter, double tol, do
     return it;
 }
 
-/* Nested iteration: the initial iterate of a multilevel solve built from its
- * coarse hierarchy.  Every coarse level l carries the rediscretised problem
- * w_0 = u0, w_i = Phi_l(w_{i-1}); the coarsest level is stepped sequentially;
- * each finer level l >= 1 takes the coarser values at its C-points
- * (w^l_{i m_l} = w^{l+1}_i) and F-relaxes; level 0 receives its C-points
- * i >= 1.  u[0] (the initial condition) and the level-0 F-points are left as
- * they are.  u: nt states. */
+/* Nested iteration (Sec. 2.2): an improved initial iterate from the coarse
+ * hierarchy.  Every coarse level l carries the rediscretised problem
+ * w_0 = u0, w_i = Phi_l(w_{i-1}).  The coarsest level is solved as in a cycle
+ * -- sequentially for MGRIT, by its local coarse grids for AT-MGRIT (from the
+ * guess v = (u0, 0, ..., 0) with r = g - A(v), Sec. 5.1) -- and each finer
+ * coarse level takes the coarser values at its C-points and runs one V-cycle
+ * of its own problem; level 0 receives its C-points i >= 1.  u[0] (the initial
+ * condition) and the level-0 F-points are left as they are.  u: nt states. */
 void or_nested_guess(const or_cfg *c, double *u)
 {
-    const int n = nspace(c), L = c->levels;
-    if (L < 2 || L > OR_MAXLEV) return;
-    double *ws = (double *)malloc(sizeof(double) * or_prop_workspace(c));
-    double *w[OR_MAXLEV];
-    int N[OR_MAXLEV];
+    or_ctx x;
+    if (ctx_init(&x, c, u, NULL) != 0) return;
+    const int n = x.n, L = x.L;
     for (int l = 1; l < L; ++l) {
-        N[l] = or_level_points(c, l);
-        w[l] = (double *)malloc(sizeof(double) * (size_t)N[l] * n);
+        memset(x.lv[l].g, 0, sizeof(double) * (size_t)x.lv[l].N * n);
+        memcpy(x.lv[l].g, u, sizeof(double) * n);
     }
-    memcpy(w[L - 1], u, sizeof(double) * n);
-    for (int j = 1; j < N[L - 1]; ++j)
-        or_apply_prop_ws(c, L - 1, w[L - 1] + (size_t)(j - 1) * n, w[L - 1] + (size_t)j * n, ws);
+    or_level *C = &x.lv[L - 1];
+    memset(C->v, 0, sizeof(double) * (size_t)C->N * n);
+    memcpy(C->v, u, sizeof(double) * n);
+    memset(C->r, 0, sizeof(double) * (size_t)C->N * n);
+    double *ws = (double *)malloc(sizeof(double) * or_prop_workspace(c));
+    for (int j = 1; j < C->N; ++j) {
+        double *r = st(&x, C->r, j);
+        const double *v = st(&x, C->v, j);
+        step(&x, L - 1, j, st(&x, C->v, j - 1), r, ws);
+        for (int q = 0; q < n; ++q) r[q] = r[q] - v[q];
+    }
+    free(ws);
+    coarsest(&x, L - 1);
     for (int l = L - 2; l >= 1; --l) {
         const int m = c->m[l];
-        for (int i = 0; i < N[l + 1]; ++i)
-            memcpy(w[l] + (size_t)i * m * n, w[l + 1] + (size_t)i * n, sizeof(double) * n);
-        for (int i = 0; i < N[l + 1]; ++i)
-            for (int t = i * m + 1; t <= i * m + m - 1 && t < N[l]; ++t)
-                or_apply_prop_ws(c, l, w[l] + (size_t)(t - 1) * n, w[l] + (size_t)t * n, ws);
+        for (int i = 0; i < x.lv[l + 1].N; ++i)
+            memcpy(st(&x, x.lv[l].u, i * m), st(&x, x.lv[l + 1].u, i), sizeof(double) * n);
+        cycle(&x, l);
     }
-    for (int i = 1; i < N[1]; ++i)
-        memcpy(u + (size_t)i * c->m[0] * n, w[1] + (size_t)i * n, sizeof(double) * n);
-    for (int l = 1; l < L; ++l) free(w[l]);
-    free(ws);
+    for (int i = 1; i < x.lv[1].N; ++i)
+        memcpy(u + (size_t)i * c->m[0] * n, st(&x, x.lv[1].u, i), sizeof(double) * n);
+    ctx_free(&x);
 }
 
 /* C-point residual norm of a level-0 iterate (F-points taken as stored). */

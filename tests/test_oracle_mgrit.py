@@ -238,36 +238,38 @@ def test_heat_k_study_k12_matches_parareal(orc):
 
 
 def test_nested_guess_closed_form(orc):
-    """Nested iteration on the 1D heat problem (three levels, backward Euler on
-    every level): per sine mode j the coarsest level steps by its symbol
-    mu_2(j) = 1 / (1 + D_2 (4/dx^2) sin^2(j pi dx / 2)), level 1 takes those
-    values at its C-points and F-relaxes with mu_1(j), so level-0 C-point
-    p = i m_1 + r carries mu_1^r mu_2^i times the initial coefficients; the
-    initial condition and the level-0 F-points are left untouched."""
+    """Nested iteration (Sec. 2.2) on the 1D heat problem, three levels, MGRIT,
+    with the exact coarse operator on level 2 (Psi_2 = Psi_1^{m_1}, Sec.
+    3.1.1): the coarsest level is solved sequentially and one V-cycle on level
+    1 is then a direct solve, so the level-0 C-point p carries mu_1(j)^p times
+    the initial sine coefficients (mu_1 the backward-Euler symbol at step
+    dt m_0); the initial condition and the level-0 F-points are left untouched."""
     nx, nt, m0, m1, dt = 15, 65, 4, 2, 1.0 / 64
-    c = orc.make_cfg(orc.HEAT1D, nx, dt=dt, nt=nt, m=(m0, m1), k=3, nu=1)
+    c = orc.make_cfg(orc.HEAT1D, nx, dt=dt, nt=nt, m=(m0, m1), k=0, nu=1,
+                     prop=[orc.PROP_SPLIT, orc.PROP_SPLIT, orc.PROP_FINEPOW])
     u0 = I.heat1d_initial_condition(nx, 5)
     u = guess(c, u0, 6)
     before = u.copy()
     orc.nested_guess(c, u)
     S = T.dst_modes(nx)
-    dx = 1.0 / (nx + 1)
-    j = np.arange(1, nx + 1)
-    mu1 = T.be_symbol_1d(j, dt * m0, dx)
-    mu2 = T.be_symbol_1d(j, dt * m0 * m1, dx)
+    mu1 = T.be_symbol_1d(np.arange(1, nx + 1), dt * m0, 1.0 / (nx + 1))
     c0 = S @ u0
     for p in range(1, (nt - 1) // m0 + 1):
-        want = S.T @ (mu1 ** (p % m1) * mu2 ** (p // m1) * c0)
-        np.testing.assert_allclose(u[p * m0], want, rtol=0, atol=1e-13)
+        np.testing.assert_allclose(u[p * m0], S.T @ (mu1 ** p * c0), rtol=0, atol=1e-13)
     fpts = [t for t in range(nt) if t % m0 != 0]
     np.testing.assert_array_equal(u[fpts], before[fpts])
     np.testing.assert_array_equal(u[0], before[0])
 
 
-def test_nested_guess_two_levels_is_the_coarse_sequential_solve(orc):
-    """With two levels the nested C-points are the coarse propagator's
-    sequential solution (Allen-Cahn, split-BE ADI after the exact reaction flow)."""
-    c = orc.make_cfg(orc.ALLEN_CAHN, 32, 32, dt=1e-4, nt=65, eps=0.02, m=(8,), k=3, nu=1,
+@pytest.mark.parametrize("k", [0, 3])
+def test_nested_guess_two_levels(orc, k):
+    """With two levels nested iteration is the coarsest solve alone: MGRIT's
+    global coarse grid gives the coarse propagator's sequential solution;
+    AT-MGRIT's local grids, started from the guess (u0, 0, ..., 0), reproduce
+    it at the first k coarse points and leave zeros beyond (each later local
+    grid starts from a zero state with a zero residual, and the propagator maps
+    0 to 0).  Allen-Cahn, split-BE ADI after the exact reaction flow."""
+    c = orc.make_cfg(orc.ALLEN_CAHN, 32, 32, dt=1e-4, nt=65, eps=0.02, m=(8,), k=k, nu=1,
                      react_exact=[False, True])
     u0 = I.uniform_field((32, 32), 3)
     u = np.zeros((65, 32, 32))
@@ -276,4 +278,7 @@ def test_nested_guess_two_levels_is_the_coarse_sequential_solve(orc):
     w = u0.copy()
     for p in range(1, 9):
         w = orc.apply_prop(c, 1, w[None])[0]
-        np.testing.assert_array_equal(u[8 * p], w)
+        if k == 0 or p <= k:
+            np.testing.assert_array_equal(u[8 * p], w)
+        else:
+            np.testing.assert_array_equal(u[8 * p], 0.0 * w)
