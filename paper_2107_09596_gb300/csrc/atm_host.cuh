@@ -800,13 +800,18 @@ struct Plan : PlanBase {
         }
     }
 
-    // Nested iteration down to level `lowest`: each level l >= 1 holds the
-    // rediscretised problem u_0 = u0, u_i = Psi_l(u_{i-1}) (g = u0 at 0, zero
-    // elsewhere; the caller provides g^1_0 when lowest >= 1); the coarsest is
-    // solved sequentially, and each finer level takes the coarser values at its
-    // C-points (injection) and F-relaxes.  Level 0 gets its C-points i >= 1.
+    // Nested iteration down to level `lowest` (Sec. 2.2): each level l >= 1
+    // carries the rediscretised problem u_0 = u0, u_i = Psi_l(u_{i-1}) (g = u0
+    // at 0, zero elsewhere; the caller provides g^1_0 when lowest >= 1).  The
+    // coarsest level is solved as in a cycle: sequentially (MGRIT) or by the
+    // local coarse grids from the guess v = (u0, 0, ..., 0), r = g - A(v)
+    // (AT-MGRIT); each finer coarse level takes the coarser values at its
+    // C-points and runs one V-cycle of its own problem; level 0 receives its
+    // C-points i >= 1.  Jobs never carry a base (no increment form).
     void add_nested(Phase &ph, int lowest)
     {
+        T *saved_base = ubase;
+        ubase = nullptr;
         for (int l = 1; l < L; ++l) {
             std::vector<AxpyJob<T>> z;
             for (int i = 1; i < lv[l].N; ++i) z.push_back(ajob(st_ptr(lv[l].g, i), nullptr));
@@ -815,16 +820,30 @@ struct Plan : PlanBase {
             add_axpy(ph, std::move(z));
         }
         Level<T> &C = lv[L - 1];
-        add_axpy(ph, {ajob(C.u, C.g)});
-        for (int j = 1; j < C.N; ++j)
-            add_sweep(ph, L - 1, {job(st_ptr(C.u, j - 1), st_ptr(C.u, j), st_ptr(C.g, j))}, 0, false);
+        if (sv.algorithm == ATM_AT_MGRIT) {
+            std::vector<AxpyJob<T>> vz;
+            vz.push_back(ajob(C.v, C.g));
+            vz.push_back(ajob(C.r, nullptr));
+            for (int i = 1; i < C.N; ++i) vz.push_back(ajob(st_ptr(C.v, i), nullptr));
+            add_axpy(ph, std::move(vz));
+            std::vector<Job<T>> js;   // r_j = Psi(v_{j-1}) + g_j - v_j
+            for (int j = 1; j < C.N; ++j)
+                js.push_back(job(st_ptr(C.v, j - 1), nullptr, st_ptr(C.g, j), nullptr, st_ptr(C.v, j), st_ptr(C.r, j)));
+            add_sweep(ph, L - 1, std::move(js), 0, false);
+            add_coarsest(ph);
+        } else {
+            add_axpy(ph, {ajob(C.u, C.g)});
+            for (int j = 1; j < C.N; ++j)
+                add_sweep(ph, L - 1, {job(st_ptr(C.u, j - 1), st_ptr(C.u, j), st_ptr(C.g, j))}, 0, false);
+        }
         for (int l = L - 2; l >= lowest; --l) {
             std::vector<AxpyJob<T>> cp;
             for (int i = (l == 0 ? 1 : 0); i < lv[l + 1].N; ++i)
                 cp.push_back(ajob(up(l, i * lv[l].m), st_ptr(lv[l + 1].u, i)));
             add_axpy(ph, std::move(cp));
-            if (l >= 1) add_frelax(ph, l, 0, false);
+            if (l >= 1) add_level_cycle(ph, l);
         }
+        ubase = saved_base;
     }
 
     // u^l_C += u^{l+1} - v^{l+1}
