@@ -134,6 +134,9 @@ typedef struct {
                                          passes for FP32 cycles while the inner iteration still
                                          contracts (256^2 Allen-Cahn to 1e-8: 14 FP64 passes with
                                          one inner cycle, 6 with three, 4 with five) */
+    int forcing;                      /* 1: level 0 has a right-hand side, u_j = Phi(u_{j-1}) + f_j
+                                         for j >= 1, f set by atm_set_rhs (zero until then); not
+                                         with C-point storage or ATM_FP32_REFINED */
     int nested_iteration;             /* 1: nested iteration -- every solve starts from the coarsest
                                          level's sequential solution (u_0 = the initial condition),
                                          interpolated down the hierarchy by injection and
@@ -188,6 +191,12 @@ atm_status atm_set_initial_condition(atm_handle *h, const double *u0);
  * iteration (its first F-relaxation overwrites the F-points); with C-point
  * storage only they are kept. */
 atm_status atm_set_initial_guess(atm_handle *h, const double *u);
+
+/* Set the right-hand side f_1 .. f_{nt_points-1} of a handle created with
+ * forcing = 1 (Sec. 2.2: forcing terms enter through the time integrator,
+ * u_j = Phi(u_{j-1}) + f_j).  `f`: FP64, nt_points states, host or device;
+ * state 0 is ignored (u_0 is the initial condition). */
+atm_status atm_set_rhs(atm_handle *h, const double *f);
 
 /* Run the solver (Algorithm 2 V-cycles, or sequential stepping) until the
  * residual 2-norm over the space-time points is <= tol or max_iter cycles

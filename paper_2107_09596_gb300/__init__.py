@@ -51,7 +51,8 @@ class SolverDesc(ctypes.Structure):
                 ("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("precision", ctypes.c_int), ("use_graph", ctypes.c_int),
                 ("profile", ctypes.c_int), ("sweep_kernel", ctypes.c_int),
-                ("refine_inner_cycles", ctypes.c_int), ("nested_iteration", ctypes.c_int),
+                ("refine_inner_cycles", ctypes.c_int), ("forcing", ctypes.c_int),
+                ("nested_iteration", ctypes.c_int),
                 ("cpoint_storage_only", ctypes.c_int)]
 
 
@@ -81,7 +82,7 @@ EXPORTS = ["atm_workspace_size", "atm_create", "atm_set_initial_condition",
            "atm_last_launch_count", "atm_get_kernel_profile", "atm_apply_propagator_noalloc",
            "atm_nn_param_count", "atm_nn_workspace_size", "atm_nn_apply", "atm_nn_loss_grad",
            "atm_train_learned_coarse", "atm_set_learned_coarse", "atm_batch_solve", "atm_last_error",
-           "atm_get_sweep_config", "atm_destroy"]
+           "atm_get_sweep_config", "atm_set_rhs", "atm_destroy"]
 
 _lib = None
 
@@ -106,6 +107,7 @@ def load(build_if_missing: bool = True):
     L.atm_create.argtypes = [ctypes.POINTER(Problem), ctypes.POINTER(SolverDesc), vp, ctypes.c_size_t, vp, ctypes.POINTER(vp)]
     L.atm_set_initial_condition.argtypes = [vp, vp]
     L.atm_set_initial_guess.argtypes = [vp, vp]
+    L.atm_set_rhs.argtypes = [vp, vp]
     L.atm_solve.argtypes = [vp, ctypes.POINTER(Result)]
     L.atm_get_solution.argtypes = [vp, i, i, vp]
     L.atm_get_residual_history.argtypes = [vp, vp, i, ctypes.POINTER(i)]
@@ -155,7 +157,7 @@ def make_solver(algorithm=AT_MGRIT, m=(8,), k=4, nu=1, fine_prop=PROP_PR_ADI,
                 coarse_prop=PROP_SPLIT_BE, reaction_substeps=None, coarse_reaction=REACT_EXACT,
                 tol=1e-10, max_iter=50,
                 precision=FP64, use_graph=True, profile=False, cpoint_only=False,
-                sweep_kernel=0, inner_cycles=0, nested=False) -> SolverDesc:
+                sweep_kernel=0, inner_cycles=0, nested=False, forcing=False) -> SolverDesc:
     s = SolverDesc()
     s.algorithm = algorithm
     s.levels = len(m) + 1
@@ -173,6 +175,7 @@ def make_solver(algorithm=AT_MGRIT, m=(8,), k=4, nu=1, fine_prop=PROP_PR_ADI,
     s.sweep_kernel = int(sweep_kernel)
     s.refine_inner_cycles = int(inner_cycles)
     s.nested_iteration = int(nested)
+    s.forcing = int(forcing)
     return s
 
 
@@ -244,6 +247,14 @@ class Solver:
         _check(load().atm_set_initial_condition(self.handle, ctypes.c_void_p(_ptr(u0))))
         self._leave()
         return u0
+
+    def set_rhs(self, f):
+        """Right-hand side f_j (nt states, FP64; state 0 ignored) of a handle created with forcing."""
+        f = self._f64(f)
+        self._enter()
+        _check(load().atm_set_rhs(self.handle, ctypes.c_void_p(_ptr(f))))
+        self._leave()
+        return f
 
     def set_initial_guess(self, u=None):
         """Iterate at time points >= 1 from `u` (nt states), or the zero guess."""

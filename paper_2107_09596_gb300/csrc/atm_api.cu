@@ -138,6 +138,12 @@ atm_status atm_set_initial_guess(atm_handle *h, const double *u)
     return h->p->set_state(1, n - 1, u + nsp);
 }
 
+atm_status atm_set_rhs(atm_handle *h, const double *f)
+{
+    if (!h || !f) return atm::fail(ATM_ERR_INVALID_ARG, "null argument");
+    return h->p->set_rhs(f);
+}
+
 atm_status atm_solve(atm_handle *h, atm_result *out)
 {
     if (!h) return atm::fail(ATM_ERR_INVALID_ARG, "null handle");

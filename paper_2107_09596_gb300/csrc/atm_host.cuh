@@ -94,6 +94,7 @@ inline SweepFn<T> pick_row(int C)
 template <typename T>
 inline SweepFn<T> row_kernel(int C, bool dirichlet, bool pr, bool react)
 {
+    if (dirichlet && C == 64) return row_sweep_kernel<T, 64, true, false, false, true>;   // lines up to 2048
     if (dirichlet) return pick_row<T, true, false, false, true>(C);
     if (pr) return react ? pick_row<T, false, true, true, false>(C) : pick_row<T, false, true, false, false>(C);
     return react ? pick_row<T, false, false, true, false>(C) : pick_row<T, false, false, false, false>(C);
@@ -306,6 +307,7 @@ struct PlanBase {
     virtual ~PlanBase() {}
     virtual atm_status finish_create() = 0;
     virtual atm_status set_state(int t0, int count, const double *src) = 0;
+    virtual atm_status set_rhs(const double *) { return fail(ATM_ERR_UNSUPPORTED, "no right-hand side on this handle"); }
     virtual atm_status get_state(int t0, int count, double *dst) = 0;
     virtual atm_status solve(atm_result *res) = 0;
     virtual atm_status apply_prop(int level, const double *in, double *out, int n) = 0;
@@ -468,7 +470,7 @@ struct Plan : PlanBase {
         if (!(pb.dt > 0) || !(pb.lx > 0) || (!is1d && !(pb.ly > 0))) return fail(ATM_ERR_INVALID_ARG, "dt, lx, ly must be > 0");
         if (pb.kind == ATM_ALLEN_CAHN && !(pb.eps > 0)) return fail(ATM_ERR_INVALID_ARG, "eps must be > 0");
         if (is1d) {
-            if (pb.nx < 2 || pb.nx > 1024) return fail(ATM_ERR_INVALID_ARG, "heat1d needs 2 <= nx <= 1024");
+            if (pb.nx < 2 || pb.nx > 2048) return fail(ATM_ERR_INVALID_ARG, "heat1d needs 2 <= nx <= 2048");
         } else {
             const int nmax = sizeof(T) == 4 ? 1024 : 512;
             if (!pow2_in(pb.nx, 32, nmax) || !pow2_in(pb.ny, 32, nmax))
@@ -495,6 +497,8 @@ struct Plan : PlanBase {
             if (sv.fine_prop < 0 || sv.fine_prop > 1 || sv.coarse_prop < 0 || sv.coarse_prop > 3)
                 return fail(ATM_ERR_INVALID_ARG, "unknown propagator");
         }
+        if (sv.forcing && (sv.cpoint_storage_only || role != ROLE_NORMAL))
+            return fail(ATM_ERR_UNSUPPORTED, "a right-hand side needs full storage and a plain FP64/FP32 handle");
         if (sv.cpoint_storage_only && sv.algorithm == ATM_SEQUENTIAL && sv.m[0] == 1)
             return fail(ATM_ERR_INVALID_ARG, "C-point storage needs m[0] >= 2 (or 0 for the default 16)");
         if (sv.coarse_prop == ATM_PROP_LEARNED || sv.coarse_prop == ATM_PROP_LEARNED_CORRECTION) {
@@ -920,7 +924,7 @@ struct Plan : PlanBase {
         }
         if (sv.algorithm == ATM_SEQUENTIAL) {
             for (int j = 1; j < pb.nt_points; ++j)
-                add_sweep(seq, 0, {job(up(0, j - 1), up(0, j))}, 0, false);
+                add_sweep(seq, 0, {job(up(0, j - 1), up(0, j), gl(0, j))}, 0, false);
             add_regen_jobs();
             return;
         }
@@ -991,6 +995,7 @@ struct Plan : PlanBase {
         bwork = nullptr;
         if (cpo) work = take<T>(n0);
         if (role == ROLE_OUTER) r_full = take<T>(n0);
+        if (role == ROLE_NORMAL && sv.forcing) lv[0].g = take<T>(n0);
         if (role == ROLE_INNER) {
             lv[0].g = take<T>(n0);
             ubase = take<T>(n0);
@@ -1541,6 +1546,7 @@ struct Plan : PlanBase {
         ATM_CK(cudaMemsetAsync(lv[0].u, 0, n0, st));
         if (work) ATM_CK(cudaMemsetAsync(work, 0, n0, st));
         if (r_full) ATM_CK(cudaMemsetAsync(r_full, 0, n0, st));
+        if (role == ROLE_NORMAL && lv[0].g) ATM_CK(cudaMemsetAsync(lv[0].g, 0, n0, st));
         if (role == ROLE_INNER) {
             ATM_CK(cudaMemsetAsync(lv[0].g, 0, n0, st));
             ATM_CK(cudaMemsetAsync(ubase, 0, n0, st));
@@ -1912,10 +1918,19 @@ struct Plan : PlanBase {
 
     // With C-point storage only the C-points of a written range are kept: the
     // iteration recomputes every F-point from the C-points before it reads one.
+    atm_status set_rhs(const double *src) override
+    {
+        if (role != ROLE_NORMAL || !lv[0].g)
+            return fail(ATM_ERR_INVALID_ARG, "the handle was not created with forcing = 1");
+        return write_states(st_ptr(lv[0].g, 1), src + nsp, lv[0].N - 1);
+    }
+
     atm_status set_state(int t0, int count, const double *src) override
     {
         if (!src || t0 < 0 || count < 0 || t0 + count > lv[0].N) return fail(ATM_ERR_INVALID_ARG, "state range out of bounds");
         if (count == 0) return ATM_OK;
+        // with a right-hand side, g_0 mirrors the initial condition (u_0 = g_0)
+        if (t0 == 0 && role == ROLE_NORMAL && lv[0].g) ATM_TRY(write_states(lv[0].g, src, 1));
         if (!cpo) return write_states(st_ptr(lv[0].u, t0), src, count);
         const int m = lv[0].m;
         for (int i = (t0 + m - 1) / m; i * m < t0 + count; ++i)

@@ -5,6 +5,11 @@ propagators themselves agree to ~1e-15 (different rounding order of the same
 exact solve).  FP32 bar: relative L2 <= 3e-6 for one propagator application
 (FP32 rounding of ~20 operations per value), looser where errors accumulate
 over many steps, as stated per test."""
+import ctypes
+import json
+import math
+import os
+
 import numpy as np
 import pytest
 
@@ -382,3 +387,76 @@ def test_nested_iteration_in_the_refined_mode(torch):
     seq = oracle.sequential(oc, u0)
     assert rel_l2(res[1][1], seq) <= 1e-7
 
+
+
+def forced_heat(oc, nx, nt, dt, lx):
+    """Right-hand side of the forced heat problem u = sin(pi x / lx * lx) cos t
+    on [0, lx] (Sec. 4.3 reading): f_j = Phi(dt b_j), f_0 = the initial condition."""
+    x = lx * np.arange(1, nx + 1) / (nx + 1)
+    t = np.arange(nt) * dt
+    b = -np.sin(np.pi * x)[None, :] * (np.sin(t) - np.pi ** 2 * np.cos(t))[:, None]
+    g = oracle.apply_prop(oc, 0, dt * b)
+    g[0] = np.sin(np.pi * x)
+    return g
+
+
+@pytest.mark.parametrize("algorithm", ["at", "seq"])
+def test_forcing_matches_oracle(torch, algorithm):
+    """A level-0 right-hand side (u_j = Phi(u_{j-1}) + f_j): iterates after 1
+    and 4 cycles (and sequential stepping) equal the oracle's with the same f."""
+    nx, nt, lx = 63, 257, 3.0
+    dt = math.pi / (nt - 1)
+    for cycles in ((1, 4) if algorithm == "at" else (0,)):
+        oc, gp, gs = pair(kind="heat1d", nx=nx, lx=lx, dt=dt, nt=nt, m=(8,), k=4, nu=0, tol=0.0,
+                          max_iter=cycles, algorithm=algorithm)
+        gs.forcing = 1
+        g = forced_heat(oc, nx, nt, dt, lx)
+        s = atm.Solver(gp, gs)
+        s.set_initial_condition(dev(torch, g[0]))
+        s.set_rhs(dev(torch, g))
+        s.solve()
+        got = s.solution().cpu().numpy()
+        if algorithm == "seq":
+            want = _oracle_seq(oc, g)
+        else:
+            want = np.zeros_like(g)
+            want[0] = g[0]
+            oracle.solve(oc, want, cycles, 0.0, np.ascontiguousarray(g))
+        assert rel_l2(got, want) <= 1e-12, (cycles, rel_l2(got, want))
+
+
+def _oracle_seq(oc, g):
+    u = np.zeros_like(g)
+    u[0] = g[0]
+    oracle.lib().or_sequential(ctypes.byref(oc), oracle._ptr(np.ascontiguousarray(g)), oracle._ptr(u))
+    return u
+
+
+def test_heat_k_study_on_the_gpu(torch):
+    """Sec. 4.3 on the GPU: 1D heat, 1025 unknowns, 16384 time points, two-level
+    F-relaxation with m = 128, random initial guess, absolute residual 1e-7:
+    k = 12 needs as many cycles as k = 128 (Parareal), and both counts equal
+    the oracle's (FP64 parity of the whole iteration)."""
+    s_ = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))["heat_k_study"]
+    nx, nt, m, tol = s_["nx"], s_["nt_points"], s_["m"], s_["tol"]
+    lx = 3.0
+    dt = math.pi / (nt - 1)
+    cycles = {}
+    for k in (s_["k_small"], s_["k_parareal"]):
+        oc, gp, gs = pair(kind="heat1d", nx=nx, lx=lx, dt=dt, nt=nt, m=(m,), k=k, nu=0, tol=tol, max_iter=60)
+        gs.forcing = 1
+        g = forced_heat(oc, nx, nt, dt, lx)
+        u = I.random_guess(nt, (nx,), 1)
+        u[0] = g[0]
+        s = atm.Solver(gp, gs)
+        s.set_initial_condition(dev(torch, g[0]))
+        s.set_initial_guess(dev(torch, u))
+        s.set_rhs(dev(torch, g))
+        r = s.solve()
+        it_o, hist_o = oracle.solve(oc, np.ascontiguousarray(u), 60, tol, np.ascontiguousarray(g))
+        print(f"\nk = {k}: GPU {r['iterations']} cycles, oracle {it_o}; residuals "
+              f"{np.round(np.log10(s.residual_history()), 1)}")
+        assert r["converged"] and r["iterations"] == it_o
+        np.testing.assert_allclose(s.residual_history(), hist_o, rtol=1e-8, atol=1e-13)
+        cycles[k] = r["iterations"]
+    assert abs(cycles[s_["k_small"]] - cycles[s_["k_parareal"]]) <= 1, cycles
