@@ -44,6 +44,7 @@ class OrCfg(ctypes.Structure):
         ("prop", ctypes.c_int * MAXLEV),
         ("react_sub", ctypes.c_int * MAXLEV),
         ("react_exact", ctypes.c_int * MAXLEV),
+        ("fcycle", ctypes.c_int),
     ]
 
 
@@ -102,7 +103,7 @@ def _ptr(a):
 
 
 def make_cfg(kind, nx, ny=1, lx=1.0, ly=1.0, dt=1.0 / 1024, nt=1025, eps=0.02,
-             m=(8,), k=4, nu=1, prop=None, react_sub=None, react_exact=None) -> OrCfg:
+             m=(8,), k=4, nu=1, prop=None, react_sub=None, react_exact=None, fcycle=False) -> OrCfg:
     """Problem + solver description.  ``m`` has one entry per coarsening
     (levels = len(m) + 1).  ``k <= 0`` selects plain MGRIT.  ``prop`` per level
     defaults to PR on level 0 and split-BE on coarser levels (2D) or BE (1D)."""
@@ -113,6 +114,7 @@ def make_cfg(kind, nx, ny=1, lx=1.0, ly=1.0, dt=1.0 / 1024, nt=1025, eps=0.02,
     for i, mi in enumerate(m):
         c.m[i] = mi
     c.k, c.nu = k, nu
+    c.fcycle = int(fcycle)
     if prop is None:
         prop = [PROP_PR if (kind != HEAT1D and l == 0) else PROP_SPLIT for l in range(c.levels)]
     for i, p in enumerate(prop):

@@ -69,6 +69,7 @@ typedef struct {
     int prop[OR_MAXLEV];    /* propagator per level */
     int react_sub[OR_MAXLEV]; /* reaction substeps per level; 0 = product of m below */
     int react_exact[OR_MAXLEV]; /* 1: exact flow of the reaction ODE instead of substeps */
+    int fcycle;             /* 1: F-cycles instead of V-cycles */
 } or_cfg;
 
 static int nspace(const or_cfg *c) { return c->kind == OR_HEAT1D ? c->nx : c->nx * c->ny; }
@@ -446,6 +447,28 @@ static void cycle(or_ctx *x, int l)
     f_relax(x, l);
 }
 
+/* One FAS F-cycle from level l (Sec. 2.2 names F-cycles as an alternative
+ * cycle type): as the V-cycle, but the coarse problem is treated by an
+ * F-cycle followed by a V-cycle on the same coarse problem, so that the
+ * coarsest level is visited several times per iteration. */
+static void fcycle(or_ctx *x, int l)
+{
+    if (l == x->L - 1) {
+        coarsest(x, l);
+        return;
+    }
+    f_relax(x, l);
+    for (int q = 0; q < x->c->nu; ++q) {
+        c_relax(x, l);
+        f_relax(x, l);
+    }
+    restrict_fas(x, l);
+    fcycle(x, l + 1);
+    if (l + 1 < x->L - 1) cycle(x, l + 1);
+    correct(x, l);
+    f_relax(x, l);
+}
+
 static double c_residual_norm(or_ctx *x, int l)
 {
     const int N = x->lv[l].N, m = x->c->m[l], NC = (N - 1) / m + 1, n = x->n;
@@ -525,7 +548,8 @@ int or_solve(const or_cfg *c, double *g, double *u, int max_iter, double tol, do
     hist[0] = c_residual_norm(&x, 0);
     int it = 0;
     while (it < max_iter && hist[it] > tol) {
-        cycle(&x, 0);
+        if (c->fcycle) fcycle(&x, 0);
+        else cycle(&x, 0);
         ++it;
         hist[it] = c_residual_norm(&x, 0);
     }

@@ -282,3 +282,42 @@ def test_nested_guess_two_levels(orc, k):
             np.testing.assert_array_equal(u[8 * p], w)
         else:
             np.testing.assert_array_equal(u[8 * p], 0.0 * w)
+
+
+@pytest.mark.parametrize("k", [0, 3])
+def test_fcycle_two_levels_is_the_v_cycle(orc, k):
+    """With two levels an F-cycle has no intermediate level to revisit: its
+    iterates equal the V-cycle's bit for bit (MGRIT and AT-MGRIT)."""
+    nx, nt, m = 15, 65, 4
+    u0 = I.heat1d_initial_condition(nx, 2)
+    out = []
+    for fc in (False, True):
+        c = orc.make_cfg(orc.HEAT1D, nx, dt=1.0 / 64, nt=nt, m=(m,), k=k, nu=1, fcycle=fc)
+        u = guess(c, u0, 3)
+        _, h = orc.solve(c, u, 3)
+        out.append((u, h))
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    np.testing.assert_array_equal(out[0][1], out[1][1])
+
+
+def test_fcycle_three_levels(orc):
+    """Three levels, AT-MGRIT on the heat problem: the F-cycle converges to the
+    sequential solution, each of its cycles contracts the C-point error at
+    least as much as a V-cycle's from the same iterate, and it differs from
+    the V-cycle (the intermediate level is visited twice)."""
+    nx, nt = 15, 129
+    u0 = I.heat1d_initial_condition(nx, 4)
+    cv = orc.make_cfg(orc.HEAT1D, nx, dt=1.0 / 64, nt=nt, m=(4, 4), k=3, nu=0)
+    cf = orc.make_cfg(orc.HEAT1D, nx, dt=1.0 / 64, nt=nt, m=(4, 4), k=3, nu=0, fcycle=True)
+    seq = orc.sequential(cv, u0)
+    uv, uf = guess(cv, u0, 5), guess(cf, u0, 5)
+    for _ in range(4):
+        ev0 = np.linalg.norm((uv - seq)[::4])
+        orc.solve(cv, uv, 1)
+        ef0 = np.linalg.norm((uf - seq)[::4])
+        orc.solve(cf, uf, 1)
+        assert np.linalg.norm((uf - seq)[::4]) / ef0 <= np.linalg.norm((uv - seq)[::4]) / ev0 + 1e-12
+    assert not np.array_equal(uv, uf)
+    it, h = orc.solve(cf, uf, 60, 1e-13)
+    assert h[-1] <= 1e-13
+    assert np.abs(uf - seq).max() <= 1e-12
