@@ -294,7 +294,7 @@ def train_learned(atm, w, device, steps, seeds=(101, 102, 103, 104, 105), batch=
 
 
 def make_desc(atm, w, algorithm, precision, profile, coarse="classical", sweep="auto", cpoint=False,
-              inner_cycles=0, nu=None, nested=False):
+              inner_cycles=0, nu=None, nested=False, fcycle=False):
     kind = {"ac": atm.ALLEN_CAHN, "heat1d": atm.HEAT1D}[w["kind"]]
     ny = w["n"] if w["kind"] != "heat1d" else 1
     prob = atm.make_problem(kind, w["n"], ny, dt=w["dt"], nt_points=w["nt"], eps=w["eps"])
@@ -306,7 +306,7 @@ def make_desc(atm, w, algorithm, precision, profile, coarse="classical", sweep="
                                coarse, atm.PROP_SPLIT_BE),
                            sweep_kernel={"auto": atm.SWEEP_AUTO, "split": atm.SWEEP_SPLIT,
                                          "fused": atm.SWEEP_FUSED, "chain": atm.SWEEP_CHAIN}[sweep],
-                           cpoint_only=cpoint, inner_cycles=inner_cycles, nested=nested)
+                           cpoint_only=cpoint, inner_cycles=inner_cycles, nested=nested, fcycle=fcycle)
     return prob, desc
 
 
@@ -408,6 +408,7 @@ def main():
                     help="fp32r: FP32 V-cycles per FP64 refinement step (0: the library default, 5)")
     ap.add_argument("--max-iter", type=int, default=None, help="override the workload's cycle cap")
     ap.add_argument("--nested", action="store_true", help="nested iteration: start from the coarse hierarchy")
+    ap.add_argument("--fcycle", action="store_true", help="F-cycles instead of V-cycles")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.workload == "batch64":
@@ -435,7 +436,7 @@ def main():
                                                 correction=args.coarse == "correction")
     prob, desc = make_desc(atm, w, args.algorithm, prec, profile=True, coarse=args.coarse,
                            sweep=args.sweep_kernel, cpoint=args.storage == "cpoint",
-                           inner_cycles=args.inner_cycles, nu=args.nu, nested=args.nested)
+                           inner_cycles=args.inner_cycles, nu=args.nu, nested=args.nested, fcycle=args.fcycle)
     solver = atm.Solver(prob, desc, device=device)
     if args.coarse in ("learned", "correction"):
         solver.set_learned_coarse(nn_params)
@@ -560,6 +561,7 @@ def main():
                            **({"nu": args.nu} if args.nu is not None else {}),
                            "algorithm": args.algorithm, "parallelism": f"{world} independent problems",
                            "sweep_kernel": args.sweep_kernel, "storage": args.storage, "nested": args.nested,
+                           "cycle": "F" if args.fcycle else "V",
                            "inner_cycles": (args.inner_cycles or 5) if args.precision == "fp32r" else None,
                            "l2": "working set larger than L2 (workspace %.2f GB; one level-0 launch reads and "
                                  "writes %.0f MB)" % (atm.workspace_size(prob, desc) / 1e9,

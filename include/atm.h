@@ -134,6 +134,10 @@ typedef struct {
                                          passes for FP32 cycles while the inner iteration still
                                          contracts (256^2 Allen-Cahn to 1e-8: 14 FP64 passes with
                                          one inner cycle, 6 with three, 4 with five) */
+    int cycle_type;                   /* 0: V-cycles (Algorithm 2); 1: F-cycles -- each coarse
+                                         problem is treated by an F-cycle followed by a V-cycle
+                                         (Sec. 2.2), so the coarsest level is visited several times
+                                         per iteration */
     int forcing;                      /* 1: level 0 has a right-hand side, u_j = Phi(u_{j-1}) + f_j
                                          for j >= 1, f set by atm_set_rhs (zero until then); not
                                          with C-point storage or ATM_FP32_REFINED */

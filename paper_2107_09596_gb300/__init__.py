@@ -51,7 +51,7 @@ class SolverDesc(ctypes.Structure):
                 ("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("precision", ctypes.c_int), ("use_graph", ctypes.c_int),
                 ("profile", ctypes.c_int), ("sweep_kernel", ctypes.c_int),
-                ("refine_inner_cycles", ctypes.c_int), ("forcing", ctypes.c_int),
+                ("refine_inner_cycles", ctypes.c_int), ("cycle_type", ctypes.c_int), ("forcing", ctypes.c_int),
                 ("nested_iteration", ctypes.c_int),
                 ("cpoint_storage_only", ctypes.c_int)]
 
@@ -157,7 +157,7 @@ def make_solver(algorithm=AT_MGRIT, m=(8,), k=4, nu=1, fine_prop=PROP_PR_ADI,
                 coarse_prop=PROP_SPLIT_BE, reaction_substeps=None, coarse_reaction=REACT_EXACT,
                 tol=1e-10, max_iter=50,
                 precision=FP64, use_graph=True, profile=False, cpoint_only=False,
-                sweep_kernel=0, inner_cycles=0, nested=False, forcing=False) -> SolverDesc:
+                sweep_kernel=0, inner_cycles=0, nested=False, forcing=False, fcycle=False) -> SolverDesc:
     s = SolverDesc()
     s.algorithm = algorithm
     s.levels = len(m) + 1
@@ -176,6 +176,7 @@ def make_solver(algorithm=AT_MGRIT, m=(8,), k=4, nu=1, fine_prop=PROP_PR_ADI,
     s.refine_inner_cycles = int(inner_cycles)
     s.nested_iteration = int(nested)
     s.forcing = int(forcing)
+    s.cycle_type = int(fcycle)
     return s
 
 

@@ -497,6 +497,7 @@ struct Plan : PlanBase {
             if (sv.fine_prop < 0 || sv.fine_prop > 1 || sv.coarse_prop < 0 || sv.coarse_prop > 3)
                 return fail(ATM_ERR_INVALID_ARG, "unknown propagator");
         }
+        if (sv.cycle_type < 0 || sv.cycle_type > 1) return fail(ATM_ERR_INVALID_ARG, "cycle_type must be 0 (V) or 1 (F)");
         if (sv.forcing && (sv.cpoint_storage_only || role != ROLE_NORMAL))
             return fail(ATM_ERR_UNSUPPORTED, "a right-hand side needs full storage and a plain FP64/FP32 handle");
         if (sv.cpoint_storage_only && sv.algorithm == ATM_SEQUENTIAL && sv.m[0] == 1)
@@ -860,6 +861,26 @@ struct Plan : PlanBase {
         add_axpy(ph, std::move(js));
     }
 
+    // F-cycle from level l (Sec. 2.2): as add_level_cycle, but the coarse
+    // problem gets an F-cycle followed by a V-cycle on the same coarse problem.
+    void add_level_fcycle(Phase &ph, int l)
+    {
+        if (l == L - 1) {
+            add_coarsest(ph);
+            return;
+        }
+        if (sv.nu == 1) {
+            add_frelax(ph, l, 0, false);
+            add_crelax(ph, l);
+        }
+        add_frelax(ph, l, 2, false);
+        add_restrict(ph, l);
+        add_level_fcycle(ph, l + 1);
+        if (l + 1 < L - 1) add_level_cycle(ph, l + 1);
+        add_correct(ph, l);
+        if (!(cpo && l == 0 && role == ROLE_INNER)) add_frelax(ph, l, 0, false);
+    }
+
     // Algorithm 2 on level l (one V-cycle visit; level 0 only with a right-hand side).
     void add_level_cycle(Phase &ph, int l)
     {
@@ -916,7 +937,8 @@ struct Plan : PlanBase {
             // the defect problem e_j = [Phi(u_{j-1} + e_{j-1}) - Phi(u_{j-1})] + r_j,
             // e_0 = r_0 = 0: its right-hand side is r itself (staged in g by the
             // caller), its iterate starts at zero
-            add_level_cycle(inner_cycle, 0);
+            if (sv.cycle_type == 1) add_level_fcycle(inner_cycle, 0);
+            else add_level_cycle(inner_cycle, 0);
             // nested iteration of the refined mode: the coarse hierarchy of the
             // original problem in FP32, down to level 1 (the caller stages u0)
             if (sv.nested_iteration && L > 1) add_nested(nested, 1);
@@ -937,7 +959,12 @@ struct Plan : PlanBase {
             add_frelax(rest, 0, 2, false);
         }
         add_restrict(rest, 0);
-        add_level_cycle(rest, 1);
+        if (sv.cycle_type == 1) {
+            add_level_fcycle(rest, 1);
+            if (L > 2) add_level_cycle(rest, 1);
+        } else {
+            add_level_cycle(rest, 1);
+        }
         add_correct(rest, 0);
         if (sv.nested_iteration) add_nested(nested, 0);
         passA0 = nested;

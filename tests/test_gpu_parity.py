@@ -460,3 +460,45 @@ def test_heat_k_study_on_the_gpu(torch):
         np.testing.assert_allclose(s.residual_history(), hist_o, rtol=1e-8, atol=1e-13)
         cycles[k] = r["iterations"]
     assert abs(cycles[s_["k_small"]] - cycles[s_["k_parareal"]]) <= 1, cycles
+
+
+FCYCLE_CASES = {
+    "ac_3lvl_ragged": dict(kind="ac", nx=64, ny=64, dt=1e-4, nt=300, m=(4, 4), k=3, nu=1),
+    "ac_4lvl_f": dict(kind="ac", nx=32, ny=32, dt=1e-4, nt=257, m=(4, 2, 2), k=4, nu=0),
+    "heat1d_3lvl_mgrit": dict(kind="heat1d", nx=127, dt=1 / 1024, nt=1025, m=(8, 4), k=0, nu=1, algorithm="mgrit"),
+}
+
+
+@pytest.mark.parametrize("case", sorted(FCYCLE_CASES))
+def test_fcycle_iterates_match_oracle(torch, case):
+    """F-cycles (an F-cycle plus a V-cycle on each coarse problem): iterates after
+    1 and 3 cycles equal the oracle's F-cycle iterates (FP64, <= 1e-12)."""
+    kw = FCYCLE_CASES[case]
+    shape = (kw["nx"],) if kw["kind"] == "heat1d" else (kw["ny"], kw["nx"])
+    u0 = I.heat1d_initial_condition(kw["nx"], 7) if kw["kind"] == "heat1d" else I.uniform_field(shape, 7)
+    for cycles in (1, 3):
+        oc, gp, gs = pair(tol=0.0, max_iter=cycles, **kw)
+        gs.cycle_type = 1
+        oc.fcycle = 1
+        s = atm.Solver(gp, gs)
+        s.set_initial_condition(dev(torch, u0))
+        s.solve()
+        want = np.zeros((kw["nt"],) + shape)
+        want[0] = u0
+        _, hist = oracle.solve(oc, want, cycles, 0.0)
+        got = s.solution().cpu().numpy()
+        assert rel_l2(got, want) <= 1e-12, (cycles, rel_l2(got, want))
+        np.testing.assert_allclose(s.residual_history(), hist, rtol=1e-9, atol=1e-14)
+
+
+def test_fcycle_refined_reaches_fp64_accuracy(torch):
+    kw = dict(kind="ac", nx=64, ny=64, dt=1e-4, nt=257, m=(4, 4), k=4, nu=1, tol=1e-9, max_iter=40,
+              precision=atm.FP32_REFINED, cpoint_only=True)
+    oc, gp, gs = pair(**kw)
+    gs.cycle_type = 1
+    s = atm.Solver(gp, gs)
+    u0 = I.uniform_field((64, 64), 8)
+    s.set_initial_condition(dev(torch, u0))
+    r = s.solve()
+    assert r["converged"], r
+    assert rel_l2(s.solution().cpu().numpy(), oracle.sequential(oc, u0)) <= 1e-7
