@@ -114,3 +114,24 @@ def conv_net_init(seed: int = 0, channels=(1, 32, 32, 32, 32, 1)):
         w = (2 * uniform01(seed + li, co * ci * 9) - 1).reshape(co, ci, 3, 3) * bound
         params.append((w, np.zeros(co)))
     return params
+
+
+def gray_scott_initial_condition(nx: int, ny: int, lx: float = 2.5, ly: float = 2.5) -> np.ndarray:
+    """The Gray-Scott initial state of Sec. 5.1 on the periodic grid
+    x_i = i lx / nx, y_j = j ly / ny: inside the square [1, 1.5]^2,
+    s = 0.25 sin^2(4 pi x) sin^2(4 pi y), u = 1 - 2 s, v = s; outside, u = 1,
+    v = 0.  Shape (2, ny, nx): the u field, then the v field."""
+    x = np.arange(nx) * (lx / nx)
+    y = np.arange(ny) * (ly / ny)
+    Y, X = np.meshgrid(y, x, indexing="ij")
+    inside = (X >= 1.0) & (X <= 1.5) & (Y >= 1.0) & (Y <= 1.5)
+    s = np.where(inside, 0.25 * np.sin(4 * np.pi * X) ** 2 * np.sin(4 * np.pi * Y) ** 2, 0.0)
+    return np.ascontiguousarray(np.stack([1.0 - 2.0 * s, s]))
+
+
+def gray_scott_random_state(nx: int, ny: int, seed: int = 0) -> np.ndarray:
+    """A seeded state of the Gray-Scott ranges: u uniform in [0.2, 1], v
+    uniform in [0, 0.45] (the ranges a run from the Sec. 5.1 initial state
+    visits).  Shape (2, ny, nx)."""
+    r = uniform01(seed, 2 * nx * ny).reshape(2, ny, nx)
+    return np.ascontiguousarray(np.stack([0.2 + 0.8 * r[0], 0.45 * r[1]]))

@@ -22,7 +22,7 @@ _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-HEAT1D, HEAT2D, ALLEN_CAHN = 0, 1, 2
+HEAT1D, HEAT2D, ALLEN_CAHN, GRAY_SCOTT = 0, 1, 2, 3
 PROP_SPLIT, PROP_PR, PROP_FINEPOW = 0, 1, 2
 MAXLEV = 8
 
@@ -45,6 +45,7 @@ class OrCfg(ctypes.Structure):
         ("react_sub", ctypes.c_int * MAXLEV),
         ("react_exact", ctypes.c_int * MAXLEV),
         ("fcycle", ctypes.c_int),
+        ("ext_prop", ctypes.c_void_p),
     ]
 
 
@@ -102,12 +103,28 @@ def _ptr(a):
     return a.ctypes.data
 
 
+# Gray-Scott propagators and their C callbacks stay alive for the process
+_keep = []
+
+
 def make_cfg(kind, nx, ny=1, lx=1.0, ly=1.0, dt=1.0 / 1024, nt=1025, eps=0.02,
-             m=(8,), k=4, nu=1, prop=None, react_sub=None, react_exact=None, fcycle=False) -> OrCfg:
+             m=(8,), k=4, nu=1, prop=None, react_sub=None, react_exact=None, fcycle=False,
+             gs=None) -> OrCfg:
     """Problem + solver description.  ``m`` has one entry per coarsening
     (levels = len(m) + 1).  ``k <= 0`` selects plain MGRIT.  ``prop`` per level
-    defaults to PR on level 0 and split-BE on coarser levels (2D) or BE (1D)."""
+    defaults to PR on level 0 and split-BE on coarser levels (2D) or BE (1D).
+    Gray-Scott (Sec. 5.1): ``gs`` = dict(du, dv, feed, kill, tol, max_iter);
+    the propagator object is ``cfg.gray_scott``."""
     c = OrCfg()
+    if kind == GRAY_SCOTT:
+        from .gray_scott import GrayScott, make_callback
+        p = dict(du=8e-5, dv=4e-5, feed=0.024, kill=0.06, tol=1e-10, max_iter=50)
+        p.update(gs or {})
+        model = GrayScott(nx, ny, lx, ly, **p)
+        cb = make_callback(model)
+        _keep.append((model, cb))
+        c.ext_prop = ctypes.cast(cb, ctypes.c_void_p).value
+        c.gray_scott = model
     c.kind, c.nx, c.ny = kind, nx, (1 if kind == HEAT1D else ny)
     c.lx, c.ly, c.dt, c.nt, c.eps = lx, ly, dt, nt, eps
     c.levels = len(m) + 1
@@ -129,6 +146,8 @@ def make_cfg(kind, nx, ny=1, lx=1.0, ly=1.0, dt=1.0 / 1024, nt=1025, eps=0.02,
 
 
 def state_shape(c: OrCfg):
+    if c.kind == GRAY_SCOTT:
+        return (2, c.ny, c.nx)
     return (c.nx,) if c.kind == HEAT1D else (c.ny, c.nx)
 
 

@@ -52,7 +52,12 @@
 
 #define OR_MAXLEV 8
 
-enum { OR_HEAT1D = 0, OR_HEAT2D = 1, OR_ALLEN_CAHN = 2 };
+enum { OR_HEAT1D = 0, OR_HEAT2D = 1, OR_ALLEN_CAHN = 2, OR_GRAY_SCOTT = 3 };
+
+/* Propagator supplied by the caller (Gray-Scott: one backward Euler step
+ * solved by Newton's method, written in numpy/scipy): out = Phi(in) with step
+ * D on level `level`. */
+typedef void (*or_ext_prop_fn)(int level, double D, const double *in, double *out);
 enum { OR_PROP_SPLIT = 0, OR_PROP_PR = 1, OR_PROP_FINEPOW = 2 };
 
 typedef struct {
@@ -70,9 +75,15 @@ typedef struct {
     int react_sub[OR_MAXLEV]; /* reaction substeps per level; 0 = product of m below */
     int react_exact[OR_MAXLEV]; /* 1: exact flow of the reaction ODE instead of substeps */
     int fcycle;             /* 1: F-cycles instead of V-cycles */
+    or_ext_prop_fn ext_prop; /* Gray-Scott: the caller's propagator */
 } or_cfg;
 
-static int nspace(const or_cfg *c) { return c->kind == OR_HEAT1D ? c->nx : c->nx * c->ny; }
+static int nspace(const or_cfg *c)
+{
+    if (c->kind == OR_HEAT1D) return c->nx;
+    /* Gray-Scott: the u field, then the v field */
+    return c->kind == OR_GRAY_SCOTT ? 2 * c->nx * c->ny : c->nx * c->ny;
+}
 static int nmax(const or_cfg *c) { return c->nx > c->ny ? c->nx : c->ny; }
 
 /* number of time points on level l: C-points of level l-1 are every m-th point */
@@ -234,6 +245,12 @@ void or_apply_prop_ws(const or_cfg *c, int l, const double *in, double *out, dou
     if (c->kind == OR_HEAT1D) {
         const double dx = c->lx / (c->nx + 1);
         solve_dirichlet(c->nx, D / (dx * dx), in, out, ws);
+        return;
+    }
+    if (c->kind == OR_GRAY_SCOTT) {
+        /* one caller at a time (the callback takes the Python interpreter) */
+#pragma omp critical(or_ext_prop)
+        c->ext_prop(l, D, in, out);
         return;
     }
     const int pr = (c->prop[l] == OR_PROP_PR);
