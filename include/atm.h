@@ -55,7 +55,21 @@ typedef enum {
 enum {
     ATM_HEAT1D = 0,      /* u_t = u_xx on [0, lx], Dirichlet 0, nx interior points, dx = lx/(nx+1) */
     ATM_HEAT2D = 1,      /* u_t = u_xx + u_yy, periodic [0,lx) x [0,ly), dx = lx/nx, dy = ly/ny */
-    ATM_ALLEN_CAHN = 2   /* u_t = Lap u + (u - u^3)/eps^2, periodic as ATM_HEAT2D */
+    ATM_ALLEN_CAHN = 2,  /* u_t = Lap u + (u - u^3)/eps^2, periodic as ATM_HEAT2D */
+    ATM_GRAY_SCOTT = 3   /* Sec. 5.1: u_t = Du Lap u - u v^2 + F (1 - u),
+                            v_t = Dv Lap v + u v^2 - (K + F) v, periodic as ATM_HEAT2D.
+                            A state is the u field followed by the v field (2 nx ny
+                            values).  Every level's propagator is one backward Euler
+                            step (step D of the level) solved by Newton's method: each
+                            Newton system by GMRES with right preconditioning (x line
+                            solves, the pointwise 2x2 reaction Jacobian, y line solves),
+                            relative tolerance 1e-7, restart 20, at most 200 iterations;
+                            a halving line search on the 2-norm of the step's residual G;
+                            stop when ||G||_2 <= max(newton_tol, newton_tol ||G(w_prev)||_2).
+                            One CTA per state.  FP64 only; 8 <= nx, ny <= 512 (any
+                            value); the propagator options and sweep kernels of the
+                            other 2D families do not apply (ATM_SWEEP_AUTO or
+                            ATM_SWEEP_SPLIT). */
 };
 
 /* One-step propagators of the 2D families on a level with step D (heat1d is
@@ -92,12 +106,16 @@ enum { ATM_SWEEP_AUTO = 0, ATM_SWEEP_SPLIT = 1, ATM_SWEEP_FUSED = 2, ATM_SWEEP_C
 #define ATM_MAX_LEVELS 8
 
 typedef struct {
-    int kind;          /* ATM_HEAT1D | ATM_HEAT2D | ATM_ALLEN_CAHN */
-    int nx, ny;        /* grid; ny ignored for heat1d.  2D: nx, ny multiples of 32 */
+    int kind;          /* ATM_HEAT1D | ATM_HEAT2D | ATM_ALLEN_CAHN | ATM_GRAY_SCOTT */
+    int nx, ny;        /* grid; ny ignored for heat1d.  2D: nx, ny powers of two in [32, 512] (FP32: 1024); Gray-Scott: 8..512 */
     double lx, ly;     /* domain lengths */
     double dt;         /* fine time step */
     int nt_points;     /* number of time points including t_0 (>= 2) */
     double eps;        /* Allen-Cahn interface parameter */
+    double gs_du, gs_dv;      /* Gray-Scott diffusion rates (>= 0) */
+    double gs_feed, gs_kill;  /* Gray-Scott F and K (>= 0) */
+    double newton_tol;        /* Gray-Scott Newton tolerance (<= 0: 1e-10) */
+    int newton_max_iter;      /* Gray-Scott Newton iterations per step (<= 0: 50; at most 500) */
 } atm_problem;
 
 typedef struct {
@@ -269,13 +287,22 @@ atm_status atm_get_kernel_profile(const atm_handle *h, int which, double *total_
 /* Kernels of level `level`'s propagator as chosen at atm_create (the
  * autotuner's pick on level 0 with ATM_SWEEP_AUTO).  Writes 5 ints:
  *   cfg[0] kernel: 0 split row + column kernels, 1 fused cluster kernel,
- *          2 learned network, 3 1D line kernel, 4 chain kernel (F-relaxations);
+ *          2 learned network, 3 1D line kernel, 4 chain kernel (F-relaxations),
+ *          5 Gray-Scott Newton kernel (cfg[1] CTAs resident at most, cfg[2]
+ *          threads per CTA, cfg[3] GMRES restart length);
  *   cfg[1] CTAs per state (fused: cluster size; split: column-kernel CTAs);
  *   cfg[2] threads per CTA (fused) or per column-kernel CTA (split);
  *   cfg[3] rows per column segment (fused) or per column-kernel thread (split);
  *   cfg[4] level 0, split: states per row/column launch pair (0 = all).
  * The refined mode reports its FP32 inner cycle. */
 atm_status atm_get_sweep_config(const atm_handle *h, int level, int *cfg);
+
+/* Gray-Scott (ATM_GRAY_SCOTT): counters of the nonlinear solves since
+ * atm_create, 4 values: out[0] Newton iterations, out[1] GMRES iterations,
+ * out[2] steps that stopped at newton_max_iter without meeting the tolerance,
+ * out[3] steps (propagator applications).  Synchronises the handle's stream.
+ * Errors: ATM_ERR_UNSUPPORTED for the other problem families. */
+atm_status atm_get_newton_stats(atm_handle *h, long long *out);
 
 /* Solve several independent problems with one CUDA graph launch on
  * `cuda_stream`: the graph holds, for every handle, its first relaxation pass

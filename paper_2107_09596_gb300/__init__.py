@@ -15,7 +15,7 @@ import numpy as np
 
 from . import build as _build
 
-HEAT1D, HEAT2D, ALLEN_CAHN = 0, 1, 2
+HEAT1D, HEAT2D, ALLEN_CAHN, GRAY_SCOTT = 0, 1, 2, 3
 PROP_SPLIT_BE, PROP_PR_ADI, PROP_LEARNED, PROP_LEARNED_CORRECTION = 0, 1, 2, 3
 REACT_EXACT, REACT_SUBSTEPS = 0, 1
 SEQUENTIAL, MGRIT, AT_MGRIT = 0, 1, 2
@@ -39,7 +39,10 @@ class AtmError(RuntimeError):
 class Problem(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
                 ("lx", ctypes.c_double), ("ly", ctypes.c_double), ("dt", ctypes.c_double),
-                ("nt_points", ctypes.c_int), ("eps", ctypes.c_double)]
+                ("nt_points", ctypes.c_int), ("eps", ctypes.c_double),
+                ("gs_du", ctypes.c_double), ("gs_dv", ctypes.c_double),
+                ("gs_feed", ctypes.c_double), ("gs_kill", ctypes.c_double),
+                ("newton_tol", ctypes.c_double), ("newton_max_iter", ctypes.c_int)]
 
 
 class SolverDesc(ctypes.Structure):
@@ -82,7 +85,7 @@ EXPORTS = ["atm_workspace_size", "atm_create", "atm_set_initial_condition",
            "atm_last_launch_count", "atm_get_kernel_profile", "atm_apply_propagator_noalloc",
            "atm_nn_param_count", "atm_nn_workspace_size", "atm_nn_apply", "atm_nn_loss_grad",
            "atm_train_learned_coarse", "atm_set_learned_coarse", "atm_batch_solve", "atm_last_error",
-           "atm_get_sweep_config", "atm_set_rhs", "atm_destroy"]
+           "atm_get_sweep_config", "atm_set_rhs", "atm_get_newton_stats", "atm_destroy"]
 
 _lib = None
 
@@ -121,6 +124,7 @@ def load(build_if_missing: bool = True):
     L.atm_last_launch_count.restype = ctypes.c_longlong
     L.atm_get_kernel_profile.argtypes = [vp, i, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_longlong)]
     L.atm_get_sweep_config.argtypes = [vp, i, ctypes.POINTER(i)]
+    L.atm_get_newton_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
     L.atm_apply_propagator_noalloc.argtypes = [ctypes.POINTER(Problem), ctypes.POINTER(SolverDesc), i, vp, vp, i, vp]
     L.atm_nn_param_count.restype = i
     L.atm_nn_workspace_size.argtypes = [i, i, i, i, ctypes.POINTER(ctypes.c_size_t)]
@@ -146,10 +150,16 @@ def _check(st: int, ok=(0,)):
     return st
 
 
-def make_problem(kind, nx, ny=1, lx=1.0, ly=1.0, dt=1e-3, nt_points=65, eps=0.02) -> Problem:
+def make_problem(kind, nx, ny=1, lx=1.0, ly=1.0, dt=1e-3, nt_points=65, eps=0.02,
+                 du=8e-5, dv=4e-5, feed=0.024, kill=0.06, newton_tol=1e-10,
+                 newton_max_iter=50) -> Problem:
+    """Problem description; du, dv, feed, kill and the Newton settings are
+    the Gray-Scott parameters (defaults: the values of the paper's Sec. 5.1)."""
     p = Problem()
     p.kind, p.nx, p.ny = kind, nx, ny
     p.lx, p.ly, p.dt, p.nt_points, p.eps = lx, ly, dt, nt_points, eps
+    p.gs_du, p.gs_dv, p.gs_feed, p.gs_kill = du, dv, feed, kill
+    p.newton_tol, p.newton_max_iter = newton_tol, newton_max_iter
     return p
 
 
@@ -216,7 +226,10 @@ class Solver:
         _check(load().atm_create(ctypes.byref(problem), ctypes.byref(solver), ctypes.c_void_p(aligned),
                                  nbytes, ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(self.handle)))
         self._leave()
-        self.state_shape = (problem.nx,) if problem.kind == HEAT1D else (problem.ny, problem.nx)
+        if problem.kind == GRAY_SCOTT:
+            self.state_shape = (2, problem.ny, problem.nx)
+        else:
+            self.state_shape = (problem.nx,) if problem.kind == HEAT1D else (problem.ny, problem.nx)
 
     def _enter(self):
         self.stream.wait_stream(self.torch.cuda.current_stream(self.device))
@@ -333,8 +346,14 @@ class Solver:
         """Kernels of a level's propagator: dict(kernel, ctas, threads, rows, chunk)."""
         cfg = (ctypes.c_int * 5)()
         _check(load().atm_get_sweep_config(self.handle, level, cfg))
-        names = {0: "split", 1: "fused", 2: "learned", 3: "line1d", 4: "chain"}
+        names = {0: "split", 1: "fused", 2: "learned", 3: "line1d", 4: "chain", 5: "newton"}
         return dict(kernel=names.get(cfg[0], str(cfg[0])), ctas=cfg[1], threads=cfg[2], rows=cfg[3], chunk=cfg[4])
+
+    def newton_stats(self):
+        """Gray-Scott: dict(newton, gmres, failures, steps) summed since creation."""
+        out = (ctypes.c_longlong * 4)()
+        _check(load().atm_get_newton_stats(self.handle, out))
+        return dict(newton=out[0], gmres=out[1], failures=out[2], steps=out[3])
 
     def set_learned_coarse(self, params):
         """Network weights (torch float32 device tensor) for coarse_prop = PROP_LEARNED or

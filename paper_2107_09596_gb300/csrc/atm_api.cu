@@ -134,7 +134,10 @@ atm_status atm_set_initial_guess(atm_handle *h, const double *u)
     if (!h) return atm::fail(ATM_ERR_INVALID_ARG, "null handle");
     if (!u) return h->p->zero_guess();
     const int n = h->p->level_points(0);
-    const size_t nsp = h->p->pb.kind == ATM_HEAT1D ? (size_t)h->p->pb.nx : (size_t)h->p->pb.nx * h->p->pb.ny;
+    const atm_problem &pb = h->p->pb;
+    const size_t nsp = pb.kind == ATM_HEAT1D     ? (size_t)pb.nx
+                       : pb.kind == ATM_GRAY_SCOTT ? 2 * (size_t)pb.nx * pb.ny
+                                                   : (size_t)pb.nx * pb.ny;
     return h->p->set_state(1, n - 1, u + nsp);
 }
 
@@ -213,6 +216,12 @@ atm_status atm_get_sweep_config(const atm_handle *h, int level, int *cfg)
 {
     if (!h || !cfg) return atm::fail(ATM_ERR_INVALID_ARG, "invalid argument");
     return h->p->sweep_config(level, cfg);
+}
+
+atm_status atm_get_newton_stats(atm_handle *h, long long *out)
+{
+    if (!h || !out) return atm::fail(ATM_ERR_INVALID_ARG, "invalid argument");
+    return h->p->newton_stats(out);
 }
 
 atm_status atm_set_learned_coarse(atm_handle *h, const float *d_params)

@@ -16,6 +16,7 @@
 #include "../../include/atm.h"
 #include "atm_common.cuh"
 #include "atm_kernels.cuh"
+#include "atm_gs.cuh"
 #include "atm_fused.h"
 #include "atm_nn.h"
 
@@ -321,6 +322,7 @@ struct PlanBase {
     virtual atm_status add_loop(cudaGraph_t g) = 0;
     virtual atm_status loop_result(atm_result *res) = 0;
     virtual atm_status sweep_config(int level, int *cfg) const = 0;
+    virtual atm_status newton_stats(long long *) { return fail(ATM_ERR_UNSUPPORTED, "not a Gray-Scott handle"); }
 };
 
 template <typename T>
@@ -339,6 +341,8 @@ struct Level {
     int fz = -1;                 // selected fused shape (-1: split row/column kernels)
     std::vector<FusedVariant<T>> chains;  // chain-kernel shapes
     int chz = -1;                // selected chain shape (-1: F-relaxation step by step)
+    bool gs = false;             // Gray-Scott: the Newton kernel applies the propagator
+    GsArgs gsa{};
 };
 
 inline bool pow2_in(int v, int lo, int hi)
@@ -358,6 +362,11 @@ struct Plan : PlanBase {
     int L = 1;
     int nsp = 0;
     bool is1d = false;
+    bool isgs = false;      // Gray-Scott: two fields per state, Newton kernel on every level
+    double *gs_scratch = nullptr;            // per-CTA slices of the Newton kernel
+    int gs_ctas = 0;                         // CTAs of a Newton launch at most
+    size_t gs_stride = 0;                    // doubles per slice
+    unsigned long long *gs_stats = nullptr;  // Newton / GMRES iterations, failures, steps
     int maxbatch = 16;
     int midcap = 16;        // states in the row-sweep intermediate (launches are chunked to it)
     // workspace layout
@@ -465,11 +474,23 @@ struct Plan : PlanBase {
     // ---------------- validation and layout ----------------
     atm_status validate() const
     {
-        if (pb.kind < ATM_HEAT1D || pb.kind > ATM_ALLEN_CAHN) return fail(ATM_ERR_INVALID_ARG, "unknown problem kind %d", pb.kind);
+        if (pb.kind < ATM_HEAT1D || pb.kind > ATM_GRAY_SCOTT) return fail(ATM_ERR_INVALID_ARG, "unknown problem kind %d", pb.kind);
         if (pb.nt_points < 2) return fail(ATM_ERR_INVALID_ARG, "nt_points must be >= 2");
         if (!(pb.dt > 0) || !(pb.lx > 0) || (!is1d && !(pb.ly > 0))) return fail(ATM_ERR_INVALID_ARG, "dt, lx, ly must be > 0");
         if (pb.kind == ATM_ALLEN_CAHN && !(pb.eps > 0)) return fail(ATM_ERR_INVALID_ARG, "eps must be > 0");
-        if (is1d) {
+        if (isgs) {
+            if (sizeof(T) != sizeof(double) || role != ROLE_NORMAL)
+                return fail(ATM_ERR_UNSUPPORTED, "Gray-Scott runs in FP64 only");
+            if (pb.nx < 8 || pb.nx > 512 || pb.ny < 8 || pb.ny > 512)
+                return fail(ATM_ERR_INVALID_ARG, "Gray-Scott needs 8 <= nx, ny <= 512");
+            if (!(pb.gs_du >= 0) || !(pb.gs_dv >= 0) || !(pb.gs_feed >= 0) || !(pb.gs_kill >= 0))
+                return fail(ATM_ERR_INVALID_ARG, "Gray-Scott rates must be >= 0");
+            if (pb.newton_max_iter > 500) return fail(ATM_ERR_INVALID_ARG, "newton_max_iter must be <= 500");
+            if (sv.sweep_kernel != ATM_SWEEP_AUTO && sv.sweep_kernel != ATM_SWEEP_SPLIT)
+                return fail(ATM_ERR_UNSUPPORTED, "Gray-Scott has no fused or chain kernels");
+            if (sv.coarse_prop == ATM_PROP_LEARNED || sv.coarse_prop == ATM_PROP_LEARNED_CORRECTION)
+                return fail(ATM_ERR_UNSUPPORTED, "no learned propagator for Gray-Scott");
+        } else if (is1d) {
             if (pb.nx < 2 || pb.nx > 2048) return fail(ATM_ERR_INVALID_ARG, "heat1d needs 2 <= nx <= 2048");
         } else {
             const int nmax = sizeof(T) == 4 ? 1024 : 512;
@@ -493,7 +514,7 @@ struct Plan : PlanBase {
             if (sv.reaction_substeps[l] < 0) return fail(ATM_ERR_INVALID_ARG, "reaction_substeps must be >= 0");
         if (sv.coarse_reaction != ATM_REACT_EXACT && sv.coarse_reaction != ATM_REACT_SUBSTEPS)
             return fail(ATM_ERR_INVALID_ARG, "unknown coarse_reaction %d", sv.coarse_reaction);
-        if (!is1d) {
+        if (!is1d && !isgs) {
             if (sv.fine_prop < 0 || sv.fine_prop > 1 || sv.coarse_prop < 0 || sv.coarse_prop > 3)
                 return fail(ATM_ERR_INVALID_ARG, "unknown propagator");
         }
@@ -511,9 +532,59 @@ struct Plan : PlanBase {
         return ATM_OK;
     }
 
+    // Newton-kernel arguments of level l (Gray-Scott): step D, diffusion
+    // numbers and the factorised periodic line operators of each species.
+    void setup_gs_level(int l)
+    {
+        Level<T> &Lv = lv[l];
+        Lv.gs = true;
+        Lv.fz = -1;
+        Lv.chz = -1;
+        GsArgs &g = Lv.gsa;
+        std::memset(&g, 0, sizeof(g));
+        double D = pb.dt;
+        for (int j = 0; j < l; ++j) D *= (double)sv.m[j];
+        const double dx = pb.lx / pb.nx, dy = pb.ly / pb.ny;
+        const double rate[2] = {pb.gs_du, pb.gs_dv};
+        g.nx = pb.nx;
+        g.ny = pb.ny;
+        g.D = D;
+        g.feed = pb.gs_feed;
+        g.kill = pb.gs_kill;
+        for (int s = 0; s < 2; ++s) {
+            g.ex[s] = D * rate[s] / (dx * dx);
+            g.ey[s] = D * rate[s] / (dy * dy);
+            const double av[2] = {g.ex[s], g.ey[s]};
+            const int nn[2] = {pb.nx, pb.ny};
+            for (int ax = 0; ax < 2; ++ax) {
+                const double a = av[ax];
+                // tridiag(-a, 1 + 2a, -a) = kappa (1 - rho S)(1 - rho S^-1)
+                const double rho = 2.0 * a / (1.0 + 2.0 * a + std::sqrt(1.0 + 4.0 * a));
+                const double kappa = (1.0 + 2.0 * a) / (1.0 + rho * rho);
+                GsLine c;
+                c.rho = rho;
+                c.kinv = 1.0 / kappa;
+                c.closure = 1.0 / (1.0 - std::pow(rho, (double)nn[ax]));
+                if (ax == 0) g.lx[s] = c; else g.ly[s] = c;
+            }
+        }
+        g.tol = pb.newton_tol > 0 ? pb.newton_tol : 1e-10;
+        g.max_newton = pb.newton_max_iter > 0 ? pb.newton_max_iter : 50;
+        g.restart = 20;
+        g.max_inner = 200;
+        g.eta = 1e-7;
+        g.scratch = gs_scratch;
+        g.cta_stride = gs_stride;
+        g.stats = gs_stats;
+    }
+
     void setup_level_op(int l)
     {
         Level<T> &Lv = lv[l];
+        if (isgs) {
+            setup_gs_level(l);
+            return;
+        }
         LevelOp<T> op = make_level_op<T>(pb, sv, l, Lv.dir_w);
         if (op.learned) {
             atm_solver cs = sv;
@@ -541,7 +612,7 @@ struct Plan : PlanBase {
     // ---------------- phase builders ----------------
     int blocks_per_job(int l) const
     {
-        if (is1d) return 1;
+        if (is1d || isgs) return 1;
         if (l < (int)lv.size() && lv[l].learned) return pb.nx * pb.ny / nn::kNNTile;
         if (l < (int)lv.size() && lv[l].fz >= 0) return lv[l].fused[lv[l].fz].G;
         return pb.nx / 32;
@@ -552,7 +623,7 @@ struct Plan : PlanBase {
     int max_blocks_per_job(int l) const
     {
         int b = blocks_per_job(l);
-        if (is1d || (l < (int)lv.size() && lv[l].learned)) return b;
+        if (is1d || isgs || (l < (int)lv.size() && lv[l].learned)) return b;
         if (b < pb.nx / 32) b = pb.nx / 32;
         if (l < (int)lv.size())
             for (const FusedVariant<T> &f : lv[l].fused)
@@ -1000,7 +1071,8 @@ struct Plan : PlanBase {
         base = ws;
         off = 0;
         is1d = (pb.kind == ATM_HEAT1D);
-        nsp = is1d ? pb.nx : pb.nx * pb.ny;
+        isgs = (pb.kind == ATM_GRAY_SCOTT);
+        nsp = is1d ? pb.nx : isgs ? 2 * pb.nx * pb.ny : pb.nx * pb.ny;
         ATM_TRY(validate());
         L = (sv.algorithm == ATM_SEQUENTIAL || role == ROLE_OUTER) ? 1 : sv.levels;
         lv.assign(L, Level<T>());
@@ -1045,7 +1117,21 @@ struct Plan : PlanBase {
             if ((size_t)midcap > cap) midcap = cap < 16 ? 16 : (int)cap;
             if (midcap > 32768) midcap = 32768;   // grid y limit of a launch
         }
-        if (!is1d) mid = take<T>((size_t)midcap * nsp);
+        if (!is1d && !isgs) mid = take<T>((size_t)midcap * nsp);
+        if (isgs) {
+            // two Newton CTAs per SM, at most 8 GiB of slices
+            int sms = 0;
+            if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0) != cudaSuccess || sms <= 0) {
+                cudaGetLastError();
+                sms = 152;
+            }
+            gs_stride = gs_cta_doubles(pb.nx, pb.ny, 20);
+            gs_ctas = 2 * sms;
+            const size_t cap = ((size_t)8 << 30) / (gs_stride * sizeof(double));
+            if ((size_t)gs_ctas > cap) gs_ctas = cap < 1 ? 1 : (int)cap;
+            gs_scratch = take<double>((size_t)gs_ctas * gs_stride);
+            gs_stats = take<unsigned long long>(4);
+        }
         if (sizeof(T) != sizeof(double)) {
             sin = take<T>((size_t)midcap * nsp);
             sout = take<T>((size_t)midcap * nsp);
@@ -1070,7 +1156,7 @@ struct Plan : PlanBase {
         for (int l = 0; l < L; ++l) {
             if (is1d) lv[l].dir_w = take<T>((size_t)pb.nx);
             setup_level_op(l);
-            if (!lv[l].learned && (!lv[l].row || (!is1d && !lv[l].col)))
+            if (!lv[l].learned && !lv[l].gs && (!lv[l].row || (!is1d && !lv[l].col)))
                 return fail(ATM_ERR_UNSUPPORTED, "no kernel instantiation for this grid size and precision");
         }
         build_phases();
@@ -1108,7 +1194,7 @@ struct Plan : PlanBase {
         long long n = 0;
         for (const LaunchRec &r : ph) {
             if (r.type == L_CHAIN) n += (r.njobs + 32767) / 32768;
-            else if (r.type != L_SWEEP || is1d) n += 1;
+            else if (r.type != L_SWEEP || is1d || isgs) n += 1;
             else if (lv[r.level].learned || lv[r.level].fz >= 0) {
                 n += sweep_pairs(r.level, r.njobs);
                 if (lv[r.level].learned && hybrid) n += 2 * ((r.njobs + midcap - 1) / midcap);
@@ -1193,6 +1279,23 @@ struct Plan : PlanBase {
                 launch_failed = true;
             return;
         }
+        if (Lv.gs) {
+            if constexpr (sizeof(T) == sizeof(double)) {
+                const bool prof = !no_events && slot >= 0 && slot < nprof;
+                if (prof) cudaEventRecordWithFlags(pev[4 * slot], st, cudaEventRecordExternal);
+                GsArgs g = Lv.gsa;
+                g.jobs = djobs;
+                g.njobs = njobs;
+                g.neg = neg;
+                g.partials = part;
+                const int grid = njobs < gs_ctas ? njobs : gs_ctas;
+                if (grid > 0) gs_newton_kernel<kGsThreads><<<grid, kGsThreads, 0, st>>>(g);
+                if (prof) cudaEventRecordWithFlags(pev[4 * slot + 3], st, cudaEventRecordExternal);
+            } else {
+                launch_failed = true;
+            }
+            return;
+        }
         SweepArgs<T> a = Lv.args;
         a.neg = neg;
         a.mid = mid;
@@ -1252,7 +1355,7 @@ struct Plan : PlanBase {
     // Number of row/column launch pairs of a sweep of njobs states on level l.
     int sweep_pairs(int l, int njobs) const
     {
-        if (is1d) return 1;
+        if (is1d || isgs) return 1;
         if (lv[l].learned) {
             const int ch = maxbatch < nn::kInferChunk ? maxbatch : nn::kInferChunk;
             return 5 * ((njobs + ch - 1) / ch);   // counted as kernels / 2 by kernels_in
@@ -1300,7 +1403,7 @@ struct Plan : PlanBase {
                 if (r.njobs > maxjobs) maxjobs = r.njobs;
             }
         chunk = 0;
-        if (is1d || recs.empty() || lv[0].learned) return ATM_OK;
+        if (is1d || isgs || recs.empty() || lv[0].learned) return ATM_OK;
         struct Cand { int fz, chunk; };
         std::vector<Cand> cands;
         const bool tune_fz = sv.sweep_kernel == ATM_SWEEP_AUTO && !lv[0].fused.empty();
@@ -1373,7 +1476,7 @@ struct Plan : PlanBase {
     // most CTAs per state often wins there.
     atm_status autotune_coarse(const Phase &ph)
     {
-        if (is1d || sv.sweep_kernel != ATM_SWEEP_AUTO) return ATM_OK;
+        if (is1d || isgs || sv.sweep_kernel != ATM_SWEEP_AUTO) return ATM_OK;
         cudaEvent_t e0, e1;
         ATM_CK(cudaEventCreate(&e0));
         ATM_CK(cudaEventCreate(&e1));
@@ -1579,6 +1682,7 @@ struct Plan : PlanBase {
             ATM_CK(cudaMemsetAsync(ubase, 0, n0, st));
             if (bwork) ATM_CK(cudaMemsetAsync(bwork, 0, n0, st));
         }
+        if (gs_stats) ATM_CK(cudaMemsetAsync(gs_stats, 0, 4 * sizeof(unsigned long long), st));
         ATM_CK(cudaEventCreate(&ev0));
         ATM_CK(cudaEventCreate(&ev1));
         pev.assign(4 * (size_t)nprof, nullptr);
@@ -2067,12 +2171,24 @@ struct Plan : PlanBase {
 
     int level_points(int level) const override { return (level >= 0 && level < L) ? lv[level].N : -1; }
 
+    atm_status newton_stats(long long *out) override
+    {
+        if (!gs_stats) return fail(ATM_ERR_UNSUPPORTED, "not a Gray-Scott handle");
+        unsigned long long h[4] = {0, 0, 0, 0};
+        ATM_CK(cudaMemcpyAsync(h, gs_stats, sizeof(h), cudaMemcpyDeviceToHost, st));
+        ATM_CK(cudaStreamSynchronize(st));
+        for (int i = 0; i < 4; ++i) out[i] = (long long)h[i];
+        return ATM_OK;
+    }
+
     atm_status sweep_config(int level, int *cfg) const override
     {
         if (level < 0 || level >= L) return fail(ATM_ERR_INVALID_ARG, "level %d out of range", level);
         const Level<T> &Lv = lv[level];
         for (int i = 0; i < 5; ++i) cfg[i] = 0;
-        if (is1d) {
+        if (Lv.gs) {
+            cfg[0] = 5; cfg[1] = gs_ctas; cfg[2] = kGsThreads; cfg[3] = Lv.gsa.restart;
+        } else if (is1d) {
             cfg[0] = 3; cfg[1] = 1; cfg[2] = 32;
         } else if (Lv.learned) {
             cfg[0] = 2;
