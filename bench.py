@@ -223,6 +223,141 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
+# Gray-Scott of Sec. 5.1: 128^2 on the periodic [0, 2.5]^2, 16384 points on
+# [0, 256], backward Euler with Newton (tolerance 1e-10), stop at the space-time
+# residual 1e-7, nested iteration; the paper's two-level (m = 64, k = 128,
+# F-relaxation; Table 1) and three-level ((64, 4), k = 32, FCF; Table 2) forms.
+GS_WORKLOAD = dict(n=128, nt=16384, dt=256.0 / 16383.0, lx=2.5, tol=1e-7, max_iter=30,
+                   newton_tol=1e-10, du=8e-5, dv=4e-5, feed=0.024, kill=0.06)
+GS_CONFIGS = {"2lvl": dict(m=(64,), k=128, nu=0), "3lvl": dict(m=(64, 4), k=32, nu=1)}
+GS_METRIC = "Gray-Scott time-to-solution at space-time residual 1e-7 and fine steps/s"
+
+
+def gs_vector_passes(st):
+    """Reads and writes of whole 2 n^2 state vectors done by the Newton kernel
+    as written, from its counters (per step 7, per Newton iteration -1, per
+    line-search trial 6, per GMRES cycle 27, per GMRES iteration 22, per basis
+    vector orthogonalised against 4)."""
+    return (7 * st["steps"] - st["newton"] + 6 * st["trials"] + 27 * st["cycles"]
+            + 22 * st["gmres"] + 4 * st["basis"])
+
+
+def run_gray_scott(args):
+    import torch
+    import paper_2107_09596_gb300 as atm
+    w = dict(GS_WORKLOAD, **GS_CONFIGS[args.gs_config])
+    if args.max_iter is not None:
+        w["max_iter"] = args.max_iter
+    device = torch.device("cuda", 0)
+    torch.cuda.set_device(device)
+    atm._build.build()
+    n = w["n"]
+    prob = atm.make_problem(atm.GRAY_SCOTT, n, n, lx=w["lx"], ly=w["lx"], dt=w["dt"], nt_points=w["nt"],
+                            du=w["du"], dv=w["dv"], feed=w["feed"], kill=w["kill"],
+                            newton_tol=w["newton_tol"], newton_max_iter=50)
+    alg = {"at": atm.AT_MGRIT, "mgrit": atm.MGRIT, "seq": atm.SEQUENTIAL}[args.algorithm]
+    nested = not args.cold and args.algorithm != "seq"
+    desc = atm.make_solver(alg, m=w["m"], k=w["k"], nu=w["nu"], tol=w["tol"], max_iter=w["max_iter"],
+                           precision=atm.FP64, use_graph=2 if args.algorithm != "seq" else True,
+                           cpoint_only=args.storage == "cpoint", nested=nested)
+    solver = atm.Solver(prob, desc, device=device)
+    u0 = torch.as_tensor(I.gray_scott_initial_condition(n, n), dtype=torch.float64, device=device)
+
+    def step():
+        solver.set_initial_guess(None)
+        solver.set_initial_condition(u0)
+        return solver.solve()
+
+    for _ in range(args.warmup):
+        res = step()
+    torch.cuda.synchronize(device)
+    st0 = solver.newton_stats()
+    clocks = ClockSampler(0)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    launches, iters = 0, []
+    e0.record(solver.stream)
+    for _ in range(args.steps):
+        res = step()
+        launches += res["launches"]
+        iters.append(res["iterations"])
+    e1.record(solver.stream)
+    torch.cuda.synchronize(device)
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    st1 = solver.newton_stats()
+    d = {k: (st1[k] - st0[k]) / args.steps for k in st1}
+    value = (w["nt"] - 1) / (ms / 1e3)
+    hist = solver.residual_history()
+
+    # end to end: the initial state from pinned host memory, the final state and
+    # the residual history back, inside the timed region
+    shape = solver.state_shape
+    h_u0 = torch.as_tensor(I.gray_scott_initial_condition(n, n), dtype=torch.float64).pin_memory()
+    h_out = torch.empty(shape, dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize(device)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        solver.set_initial_guess(None)
+        solver.set_initial_condition(h_u0)
+        solver.solve()
+        solver.solution(w["nt"] - 1, 1, out=h_out)
+        h2 = solver.residual_history()
+    torch.cuda.synchronize(device)
+    e2e_ms = (time.perf_counter() - t) * 1e3 / args.steps
+    state_bytes = int(np.prod(shape)) * 8
+
+    # roofline of the Newton kernel: whole-vector passes (from its counters)
+    # over the timed region, against the measured HBM copy rate
+    pk = peaks()
+    passes = gs_vector_passes(d)
+    nbytes = passes * state_bytes
+    achieved = nbytes / (ms / 1e3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / pk["hbm_gbs"], "traffic": None,
+            "kernel": "gs_newton_kernel (every propagator application of the solve)",
+            "peak_source": f"{pk['hbm_src']} STREAM copy (MEASURED_PEAKS.json)",
+            "algorithmic": f"{passes:.0f} passes over a {state_bytes} B state per solve (Newton kernel as "
+                           f"written: counters x passes per event) / timed solve time (includes the "
+                           f"few non-Newton kernels: a lower bound of the kernel's own rate)"}
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+        c = oracle.make_cfg(oracle.GRAY_SCOTT, n, n, lx=w["lx"], ly=w["lx"], dt=w["dt"], nt=3, m=(2,),
+                            gs=dict(du=w["du"], dv=w["dv"], feed=w["feed"], kill=w["kill"],
+                                    tol=w["newton_tol"], max_iter=50))
+        x = I.gray_scott_initial_condition(n, n)[None]
+        steps_cpu = 6
+        t = time.perf_counter()
+        for _ in range(steps_cpu):
+            x = oracle.apply_prop(c, 0, x)
+        sec = time.perf_counter() - t
+        cpu = {"value": steps_cpu / sec, "unit": "fine steps/s", "cores": 1, "kind": "oracle",
+               "sample": f"{steps_cpu} sequential backward Euler Newton steps of the oracle from the "
+                         f"initial state ({sec:.1f} s; sparse LU per Newton iteration): its sequential "
+                         f"stepping rate, the fastest the oracle covers the time axis"}
+    line = {"metric": GS_METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (the paper's initial state)",
+            "config": {"workload": "gray_scott_128", "gs_config": args.gs_config,
+                       **{k: (list(v) if isinstance(v, tuple) else v) for k, v in w.items()},
+                       "algorithm": args.algorithm, "storage": args.storage, "nested": nested,
+                       "l2": "working set larger than L2 (Newton scratch %.2f GB)" % (
+                           atm.workspace_size(prob, desc) / 1e9)},
+            "iterations": int(np.median(iters)), "time_to_solution_ms": ms,
+            "final_residual": float(res["final_residual"]),
+            "residual_history": [float(v) for v in hist][:64],
+            "newton_per_solve": d,
+            "e2e": {"value": (w["nt"] - 1) / (e2e_ms / 1e3), "unit": UNIT,
+                    "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes + 8 * len(h2)},
+            "gpu_launches": int(launches),
+            "kernels_per_level": [solver.sweep_config(0)],
+            "roofline": roof, "cpu_baseline": cpu, "clocks": clk}
+    print(json.dumps(line), flush=True)
+    solver.close()
+
+
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -389,8 +524,13 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["atm", "reference"], default="atm")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch64"], default="allen_cahn_256",
-                    help="batch64: 64 drawn problems, batched against one at a time (not the default)")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch64", "gray_scott_128"],
+                    default="allen_cahn_256",
+                    help="batch64: 64 drawn problems, batched against one at a time; gray_scott_128: the "
+                         "Gray-Scott problem of Sec. 5.1 (neither is the default)")
+    ap.add_argument("--gs-config", choices=sorted(GS_CONFIGS), default="2lvl",
+                    help="gray_scott_128: 2lvl (m = 64, k = 128, F) or 3lvl ((64, 4), k = 32, FCF)")
+    ap.add_argument("--cold", action="store_true", help="gray_scott_128: zero guess instead of nested iteration")
     ap.add_argument("--algorithm", choices=["at", "mgrit", "seq"], default="at")
     ap.add_argument("--precision", choices=["fp64", "fp32", "fp32r"], default="fp32r",
                     help="fp32r: FP32 propagation with FP64 refinement (the fastest form that reaches 1e-8)")
@@ -413,6 +553,13 @@ def main():
     args = ap.parse_args()
     if args.workload == "batch64":
         run_batch(args)
+        return
+    if args.workload == "gray_scott_128":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "gray_scott_128 has no reference arm; "
+                              "its CPU baseline is the oracle's stepping rate in the atm line"}))
+            return
+        run_gray_scott(args)
         return
     w = dict(WORKLOADS[args.workload])
     if args.max_iter is not None:

@@ -298,9 +298,11 @@ atm_status atm_get_kernel_profile(const atm_handle *h, int which, double *total_
 atm_status atm_get_sweep_config(const atm_handle *h, int level, int *cfg);
 
 /* Gray-Scott (ATM_GRAY_SCOTT): counters of the nonlinear solves since
- * atm_create, 4 values: out[0] Newton iterations, out[1] GMRES iterations,
+ * atm_create, 8 values: out[0] Newton iterations, out[1] GMRES iterations,
  * out[2] steps that stopped at newton_max_iter without meeting the tolerance,
- * out[3] steps (propagator applications).  Synchronises the handle's stream.
+ * out[3] steps (propagator applications), out[4] sum over GMRES iterations of
+ * the basis vectors orthogonalised against, out[5] line-search trials,
+ * out[6] GMRES restart cycles, out[7] 0.  Synchronises the handle's stream.
  * Errors: ATM_ERR_UNSUPPORTED for the other problem families. */
 atm_status atm_get_newton_stats(atm_handle *h, long long *out);
 

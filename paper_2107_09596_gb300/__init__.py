@@ -350,10 +350,12 @@ class Solver:
         return dict(kernel=names.get(cfg[0], str(cfg[0])), ctas=cfg[1], threads=cfg[2], rows=cfg[3], chunk=cfg[4])
 
     def newton_stats(self):
-        """Gray-Scott: dict(newton, gmres, failures, steps) summed since creation."""
-        out = (ctypes.c_longlong * 4)()
+        """Gray-Scott counters summed since creation: Newton and GMRES iterations,
+        failures, steps, orthogonalisations (basis), line-search trials, GMRES cycles."""
+        out = (ctypes.c_longlong * 8)()
         _check(load().atm_get_newton_stats(self.handle, out))
-        return dict(newton=out[0], gmres=out[1], failures=out[2], steps=out[3])
+        return dict(newton=out[0], gmres=out[1], failures=out[2], steps=out[3], basis=out[4],
+                    trials=out[5], cycles=out[6])
 
     def set_learned_coarse(self, params):
         """Network weights (torch float32 device tensor) for coarse_prop = PROP_LEARNED or

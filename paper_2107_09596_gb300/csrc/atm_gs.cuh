@@ -54,8 +54,14 @@ struct GsArgs {
     double *scratch;          // per-CTA slices of cta_stride doubles
     size_t cta_stride;
     double *partials;         // per job: sum of r^2 (null: none)
-    unsigned long long *stats;   // Newton iterations, GMRES iterations, failures, steps
+    unsigned long long *stats;   // kGsStats counters (see gs_newton_kernel)
 };
+
+// Counters of the Newton kernel: Newton iterations, GMRES iterations, steps
+// that missed the tolerance, steps, sum over GMRES iterations of the basis
+// vectors orthogonalised against (j + 1), line-search trials, GMRES restart
+// cycles, unused.
+constexpr int kGsStats = 8;
 
 // Doubles of one CTA's scratch slice: W, G, d, Z and restart + 1 Krylov vectors.
 inline size_t gs_cta_doubles(int nx, int ny, int restart)
@@ -198,7 +204,7 @@ struct GsSmem {
 // relative residual eta (||G||_2 = beta0) or max_inner iterations.
 // Returns the iterations taken.
 __device__ __forceinline__ int gs_gmres(const GsArgs &a, const double *W, const double *G, double beta0, double *d,
-                        double *Z, double *V, GsSmem &sm)
+                        double *Z, double *V, GsSmem &sm, unsigned long long &basis, unsigned long long &cycles)
 {
     const int n2 = 2 * a.nx * a.ny, kr = a.restart;
     const double target = a.eta * beta0;
@@ -228,6 +234,7 @@ __device__ __forceinline__ int gs_gmres(const GsArgs &a, const double *W, const 
             for (int p = threadIdx.x; p < n2; p += blockDim.x) V[p] *= ib;
         }
         first = false;
+        ++cycles;
         if (threadIdx.x == 0) sm.gg[0] = beta;
         __syncthreads();
         int j = 0;
@@ -291,6 +298,7 @@ __device__ __forceinline__ int gs_gmres(const GsArgs &a, const double *W, const 
             res = sm.sh[34];
             ++j;
             ++total;
+            basis += (unsigned long long)j;
             if (res <= target || total >= a.max_inner || !(hn > 0.0)) {
                 done = true;
                 break;
@@ -338,14 +346,16 @@ __global__ void __launch_bounds__(NT) gs_newton_kernel(GsArgs a)
         double f = sqrt(gs_residual(a, W, win, G, sm.sh));
         const double stop = fmax(a.tol, a.tol * f);
         int it = 0, inner = 0;
+        unsigned long long basis = 0, cycles = 0, trials = 0;
         while (f > stop && it < a.max_newton) {
-            inner += gs_gmres(a, W, G, f, d, Z, V, sm);
+            inner += gs_gmres(a, W, G, f, d, Z, V, sm, basis, cycles);
             double *Wt = V, *Gt = V + n2;
             double lam = 1.0, ft = f;
             for (int h = 0; h < 11; ++h) {
                 for (int p = threadIdx.x; p < n2; p += blockDim.x) Wt[p] = fma(-lam, d[p], W[p]);
                 __syncthreads();
                 ft = sqrt(gs_residual(a, Wt, win, Gt, sm.sh));
+                ++trials;
                 if (ft <= (1.0 - 1e-4 * lam) * f || h == 10) break;
                 lam *= 0.5;
             }
@@ -362,6 +372,9 @@ __global__ void __launch_bounds__(NT) gs_newton_kernel(GsArgs a)
             atomicAdd(&a.stats[1], (unsigned long long)inner);
             if (f > stop) atomicAdd(&a.stats[2], 1ull);
             atomicAdd(&a.stats[3], 1ull);
+            atomicAdd(&a.stats[4], basis);
+            atomicAdd(&a.stats[5], trials);
+            atomicAdd(&a.stats[6], cycles);
         }
         double acc = 0.0;
         if (jb.sub) {

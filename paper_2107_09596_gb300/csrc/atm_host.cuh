@@ -1130,7 +1130,7 @@ struct Plan : PlanBase {
             const size_t cap = ((size_t)8 << 30) / (gs_stride * sizeof(double));
             if ((size_t)gs_ctas > cap) gs_ctas = cap < 1 ? 1 : (int)cap;
             gs_scratch = take<double>((size_t)gs_ctas * gs_stride);
-            gs_stats = take<unsigned long long>(4);
+            gs_stats = take<unsigned long long>(kGsStats);
         }
         if (sizeof(T) != sizeof(double)) {
             sin = take<T>((size_t)midcap * nsp);
@@ -1682,7 +1682,7 @@ struct Plan : PlanBase {
             ATM_CK(cudaMemsetAsync(ubase, 0, n0, st));
             if (bwork) ATM_CK(cudaMemsetAsync(bwork, 0, n0, st));
         }
-        if (gs_stats) ATM_CK(cudaMemsetAsync(gs_stats, 0, 4 * sizeof(unsigned long long), st));
+        if (gs_stats) ATM_CK(cudaMemsetAsync(gs_stats, 0, kGsStats * sizeof(unsigned long long), st));
         ATM_CK(cudaEventCreate(&ev0));
         ATM_CK(cudaEventCreate(&ev1));
         pev.assign(4 * (size_t)nprof, nullptr);
@@ -2174,10 +2174,10 @@ struct Plan : PlanBase {
     atm_status newton_stats(long long *out) override
     {
         if (!gs_stats) return fail(ATM_ERR_UNSUPPORTED, "not a Gray-Scott handle");
-        unsigned long long h[4] = {0, 0, 0, 0};
+        unsigned long long h[kGsStats] = {};
         ATM_CK(cudaMemcpyAsync(h, gs_stats, sizeof(h), cudaMemcpyDeviceToHost, st));
         ATM_CK(cudaStreamSynchronize(st));
-        for (int i = 0; i < 4; ++i) out[i] = (long long)h[i];
+        for (int i = 0; i < kGsStats; ++i) out[i] = (long long)h[i];
         return ATM_OK;
     }
 
