@@ -61,9 +61,10 @@ enum {
                             A state is the u field followed by the v field (2 nx ny
                             values).  Every level's propagator is one backward Euler
                             step (step D of the level) solved by Newton's method: each
-                            Newton system by GMRES with right preconditioning (x line
-                            solves, the pointwise 2x2 reaction Jacobian, y line solves),
-                            relative tolerance 1e-7, restart 20, at most 200 iterations;
+                            Newton system by GMRES in FP32 with right preconditioning (x
+                            line solves, the pointwise 2x2 reaction Jacobian, y line
+                            solves), relative tolerance 1e-5, restart 20, at most 200
+                            iterations (iterate, residual and step in FP64);
                             a halving line search on the 2-norm of the step's residual G;
                             stop when ||G||_2 <= max(newton_tol, newton_tol ||G(w_prev)||_2).
                             One CTA per state.  FP64 only; 8 <= nx, ny <= 512 (any

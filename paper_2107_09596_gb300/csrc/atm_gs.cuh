@@ -12,6 +12,13 @@
 // ||G(w)||, else the last); Newton stops when ||G||_2 <= max(tol, tol ||G(w_prev)||_2)
 // or after max_newton iterations (counted as a failure).
 //
+// Precision: the iterate w, the residual G, the Newton step d and the line
+// search are FP64 (they decide the step's result: its root of G to `tol`).
+// The Newton system is only solved to a relative eta (inexact Newton), so
+// GMRES runs in FP32 -- its Krylov basis, operator and preconditioner -- with
+// FP64 Givens rotations and block sums; a restart forms its residual
+// G - M d in FP64.  (FP64 arithmetic runs at 1/64 of the FP32 rate here.)
+//
 // Preconditioner: P = (I - D Du,v Lap_x)(I - D J(w))(I - D Du,v Lap_y), i.e.
 // periodic constant-coefficient line solves along x, the pointwise 2x2
 // reaction Jacobian, and line solves along y.  Each line operator
@@ -20,8 +27,8 @@
 // recurrences with the closure 1 / (1 - rho^n).
 //
 // One CTA owns one state for its whole nonlinear solve; the state's vectors
-// (iterate, residual, Newton step, preconditioned vector, Krylov basis) live in
-// a per-CTA slice of global scratch.  Reductions are deterministic CTA sums.
+// live in a per-CTA slice of global scratch.  Reductions are deterministic CTA
+// sums.
 #pragma once
 
 #include "atm_kernels.cuh"
@@ -29,12 +36,16 @@
 namespace atm {
 
 constexpr int kGsMaxRestart = 30;
-constexpr int kGsThreads = 256;
+constexpr int kGsThreads = 512;
 
 struct GsLine {
     double rho;       // decay factor of the factorised line operator
     double kinv;      // 1 / kappa
     double closure;   // 1 / (1 - rho^n)
+};
+
+struct GsLine32 {
+    float rho, kinv, closure;
 };
 
 struct GsArgs {
@@ -51,7 +62,7 @@ struct GsArgs {
     int restart;              // GMRES restart length (<= kGsMaxRestart)
     int max_inner;            // GMRES iterations per Newton system
     double eta;               // GMRES relative tolerance
-    double *scratch;          // per-CTA slices of cta_stride doubles
+    unsigned char *scratch;   // per-CTA slices of cta_stride bytes
     size_t cta_stride;
     double *partials;         // per job: sum of r^2 (null: none)
     unsigned long long *stats;   // kGsStats counters (see gs_newton_kernel)
@@ -63,10 +74,13 @@ struct GsArgs {
 // cycles, unused.
 constexpr int kGsStats = 8;
 
-// Doubles of one CTA's scratch slice: W, G, d, Z and restart + 1 Krylov vectors.
-inline size_t gs_cta_doubles(int nx, int ny, int restart)
+// Bytes of one CTA's scratch slice: five FP64 vectors (W, G, d, trial W,
+// trial G) and restart + 2 FP32 vectors (Z and the Krylov basis), each of
+// 2 nx ny values.
+inline size_t gs_cta_bytes(int nx, int ny, int restart)
 {
-    return (size_t)(restart + 5) * 2 * (size_t)nx * ny;
+    const size_t n2 = 2 * (size_t)nx * ny;
+    return 5 * n2 * sizeof(double) + (size_t)(restart + 2) * n2 * sizeof(float);
 }
 
 // CTA-wide sum in a fixed order; every thread receives the total.
@@ -92,42 +106,94 @@ __device__ __forceinline__ double gs_sum(double v, double *sh)
 // Periodic solve of tridiag(-a, 1 + 2a, -a) x = f along one line of n values
 // at `stride`; o may equal f.  z = rho z(-1) + f / kappa (periodic), then
 // x = rho x(+1) + z (periodic); each periodic recurrence starts from its
-// closed-form wrap-around value.
-__device__ __forceinline__ void gs_line_solve(const double *f, double *o, int stride, int n, GsLine c)
+// closed-form wrap-around value.  Values move in blocks of B loads issued
+// before the block's serial multiply-adds, so that the loads of a block
+// overlap instead of each waiting for the previous step.
+template <int B>
+__device__ __forceinline__ void gs_line_solve(const float *f, float *o, int stride, int n, GsLine32 c)
 {
-    double s = 0.0;
-    for (int i = 0; i < n; ++i) s = fma(c.rho, s, f[(size_t)i * stride]);
-    double prev = c.kinv * s * c.closure;                 // z_{n-1}
-    for (int i = 0; i < n; ++i) {
-        const double z = fma(c.rho, prev, c.kinv * f[(size_t)i * stride]);
-        o[(size_t)i * stride] = z;
-        prev = z;
+    float s = 0.0f;
+    for (int i0 = 0; i0 < n; i0 += B) {
+        float v[B];
+#pragma unroll
+        for (int k = 0; k < B; ++k) v[k] = (i0 + k < n) ? f[(size_t)(i0 + k) * stride] : 0.0f;
+#pragma unroll
+        for (int k = 0; k < B; ++k)
+            if (i0 + k < n) s = fmaf(c.rho, s, v[k]);
     }
-    s = 0.0;
-    for (int i = n - 1; i >= 0; --i) s = fma(c.rho, s, o[(size_t)i * stride]);
+    float prev = c.kinv * s * c.closure;                  // z_{n-1}
+    for (int i0 = 0; i0 < n; i0 += B) {
+        float v[B];
+#pragma unroll
+        for (int k = 0; k < B; ++k) v[k] = (i0 + k < n) ? f[(size_t)(i0 + k) * stride] : 0.0f;
+#pragma unroll
+        for (int k = 0; k < B; ++k)
+            if (i0 + k < n) {
+                prev = fmaf(c.rho, prev, c.kinv * v[k]);
+                o[(size_t)(i0 + k) * stride] = prev;
+            }
+    }
+    s = 0.0f;
+    for (int i1 = n; i1 > 0; i1 -= B) {
+        float v[B];
+#pragma unroll
+        for (int k = 0; k < B; ++k) v[k] = (i1 - 1 - k >= 0) ? o[(size_t)(i1 - 1 - k) * stride] : 0.0f;
+#pragma unroll
+        for (int k = 0; k < B; ++k)
+            if (i1 - 1 - k >= 0) s = fmaf(c.rho, s, v[k]);
+    }
     prev = s * c.closure;                                 // x_n = x_0
-    for (int i = n - 1; i >= 0; --i) {
-        const double x = fma(c.rho, prev, o[(size_t)i * stride]);
-        o[(size_t)i * stride] = x;
-        prev = x;
+    for (int i1 = n; i1 > 0; i1 -= B) {
+        float v[B];
+#pragma unroll
+        for (int k = 0; k < B; ++k) v[k] = (i1 - 1 - k >= 0) ? o[(size_t)(i1 - 1 - k) * stride] : 0.0f;
+#pragma unroll
+        for (int k = 0; k < B; ++k)
+            if (i1 - 1 - k >= 0) {
+                prev = fmaf(c.rho, prev, v[k]);
+                o[(size_t)(i1 - 1 - k) * stride] = prev;
+            }
     }
 }
 
-// G = W - Win - (Lap_D W + D R(W)); returns ||G||_2^2 (all threads).
+// Grid point p = y nx + x of a thread's strided walk and its periodic
+// neighbours, advanced by NT points at a time without a division per point.
+struct GsWalk {
+    int p, x, y;
+    __device__ __forceinline__ explicit GsWalk(int nx) : p(threadIdx.x), x(threadIdx.x), y(0)
+    {
+        while (x >= nx) { x -= nx; ++y; }
+    }
+    template <int NT>
+    __device__ __forceinline__ void next(int nx)
+    {
+        p += NT;
+        x += NT;
+        while (x >= nx) { x -= nx; ++y; }
+    }
+    __device__ __forceinline__ void nbrs(int nx, int ny, int n, int &xm, int &xp, int &ym, int &yp) const
+    {
+        xm = x == 0 ? p + nx - 1 : p - 1;
+        xp = x == nx - 1 ? p - nx + 1 : p + 1;
+        ym = y == 0 ? p + n - nx : p - nx;
+        yp = y == ny - 1 ? p - n + nx : p + nx;
+    }
+};
+
+// G = W - Win - (Lap_D W + D R(W)) in FP64; returns ||G||_2^2 (all threads).
+template <int NT>
 __device__ __forceinline__ double gs_residual(const GsArgs &a, const double *W, const double *Win, double *G, double *sh)
 {
     const int nx = a.nx, ny = a.ny, n = nx * ny;
     const double kf = a.kill + a.feed;
     double acc = 0.0;
-    for (int p = threadIdx.x; p < n; p += blockDim.x) {
-        const int y = p / nx, x = p - y * nx;
-        const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
-        const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+    for (GsWalk w(nx); w.p < n; w.next<NT>(nx)) {
+        int xm, xp, ym, yp;
+        w.nbrs(nx, ny, n, xm, xp, ym, yp);
+        const int p = w.p;
         const double u = W[p], v = W[n + p];
-        const double lu = a.ex[0] * (W[y * nx + xm] + W[y * nx + xp] - 2.0 * u) +
-                          a.ey[0] * (W[ym * nx + x] + W[yp * nx + x] - 2.0 * u);
-        const double lv = a.ex[1] * (W[n + y * nx + xm] + W[n + y * nx + xp] - 2.0 * v) +
-                          a.ey[1] * (W[n + ym * nx + x] + W[n + yp * nx + x] - 2.0 * v);
+        const double lu = a.ex[0] * (W[xm] + W[xp] - 2.0 * u) + a.ey[0] * (W[ym] + W[yp] - 2.0 * u);
+        const double lv = a.ex[1] * (W[n + xm] + W[n + xp] - 2.0 * v) + a.ey[1] * (W[n + ym] + W[n + yp] - 2.0 * v);
         const double uvv = u * v * v;
         const double gu = u - Win[p] - lu - a.D * (a.feed * (1.0 - u) - uvv);
         const double gv = v - Win[n + p] - lv - a.D * (uvv - kf * v);
@@ -139,21 +205,20 @@ __device__ __forceinline__ double gs_residual(const GsArgs &a, const double *W, 
     return gs_sum(acc, sh);
 }
 
-// out = M(W) z = z - Lap_D z - D J(W) z (no synchronisation).
-__device__ __forceinline__ void gs_apply_M(const GsArgs &a, const double *W, const double *z, double *out)
+// out = M(W) z in FP64 (restart residuals; no synchronisation).
+template <int NT>
+__device__ __forceinline__ void gs_apply_M64(const GsArgs &a, const double *W, const double *z, double *out)
 {
     const int nx = a.nx, ny = a.ny, n = nx * ny;
     const double kf = a.kill + a.feed;
-    for (int p = threadIdx.x; p < n; p += blockDim.x) {
-        const int y = p / nx, x = p - y * nx;
-        const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
-        const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+    for (GsWalk w(nx); w.p < n; w.next<NT>(nx)) {
+        int xm, xp, ym, yp;
+        w.nbrs(nx, ny, n, xm, xp, ym, yp);
+        const int p = w.p;
         const double u = W[p], v = W[n + p];
         const double zu = z[p], zv = z[n + p];
-        const double lu = a.ex[0] * (z[y * nx + xm] + z[y * nx + xp] - 2.0 * zu) +
-                          a.ey[0] * (z[ym * nx + x] + z[yp * nx + x] - 2.0 * zu);
-        const double lv = a.ex[1] * (z[n + y * nx + xm] + z[n + y * nx + xp] - 2.0 * zv) +
-                          a.ey[1] * (z[n + ym * nx + x] + z[n + yp * nx + x] - 2.0 * zv);
+        const double lu = a.ex[0] * (z[xm] + z[xp] - 2.0 * zu) + a.ey[0] * (z[ym] + z[yp] - 2.0 * zu);
+        const double lv = a.ex[1] * (z[n + xm] + z[n + xp] - 2.0 * zv) + a.ey[1] * (z[n + ym] + z[n + yp] - 2.0 * zv);
         const double j11 = -(v * v + a.feed), j12 = -2.0 * u * v;
         const double j21 = v * v, j22 = 2.0 * u * v - kf;
         out[p] = zu - lu - a.D * (j11 * zu + j12 * zv);
@@ -161,33 +226,67 @@ __device__ __forceinline__ void gs_apply_M(const GsArgs &a, const double *W, con
     }
 }
 
-// z = P^-1 x (x != z); ends synchronised.
-__device__ __forceinline__ void gs_precond(const GsArgs &a, const double *W, const double *x, double *z)
+// The same operator in FP32 on FP32 vectors (GMRES; no synchronisation).
+template <int NT>
+__device__ __forceinline__ void gs_apply_M32(const GsArgs &a, const double *W, const float *z, float *out)
 {
     const int nx = a.nx, ny = a.ny, n = nx * ny;
-    for (int t = threadIdx.x; t < 2 * ny; t += blockDim.x) {
-        const int s = t / ny, y = t - s * ny;
-        gs_line_solve(x + (size_t)s * n + (size_t)y * nx, z + (size_t)s * n + (size_t)y * nx, 1, nx,
-                      s ? a.lx[1] : a.lx[0]);
+    const float D = (float)a.D, feed = (float)a.feed, kf = (float)(a.kill + a.feed);
+    const float exu = (float)a.ex[0], eyu = (float)a.ey[0], exv = (float)a.ex[1], eyv = (float)a.ey[1];
+    for (GsWalk w(nx); w.p < n; w.next<NT>(nx)) {
+        int xm, xp, ym, yp;
+        w.nbrs(nx, ny, n, xm, xp, ym, yp);
+        const int p = w.p;
+        const float u = (float)W[p], v = (float)W[n + p];
+        const float zu = z[p], zv = z[n + p];
+        const float lu = exu * (z[xm] + z[xp] - 2.0f * zu) + eyu * (z[ym] + z[yp] - 2.0f * zu);
+        const float lv = exv * (z[n + xm] + z[n + xp] - 2.0f * zv) + eyv * (z[n + ym] + z[n + yp] - 2.0f * zv);
+        const float j11 = -(v * v + feed), j12 = -2.0f * u * v;
+        const float j21 = v * v, j22 = 2.0f * u * v - kf;
+        out[p] = zu - lu - D * (j11 * zu + j12 * zv);
+        out[n + p] = zv - lv - D * (j21 * zu + j22 * zv);
+    }
+}
+
+__device__ __forceinline__ GsLine32 gs_line32(const GsLine &c)
+{
+    GsLine32 r;
+    r.rho = (float)c.rho;
+    r.kinv = (float)c.kinv;
+    r.closure = (float)c.closure;
+    return r;
+}
+
+// z = P^-1 x in FP32 (x != z); ends synchronised.
+template <int NT>
+__device__ __forceinline__ void gs_precond(const GsArgs &a, const double *W, const float *x, float *z)
+{
+    const int nx = a.nx, ny = a.ny, n = nx * ny;
+    for (int t = threadIdx.x; t < 2 * ny; t += NT) {
+        const int s = t >= ny, y = t - s * ny;
+        gs_line_solve<8>(x + (size_t)s * n + (size_t)y * nx, z + (size_t)s * n + (size_t)y * nx, 1, nx,
+                         gs_line32(s ? a.lx[1] : a.lx[0]));
     }
     __syncthreads();
-    const double kf = a.kill + a.feed;
-    for (int p = threadIdx.x; p < n; p += blockDim.x) {
-        const double u = W[p], v = W[n + p];
-        const double a11 = 1.0 + a.D * (v * v + a.feed), a12 = 2.0 * a.D * u * v;
-        const double a21 = -a.D * v * v, a22 = 1.0 - a.D * (2.0 * u * v - kf);
-        const double det = a11 * a22 - a12 * a21;
-        if (fabs(det) > 1e-12) {   // a (numerically) singular point keeps the identity
-            const double zu = z[p], zv = z[n + p];
-            z[p] = (a22 * zu - a12 * zv) / det;
-            z[n + p] = (a11 * zv - a21 * zu) / det;
+    const float D = (float)a.D, feed = (float)a.feed, kf = (float)(a.kill + a.feed);
+#pragma unroll 4
+    for (int p = threadIdx.x; p < n; p += NT) {
+        const float u = (float)W[p], v = (float)W[n + p];
+        const float a11 = 1.0f + D * (v * v + feed), a12 = 2.0f * D * u * v;
+        const float a21 = -D * v * v, a22 = 1.0f - D * (2.0f * u * v - kf);
+        const float det = a11 * a22 - a12 * a21;
+        if (fabsf(det) > 1e-6f) {   // a (numerically) singular point keeps the identity
+            const float zu = z[p], zv = z[n + p];
+            const float id = 1.0f / det;
+            z[p] = (a22 * zu - a12 * zv) * id;
+            z[n + p] = (a11 * zv - a21 * zu) * id;
         }
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < 2 * nx; t += blockDim.x) {
-        const int s = t / nx, x = t - s * nx;
-        double *line = z + (size_t)s * n + x;
-        gs_line_solve(line, line, nx, ny, s ? a.ly[1] : a.ly[0]);
+    for (int t = threadIdx.x; t < 2 * nx; t += NT) {
+        const int s = t >= nx, x = t - s * nx;
+        float *line = z + (size_t)s * n + x;
+        gs_line_solve<8>(line, line, nx, ny, gs_line32(s ? a.ly[1] : a.ly[0]));
     }
     __syncthreads();
 }
@@ -201,14 +300,17 @@ struct GsSmem {
 };
 
 // d ~= M(W)^-1 G by right-preconditioned restarted GMRES from d = 0, to
-// relative residual eta (||G||_2 = beta0) or max_inner iterations.
-// Returns the iterations taken.
+// relative residual eta (||G||_2 = beta0) or max_inner iterations; the
+// Krylov basis V and Z are FP32, d is FP64 (T a free FP64 vector).  Returns
+// the iterations taken.
+template <int NT>
 __device__ __forceinline__ int gs_gmres(const GsArgs &a, const double *W, const double *G, double beta0, double *d,
-                        double *Z, double *V, GsSmem &sm, unsigned long long &basis, unsigned long long &cycles)
+                                        double *T, float *Z, float *V, GsSmem &sm, unsigned long long &basis,
+                                        unsigned long long &cycles)
 {
     const int n2 = 2 * a.nx * a.ny, kr = a.restart;
     const double target = a.eta * beta0;
-    for (int p = threadIdx.x; p < n2; p += blockDim.x) d[p] = 0.0;
+    for (int p = threadIdx.x; p < n2; p += NT) d[p] = 0.0;
     int total = 0;
     bool first = true;
     while (true) {
@@ -217,21 +319,22 @@ __device__ __forceinline__ int gs_gmres(const GsArgs &a, const double *W, const 
             beta = beta0;
             if (!(beta > 0.0)) break;
             const double ib = 1.0 / beta;
-            for (int p = threadIdx.x; p < n2; p += blockDim.x) V[p] = G[p] * ib;
+            for (int p = threadIdx.x; p < n2; p += NT) V[p] = (float)(G[p] * ib);
         } else {
+            // restart: the residual G - M d in FP64
             __syncthreads();
-            gs_apply_M(a, W, d, V);
+            gs_apply_M64<NT>(a, W, d, T);
             __syncthreads();
             double acc = 0.0;
-            for (int p = threadIdx.x; p < n2; p += blockDim.x) {
-                const double r = G[p] - V[p];
-                V[p] = r;
+            for (int p = threadIdx.x; p < n2; p += NT) {
+                const double r = G[p] - T[p];
+                T[p] = r;
                 acc = fma(r, r, acc);
             }
             beta = sqrt(gs_sum(acc, sm.sh));
             if (beta <= target) break;
             const double ib = 1.0 / beta;
-            for (int p = threadIdx.x; p < n2; p += blockDim.x) V[p] *= ib;
+            for (int p = threadIdx.x; p < n2; p += NT) V[p] = (float)(T[p] * ib);
         }
         first = false;
         ++cycles;
@@ -241,40 +344,41 @@ __device__ __forceinline__ int gs_gmres(const GsArgs &a, const double *W, const 
         double res = beta;
         bool done = false;
         while (j < kr) {
-            const double *Vj = V + (size_t)j * n2;
-            double *Vn = V + (size_t)(j + 1) * n2;
-            gs_precond(a, W, Vj, Z);
-            gs_apply_M(a, W, Z, Vn);
+            const float *Vj = V + (size_t)j * n2;
+            float *Vn = V + (size_t)(j + 1) * n2;
+            gs_precond<NT>(a, W, Vj, Z);
+            gs_apply_M32<NT>(a, W, Z, Vn);
             __syncthreads();
             // modified Gram-Schmidt; the update by V_i and the product with
             // V_{i+1} (or the squared norm) share one pass
-            double acc = 0.0;
-            for (int p = threadIdx.x; p < n2; p += blockDim.x) acc = fma(Vn[p], V[p], acc);
-            double h = gs_sum(acc, sm.sh);
+            float accf = 0.0f;
+            for (int p = threadIdx.x; p < n2; p += NT) accf = fmaf(Vn[p], V[p], accf);
+            double h = gs_sum((double)accf, sm.sh);
             for (int i = 0; i <= j; ++i) {
-                const double *Vi = V + (size_t)i * n2;
-                acc = 0.0;
+                const float *Vi = V + (size_t)i * n2;
+                const float hf = (float)h;
+                accf = 0.0f;
                 if (i < j) {
-                    const double *Vq = Vi + n2;
-                    for (int p = threadIdx.x; p < n2; p += blockDim.x) {
-                        const double w = fma(-h, Vi[p], Vn[p]);
+                    const float *Vq = Vi + n2;
+                    for (int p = threadIdx.x; p < n2; p += NT) {
+                        const float w = fmaf(-hf, Vi[p], Vn[p]);
                         Vn[p] = w;
-                        acc = fma(w, Vq[p], acc);
+                        accf = fmaf(w, Vq[p], accf);
                     }
                 } else {
-                    for (int p = threadIdx.x; p < n2; p += blockDim.x) {
-                        const double w = fma(-h, Vi[p], Vn[p]);
+                    for (int p = threadIdx.x; p < n2; p += NT) {
+                        const float w = fmaf(-hf, Vi[p], Vn[p]);
                         Vn[p] = w;
-                        acc = fma(w, w, acc);
+                        accf = fmaf(w, w, accf);
                     }
                 }
                 if (threadIdx.x == 0) sm.H[i * kr + j] = h;
-                h = gs_sum(acc, sm.sh);
+                h = gs_sum((double)accf, sm.sh);
             }
             const double hn = sqrt(h);
             if (hn > 0.0) {
-                const double ih = 1.0 / hn;
-                for (int p = threadIdx.x; p < n2; p += blockDim.x) Vn[p] *= ih;
+                const float ih = (float)(1.0 / hn);
+                for (int p = threadIdx.x; p < n2; p += NT) Vn[p] *= ih;
             }
             if (threadIdx.x == 0) {
                 sm.H[(j + 1) * kr + j] = hn;
@@ -314,56 +418,57 @@ __device__ __forceinline__ int gs_gmres(const GsArgs &a, const double *W, const 
             }
         }
         __syncthreads();
-        double *S = V + (size_t)j * n2;
-        for (int p = threadIdx.x; p < n2; p += blockDim.x) {
-            double s = 0.0;
-            for (int i = 0; i < j; ++i) s = fma(sm.yv[i], V[(size_t)i * n2 + p], s);
+        float *S = V + (size_t)j * n2;
+        for (int p = threadIdx.x; p < n2; p += NT) {
+            float s = 0.0f;
+            for (int i = 0; i < j; ++i) s = fmaf((float)sm.yv[i], V[(size_t)i * n2 + p], s);
             S[p] = s;
         }
         __syncthreads();
-        gs_precond(a, W, S, Z);
-        for (int p = threadIdx.x; p < n2; p += blockDim.x) d[p] += Z[p];
+        gs_precond<NT>(a, W, S, Z);
+        for (int p = threadIdx.x; p < n2; p += NT) d[p] += (double)Z[p];
         __syncthreads();
         if (done || res <= target) break;
     }
     return total;
 }
 
-// One backward Euler step per job; job epilogue as the other propagator kernels.
+// One backward Euler step per job; job epilogue as the other propagator
+// kernels.  Grid: min(jobs, resident slices) CTAs of NT threads, each taking
+// jobs blockIdx.x, blockIdx.x + gridDim.x, ...
 template <int NT>
-__global__ void __launch_bounds__(NT) gs_newton_kernel(GsArgs a)
+__global__ void __launch_bounds__(NT, 2) gs_newton_kernel(GsArgs a)
 {
     __shared__ GsSmem sm;
     const int n2 = 2 * a.nx * a.ny;
-    double *slice = a.scratch + (size_t)blockIdx.x * a.cta_stride;
-    double *W = slice, *G = slice + n2, *d = slice + 2 * (size_t)n2, *Z = slice + 3 * (size_t)n2;
-    double *V = slice + 4 * (size_t)n2;
+    unsigned char *slice = a.scratch + (size_t)blockIdx.x * a.cta_stride;
+    double *W = reinterpret_cast<double *>(slice);
+    double *G = W + n2, *d = G + n2, *Wt = d + n2, *Gt = Wt + n2;
+    float *Z = reinterpret_cast<float *>(Gt + n2);
+    float *V = Z + n2;
     for (int job = blockIdx.x; job < a.njobs; job += gridDim.x) {
         const Job<double> jb = a.jobs[job];
         const double *win = jb.in;
-        for (int p = threadIdx.x; p < n2; p += blockDim.x) W[p] = win[p];
+        for (int p = threadIdx.x; p < n2; p += NT) W[p] = win[p];
         __syncthreads();
-        double f = sqrt(gs_residual(a, W, win, G, sm.sh));
+        double f = sqrt(gs_residual<NT>(a, W, win, G, sm.sh));
         const double stop = fmax(a.tol, a.tol * f);
         int it = 0, inner = 0;
         unsigned long long basis = 0, cycles = 0, trials = 0;
         while (f > stop && it < a.max_newton) {
-            inner += gs_gmres(a, W, G, f, d, Z, V, sm, basis, cycles);
-            double *Wt = V, *Gt = V + n2;
+            inner += gs_gmres<NT>(a, W, G, f, d, Wt, Z, V, sm, basis, cycles);
             double lam = 1.0, ft = f;
             for (int h = 0; h < 11; ++h) {
-                for (int p = threadIdx.x; p < n2; p += blockDim.x) Wt[p] = fma(-lam, d[p], W[p]);
+                for (int p = threadIdx.x; p < n2; p += NT) Wt[p] = fma(-lam, d[p], W[p]);
                 __syncthreads();
-                ft = sqrt(gs_residual(a, Wt, win, Gt, sm.sh));
+                ft = sqrt(gs_residual<NT>(a, Wt, win, Gt, sm.sh));
                 ++trials;
                 if (ft <= (1.0 - 1e-4 * lam) * f || h == 10) break;
                 lam *= 0.5;
             }
-            for (int p = threadIdx.x; p < n2; p += blockDim.x) {
-                W[p] = Wt[p];
-                G[p] = Gt[p];
-            }
-            __syncthreads();
+            // accept: swap the iterate and residual with the trial ones
+            double *t0 = W; W = Wt; Wt = t0;
+            double *t1 = G; G = Gt; Gt = t1;
             f = ft;
             ++it;
         }
@@ -378,9 +483,9 @@ __global__ void __launch_bounds__(NT) gs_newton_kernel(GsArgs a)
         }
         double acc = 0.0;
         if (jb.sub) {
-            for (int p = threadIdx.x; p < n2; p += blockDim.x) apply_epilogue<double, true>(jb, p, W[p], a.neg, acc);
+            for (int p = threadIdx.x; p < n2; p += NT) apply_epilogue<double, true>(jb, p, W[p], a.neg, acc);
         } else {
-            for (int p = threadIdx.x; p < n2; p += blockDim.x) apply_epilogue<double, false>(jb, p, W[p], a.neg, acc);
+            for (int p = threadIdx.x; p < n2; p += NT) apply_epilogue<double, false>(jb, p, W[p], a.neg, acc);
         }
         if (a.partials) {
             const double t = gs_sum(acc, sm.sh);

@@ -363,9 +363,9 @@ struct Plan : PlanBase {
     int nsp = 0;
     bool is1d = false;
     bool isgs = false;      // Gray-Scott: two fields per state, Newton kernel on every level
-    double *gs_scratch = nullptr;            // per-CTA slices of the Newton kernel
+    unsigned char *gs_scratch = nullptr;     // per-CTA slices of the Newton kernel
     int gs_ctas = 0;                         // CTAs of a Newton launch at most
-    size_t gs_stride = 0;                    // doubles per slice
+    size_t gs_stride = 0;                    // bytes per slice
     unsigned long long *gs_stats = nullptr;  // Newton / GMRES iterations, failures, steps
     int maxbatch = 16;
     int midcap = 16;        // states in the row-sweep intermediate (launches are chunked to it)
@@ -572,7 +572,7 @@ struct Plan : PlanBase {
         g.max_newton = pb.newton_max_iter > 0 ? pb.newton_max_iter : 50;
         g.restart = 20;
         g.max_inner = 200;
-        g.eta = 1e-7;
+        g.eta = 1e-5;
         g.scratch = gs_scratch;
         g.cta_stride = gs_stride;
         g.stats = gs_stats;
@@ -1125,11 +1125,11 @@ struct Plan : PlanBase {
                 cudaGetLastError();
                 sms = 152;
             }
-            gs_stride = gs_cta_doubles(pb.nx, pb.ny, 20);
+            gs_stride = (gs_cta_bytes(pb.nx, pb.ny, 20) + 255) & ~(size_t)255;
             gs_ctas = 2 * sms;
-            const size_t cap = ((size_t)8 << 30) / (gs_stride * sizeof(double));
+            const size_t cap = ((size_t)8 << 30) / gs_stride;
             if ((size_t)gs_ctas > cap) gs_ctas = cap < 1 ? 1 : (int)cap;
-            gs_scratch = take<double>((size_t)gs_ctas * gs_stride);
+            gs_scratch = take<unsigned char>((size_t)gs_ctas * gs_stride);
             gs_stats = take<unsigned long long>(kGsStats);
         }
         if (sizeof(T) != sizeof(double)) {
