@@ -244,6 +244,36 @@ def gs_vector_bytes(st, n2):
     return (8 * f64 + 4 * f32) * n2
 
 
+def run_gs_probe(args):
+    """One level-0 and one level-1 Newton launch of the two-level Gray-Scott
+    handle on 255 states (0.7 x the initial state + 0.3 x seeded random
+    states): the small case for profiling the Newton kernel."""
+    import torch
+    import paper_2107_09596_gb300 as atm
+    w = dict(GS_WORKLOAD, **GS_CONFIGS["2lvl"])
+    atm._build.build()
+    n = w["n"]
+    prob = atm.make_problem(atm.GRAY_SCOTT, n, n, lx=w["lx"], ly=w["lx"], dt=w["dt"], nt_points=w["nt"],
+                            du=w["du"], dv=w["dv"], feed=w["feed"], kill=w["kill"],
+                            newton_tol=w["newton_tol"], newton_max_iter=50)
+    desc = atm.make_solver(atm.AT_MGRIT, m=w["m"], k=w["k"], nu=w["nu"], tol=w["tol"], max_iter=w["max_iter"],
+                           cpoint_only=True)
+    s = atm.Solver(prob, desc)
+    x = np.stack([0.3 * I.gray_scott_random_state(n, n, seed) + 0.7 * I.gray_scott_initial_condition(n, n)
+                  for seed in range(255)])
+    xd = torch.as_tensor(x, device="cuda:0")
+    ms = []
+    for level in (0, 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s.stream)
+        s.apply_propagator(level, xd)
+        e1.record(s.stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    print(json.dumps({"gs_probe": {"states": 255, "level_ms": ms, "newton": s.newton_stats()}}))
+    s.close()
+
+
 def run_gray_scott(args):
     import torch
     import paper_2107_09596_gb300 as atm
@@ -533,6 +563,9 @@ def main():
     ap.add_argument("--gs-config", choices=sorted(GS_CONFIGS), default="2lvl",
                     help="gray_scott_128: 2lvl (m = 64, k = 128, F) or 3lvl ((64, 4), k = 32, FCF)")
     ap.add_argument("--cold", action="store_true", help="gray_scott_128: zero guess instead of nested iteration")
+    ap.add_argument("--gs-probe", action="store_true",
+                    help="gray_scott_128: only one level-0 and one level-1 Newton launch on 255 states "
+                         "(the profiling case)")
     ap.add_argument("--algorithm", choices=["at", "mgrit", "seq"], default="at")
     ap.add_argument("--precision", choices=["fp64", "fp32", "fp32r"], default="fp32r",
                     help="fp32r: FP32 propagation with FP64 refinement (the fastest form that reaches 1e-8)")
@@ -561,7 +594,10 @@ def main():
             print(json.dumps({"impl": "reference", "unavailable": "gray_scott_128 has no reference arm; "
                               "its CPU baseline is the oracle's stepping rate in the atm line"}))
             return
-        run_gray_scott(args)
+        if args.gs_probe:
+            run_gs_probe(args)
+        else:
+            run_gray_scott(args)
         return
     w = dict(WORKLOADS[args.workload])
     if args.max_iter is not None:
