@@ -41,6 +41,9 @@
  *              w = u for the heat equation.
  *     FINEPOW: m_{l-1} applications of the next finer level's propagator
  *              (the exact coarse operator Phi^m of Sec. 3.1.1).
+ *   gray-scott (Sec. 5.1): two fields per state; one backward Euler step
+ *            solved by Newton's method, supplied by the caller (ext_prop; the
+ *            test suite's numpy/scipy implementation in gray_scott.py).
  */
 #include <math.h>
 #include <stdlib.h>
