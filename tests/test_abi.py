@@ -71,3 +71,32 @@ def test_invalid_solver_rejected(atm, change):
     s = atm.make_solver(**kw)
     with pytest.raises(atm.AtmError):
         atm.workspace_size(p, s)
+
+
+def test_gray_scott_workspace_and_validation(atm):
+    # 128^2 x 16384 points, m = 64, full storage: level 0, four arrays on level 1,
+    # and the Newton kernel's slices (two per SM: five FP64 and 22 FP32 vectors)
+    p = atm.make_problem(atm.GRAY_SCOTT, 128, 128, lx=2.5, ly=2.5, dt=256 / 16383, nt_points=16384)
+    s = atm.make_solver(atm.AT_MGRIT, m=(64,), k=128, nu=0, tol=1e-7)
+    n = atm.workspace_size(p, s)
+    state = 2 * 128 * 128 * 8
+    slices = 2 * 152 * (5 * state + 22 * state // 2)
+    base = (16384 + 4 * 256) * state
+    assert base + slices <= n < base + slices + 300 * state
+    # C-point storage keeps the C-points and one working state per interval
+    sc = atm.make_solver(atm.AT_MGRIT, m=(64,), k=128, nu=0, tol=1e-7, cpoint_only=True)
+    assert atm.workspace_size(p, sc) < n - 15000 * state
+    for change in (dict(precision=atm.FP32), dict(precision=atm.FP32_REFINED),
+                   dict(sweep_kernel=atm.SWEEP_FUSED), dict(sweep_kernel=atm.SWEEP_CHAIN),
+                   dict(coarse_prop=atm.PROP_LEARNED)):
+        bad = atm.make_solver(atm.AT_MGRIT, m=(64,), k=128, nu=0, **change)
+        with pytest.raises(atm.AtmError):
+            atm.workspace_size(p, bad)
+    for change in (dict(nx=4), dict(ny=1024), dict(du=-1.0), dict(newton_max_iter=501)):
+        kw = dict(kind=atm.GRAY_SCOTT, nx=64, ny=64, lx=2.5, ly=2.5, dt=0.01, nt_points=129)
+        kw.update(change)
+        with pytest.raises(atm.AtmError):
+            atm.workspace_size(atm.make_problem(**kw), atm.make_solver(atm.AT_MGRIT, m=(8,), k=4))
+    # any grid size from 8 to 512 is allowed
+    atm.workspace_size(atm.make_problem(atm.GRAY_SCOTT, 40, 24, lx=2.5, ly=1.5, dt=0.01, nt_points=65),
+                       atm.make_solver(atm.MGRIT, m=(8,), k=1))
