@@ -47,7 +47,7 @@ WORKLOADS = {
                             tol=1e-2, max_iter=30),
 }
 
-# Textbook flops per grid value of one sweep kernel (see DESIGN.md):
+# Textbook flops per grid value of one sweep kernel:
 # PR explicit term 5, periodic tridiagonal solve 7 (Thomas 5 + rank-one
 # periodic correction 2), split-BE right-hand side 0, reaction substep 5,
 # Dirichlet tridiagonal solve 5 (+2 for the first-row correction).
@@ -68,7 +68,7 @@ def peaks():
     return {
         "hbm_gbs": mp.get("hbm_gbs", 6800.0),
         "hbm_src": "measured" if "hbm_gbs" in mp else "fallback",
-        # FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (derivation in the design doc)
+        # FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (GB300's FP64 rate, 1/64 of FP32)
         "fp64_tflops": 152 * 2 * 2 * 2.07e9 / 1e12,
     }
 
