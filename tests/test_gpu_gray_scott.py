@@ -156,3 +156,25 @@ def test_invalid_gray_scott_options_are_rejected(torch):
     _, gp, gs = gs_pair(nx=4)
     with pytest.raises(atm.AtmError):
         atm.Solver(gp, gs)
+
+
+def test_paper_iteration_counts_at_full_size(torch):
+    """Sec. 5.1 at the paper's size (128^2, 16384 points, nested iteration,
+    Newton tolerance 1e-10, space-time residual 1e-7): the iteration counts
+    printed in Tables 1 and 2."""
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
+    u0 = initial_state(128, 128)
+    for case in gold["gray_scott_iterations"]["cases"]:
+        _, gp, gs = gs_pair(nx=128, ny=128, nt=16384, m=tuple(case["m"]), k=max(case["k"], 1),
+                            nu=case["nu"], algorithm=case["algorithm"], tol=1e-7, max_iter=30,
+                            use_graph=2, cpoint_only=True, nested=True, newton_tol=1e-10)
+        s = atm.Solver(gp, gs)
+        s.set_initial_condition(dev(torch, u0))
+        r = s.solve()
+        print(f"\n{case['name']}: {r['iterations']} cycles (paper {case['iterations']}), "
+              f"residual {r['final_residual']:.2e}")
+        assert r["converged"] and r["iterations"] == case["iterations"]
+        assert s.newton_stats()["failures"] == 0
+        s.close()
