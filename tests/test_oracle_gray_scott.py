@@ -146,3 +146,38 @@ def test_large_k_is_mgrit(orc):
         orc.solve(c, u, max_iter=2)
         res.append(u)
     assert np.array_equal(res[0], res[1])
+
+
+def test_fcycle_with_two_levels_is_the_v_cycle(orc):
+    # with two levels the coarse problem is solved directly (local grids), so
+    # an F-cycle and a V-cycle are the same cycle, operation for operation
+    u0 = I.gray_scott_initial_condition(16, 16)
+    res = []
+    for fc in (False, True):
+        c = gs_cfg(orc, nt=33, m=(4,), k=3, nu=1, fcycle=fc)
+        u = np.zeros((33, 2, 16, 16))
+        u[0] = u0
+        _, hist = orc.solve(c, u, max_iter=2)
+        res.append((u, hist))
+    assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
+
+
+def test_nested_guess_two_levels_is_the_coarse_local_grid_solve(orc):
+    # two levels: the nested start is the coarsest level solved by its local
+    # grids from the guess (u0, 0, ..) (Sec. 2.2 nested iteration with the
+    # local grids of Sec. 5.1).  The grid of point p starts at p - k + 1 from
+    # v + r there; for p <= k that start is u0 or Psi(u0), so points 0..k are
+    # the coarse sequential solution; later grids start from Psi(0), not from
+    # the solution.
+    nt, m, k = 33, 4, 3
+    c = gs_cfg(orc, nt=nt, m=(m,), k=k, nu=1)
+    u0 = I.gray_scott_initial_condition(16, 16)
+    u = np.zeros((nt, 2, 16, 16))
+    u[0] = u0
+    orc.nested_guess(c, u)
+    # the coarse sequential solution with step m dt
+    cc = gs_cfg(orc, dt=m * DT, nt=(nt - 1) // m + 1, m=(2,), k=1)
+    seq = orc.sequential(cc, u0)
+    for p in range(k + 1):
+        np.testing.assert_allclose(u[p * m], seq[p], rtol=0, atol=1e-11)
+    assert np.abs(u[(k + 1) * m] - seq[k + 1]).max() > 1e-6
