@@ -230,6 +230,9 @@ def run_batch(args):
 GS_WORKLOAD = dict(n=128, nt=16384, dt=256.0 / 16383.0, lx=2.5, tol=1e-7, max_iter=30,
                    newton_tol=1e-10, du=8e-5, dv=4e-5, feed=0.024, kill=0.06)
 GS_CONFIGS = {"2lvl": dict(m=(64,), k=128, nu=0), "3lvl": dict(m=(64, 4), k=32, nu=1)}
+# the other rows of Tables 1 and 2 (k = half the coarsest grid's points)
+GS_CONFIGS.update({f"2lvl_m{mm}": dict(m=(mm,), k=8192 // mm, nu=0) for mm in (128, 256, 512)})
+GS_CONFIGS.update({f"3lvl_64_{m1}": dict(m=(64, m1), k=128 // m1, nu=1) for m1 in (2, 8, 16)})
 GS_METRIC = "Gray-Scott time-to-solution at space-time residual 1e-7 and fine steps/s"
 
 
@@ -561,7 +564,8 @@ def main():
                     help="batch64: 64 drawn problems, batched against one at a time; gray_scott_128: the "
                          "Gray-Scott problem of Sec. 5.1 (neither is the default)")
     ap.add_argument("--gs-config", choices=sorted(GS_CONFIGS), default="2lvl",
-                    help="gray_scott_128: 2lvl (m = 64, k = 128, F) or 3lvl ((64, 4), k = 32, FCF)")
+                    help="gray_scott_128: 2lvl (m = 64, k = 128, F), 3lvl ((64, 4), k = 32, FCF), or "
+                         "another row of Tables 1-2: 2lvl_m128/256/512, 3lvl_64_2/8/16")
     ap.add_argument("--cold", action="store_true", help="gray_scott_128: zero guess instead of nested iteration")
     ap.add_argument("--gs-probe", action="store_true",
                     help="gray_scott_128: only one level-0 and one level-1 Newton launch on 255 states "
