@@ -181,3 +181,27 @@ def test_nested_guess_two_levels_is_the_coarse_local_grid_solve(orc):
     for p in range(k + 1):
         np.testing.assert_allclose(u[p * m], seq[p], rtol=0, atol=1e-11)
     assert np.abs(u[(k + 1) * m] - seq[k + 1]).max() > 1e-6
+
+
+def test_line_search_carries_newton_through_a_hard_step(orc):
+    # a large step from an unstructured state: full Newton steps overshoot by
+    # orders of magnitude (first trial ~1e6 against ||G|| ~ 3); the halving
+    # line search keeps every accepted residual below the previous one until
+    # the quadratic phase, and the step meets the tolerance
+    from oracle.gray_scott import GrayScott
+    gs = GrayScott(16, 16, 2.5, 2.5, tol=1e-12, max_iter=60, **PAR)
+    w0 = I.gray_scott_random_state(16, 16, seed=9).ravel()
+    D = 3.0
+    trials = []
+    orig = gs.be_residual
+
+    def record(w, w_prev, DD):
+        G = orig(w, w_prev, DD)
+        trials.append(np.linalg.norm(G))
+        return G
+
+    gs.be_residual = record
+    w = gs.step(w0, D)
+    assert gs.failures == 0 and np.linalg.norm(orig(w, w0, D)) <= 1e-12
+    assert max(trials) > 1e5 * trials[0]            # full steps do overshoot
+    assert gs.newton_iterations > 5                  # and the search is what carries it
