@@ -374,7 +374,7 @@ def run_gray_scott(args):
                          f"stepping rate, the fastest the oracle covers the time axis"}
     line = {"metric": GS_METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic (the paper's initial state)",
+            "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic (the paper's initial state)",
             "config": {"workload": "gray_scott_128", "gs_config": args.gs_config,
                        **{k: (list(v) if isinstance(v, tuple) else v) for k, v in w.items()},
                        "algorithm": args.algorithm, "storage": args.storage, "nested": nested,
