@@ -63,13 +63,20 @@ def load_json(path, default=None):
         return default
 
 
-def peaks():
+# FP64 rate derived from unit counts and clocks: 152 SMs x 2 FP64 FMA per
+# clock x 2 flop x 2.07 GHz (GB300's FP64 rate, 1/64 of FP32)
+FP64_DERIVED_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def peaks(fp64_measured=None):
     mp = load_json(os.path.join(ROOT, "MEASURED_PEAKS.json"), {}) or {}
     return {
         "hbm_gbs": mp.get("hbm_gbs", 6800.0),
         "hbm_src": "measured" if "hbm_gbs" in mp else "fallback",
-        # FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (GB300's FP64 rate, 1/64 of FP32)
-        "fp64_tflops": 152 * 2 * 2 * 2.07e9 / 1e12,
+        "fp64_tflops": fp64_measured if fp64_measured else FP64_DERIVED_TFLOPS,
+        "fp64_src": (f"measured FP64 FMA probe on this GPU (atm_measure_fp64_rate; derived peak "
+                     f"{FP64_DERIVED_TFLOPS:.3f})" if fp64_measured else
+                     "derived FP64 FMA rate (152 SMs x 2 FMA/clk x 2.07 GHz)"),
     }
 
 
@@ -486,67 +493,91 @@ def initial_condition(w, seed):
     return I.uniform_field((w["n"], w["n"]), seed)
 
 
-def oracle_cycles(workload, fallback):
-    """The oracle's own cycle count to the workload's tolerance (FP64 AT-MGRIT,
-    written by oracle/make_golden.py)."""
-    gold = load_json(os.path.join(ROOT, "tests", "golden", "oracle_histories.json"), {}) or {}
-    key = {"allen_cahn_256": "cfg2_at_k8", "heat1d_127": "cfg1_at_k4"}.get(workload)
-    return gold.get(key, {}).get("iterations", fallback)
-
-
-def oracle_cycle_sample(w, iterations):
-    """CPU baseline: the oracle (as it stands) runs the initial F-relaxation and
-    one V-cycle of the same workload; time-to-solution is scaled to the oracle's
-    own FP64 cycle count."""
+def oracle_cfg(w):
     import oracle
     kind = {"ac": oracle.ALLEN_CAHN, "heat1d": oracle.HEAT1D}[w["kind"]]
     ny = w["n"] if w["kind"] != "heat1d" else 1
-    c = oracle.make_cfg(kind, w["n"], ny, dt=w["dt"], nt=w["nt"], eps=w["eps"], m=w["m"],
-                        k=w["k"], nu=w["nu"], react_exact=[l > 0 for l in range(len(w["m"]) + 1)])
-    u = np.zeros((w["nt"],) + oracle.state_shape(c))
-    u[0] = initial_condition(w, 0)
+    return oracle.make_cfg(kind, w["n"], ny, dt=w["dt"], nt=w["nt"], eps=w["eps"], m=w["m"],
+                           k=w["k"], nu=w["nu"], react_exact=[l > 0 for l in range(len(w["m"]) + 1)])
+
+
+def oracle_sequential_baseline(w, seed):
+    """CPU baseline: the oracle (as it stands) solves the same workload
+    completely by sequential time stepping -- the fixed point every solver
+    converges to (Sec. 2), exact up to rounding -- on one host core.  Returns
+    the baseline entry and the oracle's C-points (every m_0-th state), from
+    which the GPU result's error is stated."""
+    import oracle
+    c = oracle_cfg(w)
+    u0 = initial_condition(w, seed)
     t = time.perf_counter()
-    oracle.solve(c, u, 1, 0.0)
+    u = oracle.sequential(c, u0)
     sec = time.perf_counter() - t
-    est = sec * max(iterations, 1)
-    return {"value": (w["nt"] - 1) / est, "unit": UNIT, "cores": oracle.num_threads(),
-            "kind": "oracle",
-            "sample": f"initial F-relaxation + 1 V-cycle of the oracle on this workload "
-                      f"({sec:.1f} s), scaled to {iterations} cycles"}
+    cps = u[::w["m"][0]].copy()
+    del u
+    return {"value": (w["nt"] - 1) / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one complete solve of this workload by the oracle's sequential time stepping "
+                      f"(FP64, {w['nt'] - 1} steps, {sec:.1f} s, measured; the oracle's AT-MGRIT solve "
+                      f"on all cores is the --impl reference line)"}, cps
 
 
-def run_reference(args, w, world, rank, dist):
-    """--impl reference: the oracle on the host cores, rank 0 only."""
+def error_vs_oracle(solver, w, cps):
+    """Relative L2 error of the GPU iterate against the oracle's sequential
+    solution: every C-point (state by state and over all of them) and the
+    final state."""
+    m0 = w["m"][0]
+    got = np.stack([solver.solution(t, 1).cpu().numpy()[0] for t in range(0, w["nt"], m0)])
+    per = [float(np.linalg.norm(got[i] - cps[i]) / max(np.linalg.norm(cps[i]), 1e-300))
+           for i in range(1, got.shape[0])]
+    tot = float(np.linalg.norm(got[1:] - cps[1:]) / np.linalg.norm(cps[1:]))
+    fin = solver.solution(w["nt"] - 1, 1).cpu().numpy()[0]
+    ref_fin = cps[-1] if (w["nt"] - 1) % m0 == 0 else None
+    out = {"against": "oracle sequential solution (FP64, same initial condition)",
+           "rel_l2_cpoints": tot, "max_rel_l2_per_cpoint": max(per), "cpoints": len(per)}
+    if ref_fin is not None:
+        out["rel_l2_final_state"] = float(np.linalg.norm(fin - ref_fin) / np.linalg.norm(ref_fin))
+    return out
+
+
+def run_reference(args, w, world, rank, dist, budget_s=150.0):
+    """--impl reference: the oracle's AT-MGRIT (FP64, all host cores, the same
+    workload, cycle and tolerance) on rank 0 only.  Each timed step is one
+    complete solve from the zero guess to ||r||_2 <= tol; a solve takes tens of
+    seconds, so the run times as many solves as fit in budget_s (at least one)
+    and reports that count in `steps`.  Warm-up: one V-cycle (untimed)."""
     if rank != 0:
         return
     import oracle
-    iters = oracle_cycles(args.workload, 13)
-    kind = {"ac": oracle.ALLEN_CAHN, "heat1d": oracle.HEAT1D}[w["kind"]]
-    ny = w["n"] if w["kind"] != "heat1d" else 1
-    c = oracle.make_cfg(kind, w["n"], ny, dt=w["dt"], nt=w["nt"], eps=w["eps"], m=w["m"],
-                        k=w["k"], nu=w["nu"], react_exact=[l > 0 for l in range(len(w["m"]) + 1)])
+    c = oracle_cfg(w)
     u0 = initial_condition(w, 0)
-    times = []
-    for s in range(args.warmup + args.steps):
-        u = np.zeros((w["nt"],) + oracle.state_shape(c))
+    u = np.zeros((w["nt"],) + oracle.state_shape(c))
+    u[0] = u0
+    oracle.solve(c, u, 1, 0.0)          # warm-up: pages the iterate in, one cycle
+    times, iters, finals = [], [], []
+    t_start = time.perf_counter()
+    while not times or (len(times) < args.steps and
+                        time.perf_counter() - t_start + float(np.mean(times)) <= budget_s):
+        u[1:] = 0.0
         u[0] = u0
         t = time.perf_counter()
-        oracle.solve(c, u, 1, 0.0)
-        if s >= args.warmup:
-            times.append(time.perf_counter() - t)
+        it, hist = oracle.solve(c, u, w["max_iter"], w["tol"])
+        times.append(time.perf_counter() - t)
+        iters.append(int(it))
+        finals.append(float(hist[-1]))
     sec = float(np.mean(times))
-    ms_solve = sec * iters * 1e3
-    value = (w["nt"] - 1) / (ms_solve / 1e3)
-    sample = (f"each step: initial F-relaxation + 1 V-cycle of the oracle ({sec:.2f} s); "
-              f"time-to-solution = step time x {iters} cycles (the oracle's own count, "
-              f"tests/golden/oracle_histories.json)")
+    value = (w["nt"] - 1) / sec
+    sample = (f"{len(times)} complete AT-MGRIT solves of the oracle (FP64, {oracle.num_threads()} threads, "
+              f"zero guess to ||r||_2 <= {w['tol']:g}: {iters[0]} cycles, final residual {finals[0]:.2e}), "
+              f"measured; warm-up: one V-cycle")
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_solve,
+            "steps": len(times), "warmup": 1, "ms_per_step": sec * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
             "config": {"workload": args.workload, **{k: (list(v) if isinstance(v, tuple) else v)
                                                      for k, v in w.items()},
-                       "algorithm": "at-mgrit", "l2": "inputs larger than L2 (host run)"},
+                       "algorithm": "at", "l2": "inputs larger than L2 (host run)"},
+            "iterations": iters[0], "final_residual": finals[0],
+            "steps_requested": args.steps, "solve_times_s": times,
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -685,7 +716,10 @@ def main():
 
     # roofline of the level-0 propagator application (row + column sweep of
     # every state of one launch table), event-timed during the timed steps
-    pk = peaks()
+    fp64_rate = None
+    if args.precision in ("fp64", "fp32r"):
+        fp64_rate = atm.measure_fp64_rate(solver.stream)
+    pk = peaks(fp64_rate)
     n_val = int(np.prod(shape))
     # states per profiled launch table: the level-0 relaxation launches cover
     # every interval; in the refined mode the profiled table is the FP64
@@ -725,7 +759,7 @@ def main():
         roof = {"bound": "alu", "achieved": achieved, "peak": pk["fp64_tflops"], "unit": "TFLOP/s",
                 "frac": achieved / pk["fp64_tflops"], "traffic": traffic, "kernel": name,
                 "avg_launch_ms": avg_ms, "launches_timed": cnt,
-                "peak_source": "derived FP64 FMA rate (152 SMs x 2 DFMA/clk x 2.07 GHz)",
+                "peak_source": pk["fp64_src"], "frac_of_derived_peak": achieved / FP64_DERIVED_TFLOPS,
                 "algorithmic": f"{fpv} flop/value x {n_val} values x {jobs} states"}
     else:
         nbytes = 2 * n_val * 4 * jobs
@@ -737,9 +771,11 @@ def main():
                 "algorithmic": f"read + write of {jobs} states of {n_val} fp32 values"}
 
     if rank == 0:
-        cpu = None
-        if world == 1 and not args.no_cpu_baseline:
-            cpu = oracle_cycle_sample(w, oracle_cycles(args.workload, int(np.median(iters))))
+        cpu, err = None, None
+        if world == 1 and not args.no_cpu_baseline and args.workload != "allen_cahn_1024":
+            cpu, cps = oracle_sequential_baseline(w, rank)
+            err = error_vs_oracle(solver, w, cps)
+            del cps
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -768,7 +804,7 @@ def main():
                     cycles_with_network_before_fallback=[i for _, i in fallbacks]),
                 "kernels_per_level": [solver.sweep_config(l) for l in range(len(w["m"]) + 1)]
                 if args.algorithm != "seq" else [solver.sweep_config(0)],
-                "roofline": roof, "cpu_baseline": cpu, "clocks": clk}
+                "roofline": roof, "cpu_baseline": cpu, "err_vs_oracle": err, "clocks": clk}
         print(json.dumps(line), flush=True)
     solver.close()
     if dist is not None:

@@ -390,7 +390,8 @@ atm_status atm_set_learned_coarse(atm_handle *h, const float *d_params);
  * per-state pointer table that the regular path keeps in the caller's
  * workspace live instead in static device arrays of this library (32 MiB of
  * intermediate, 64 table entries); every GPU on which the library's kernels
- * are loaded holds them until the process exits.
+ * are loaded holds them until the process exits.  The table is written by a
+ * kernel on cuda_stream; the call makes no host-to-device copy.
  *
  * Callers that need it: code that may not call cudaMalloc at all, such as a
  * component embedded in an application whose memory manager owns the whole
@@ -400,18 +401,30 @@ atm_status atm_set_learned_coarse(atm_handle *h, const float *d_params);
  * Limits: the 2D problems only (ATM_HEAT2D, ATM_ALLEN_CAHN), nx and ny powers
  * of two in [32, 512], nstates <= 64 and nstates * nx * ny * 8 <= 32 MiB;
  * anything larger returns ATM_ERR_INVALID_ARG with the limit in the message.
- * Arithmetic is FP64 whatever solver->precision says.
+ * Arithmetic is FP64 whatever solver->precision says.  A learned coarse
+ * propagator (ATM_PROP_LEARNED, ATM_PROP_LEARNED_CORRECTION) is accepted on
+ * every level but level 1, where the network lives in a handle: level 1 of such
+ * a description returns ATM_ERR_UNSUPPORTED.
  * d_in, d_out: FP64 device arrays of nstates states (they may alias); the work
  * is issued on cuda_stream and the call returns without waiting for it.
- * The first call on a device (with that device current) looks up the device
- * addresses of the static arrays; make that first call before any stream
- * capture on the device.  All calls on a device share the same arrays, so
- * calls that may run at the same time on the GPU (other streams, other host
- * threads) race and must be serialised by the caller.  Nothing in the arrays
- * has to start at zero: each call writes everything it later reads. */
+ * Set-up: the first call on a device (with that device current), and the first
+ * one after the device's context was re-created, looks up the device addresses
+ * of the static arrays; make that first call before any stream capture on the
+ * device.  All calls on a device share the same arrays, so calls that may run
+ * at the same time on the GPU (other streams, other host threads) race and
+ * must be serialised by the caller.  Nothing in the arrays has to start at
+ * zero: each call writes everything it later reads. */
 atm_status atm_apply_propagator_noalloc(const atm_problem *prob, const atm_solver *solver, int level,
                                         const double *d_in, double *d_out, int nstates,
                                         void *cuda_stream);
+
+/* Measured FP64 fused multiply-add throughput of the current device in
+ * TFLOP/s (2 flop per FMA): a kernel of 4 CTAs per SM, 256 threads, eight
+ * independent FMA chains per thread, timed with CUDA events on cuda_stream
+ * (best of three after a warm-up).  The paper has no counterpart; it is the
+ * measured denominator of the FP64 roofline.  Blocks until done; allocates
+ * nothing. */
+atm_status atm_measure_fp64_rate(void *cuda_stream, double *tflops);
 
 /* Message of the calling thread's last error ("" if none). */
 const char *atm_last_error(void);

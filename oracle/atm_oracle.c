@@ -16,7 +16,7 @@
  *   - plain MGRIT (the global coarsest grid solved sequentially), which the
  *     paper states is the k >= N_T + 1 special case (Sec. 2.1, 2.2).
  *
- * Readings where the paper is silent (each is listed in the design notes):
+ * Readings where the paper is silent:
  *   - FAS right-hand side on every coarse level: g^{l+1} = A^{l+1}(v) + R_I r
  *     (standard FAS, the paper's reference for MGRIT); at the coarsest level
  *     the local system's first row is the identity, so a local chain starts at

@@ -85,7 +85,8 @@ EXPORTS = ["atm_workspace_size", "atm_create", "atm_set_initial_condition",
            "atm_last_launch_count", "atm_get_kernel_profile", "atm_apply_propagator_noalloc",
            "atm_nn_param_count", "atm_nn_workspace_size", "atm_nn_apply", "atm_nn_loss_grad",
            "atm_train_learned_coarse", "atm_set_learned_coarse", "atm_batch_solve", "atm_last_error",
-           "atm_get_sweep_config", "atm_set_rhs", "atm_get_newton_stats", "atm_destroy"]
+           "atm_get_sweep_config", "atm_set_rhs", "atm_get_newton_stats", "atm_measure_fp64_rate",
+           "atm_destroy"]
 
 _lib = None
 
@@ -134,6 +135,7 @@ def load(build_if_missing: bool = True):
                                            ctypes.POINTER(TrainResult), vp, ctypes.c_size_t, vp]
     L.atm_set_learned_coarse.argtypes = [vp, vp]
     L.atm_batch_solve.argtypes = [ctypes.POINTER(vp), i, vp, ctypes.POINTER(Result)]
+    L.atm_measure_fp64_rate.argtypes = [vp, ctypes.POINTER(d)]
     L.atm_last_error.restype = ctypes.c_char_p
     L.atm_destroy.argtypes = [vp]
     for name in EXPORTS:
@@ -194,6 +196,15 @@ def workspace_size(problem: Problem, solver: SolverDesc) -> int:
     n = ctypes.c_size_t()
     _check(load().atm_workspace_size(ctypes.byref(problem), ctypes.byref(solver), ctypes.byref(n)))
     return n.value
+
+
+def measure_fp64_rate(stream=None) -> float:
+    """Measured FP64 FMA throughput of the current device (TFLOP/s)."""
+    import torch
+    st = stream if stream is not None else torch.cuda.current_stream()
+    v = ctypes.c_double()
+    _check(load().atm_measure_fp64_rate(ctypes.c_void_p(st.cuda_stream), ctypes.byref(v)))
+    return v.value
 
 
 def _ptr(x) -> int:

@@ -93,6 +93,25 @@ atm_status check_args(const atm_problem *pb, const atm_solver *sv)
     return ATM_OK;
 }
 
+// FP64 FMA throughput probe: every thread runs eight independent FMA chains
+// (enough independent work per SM to keep the FP64 pipe busy); an empty asm
+// statement consumes the result so that the chains are not removed.
+__global__ void __launch_bounds__(256) fp64_fma_probe_kernel(int iters)
+{
+    double a[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = 1.0 + 1e-3 * (threadIdx.x + k);
+    const double b = 0.999999999, c = 1e-9;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) a[k] = fma(a[k], b, c);
+    }
+    double t = 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) t += a[k];
+    asm volatile("" ::"d"(t));
+}
+
 }  // namespace
 
 extern "C" {
@@ -270,6 +289,39 @@ atm_status atm_batch_solve(atm_handle *const *hs, int n, void *cuda_stream, atm_
         if (first == ATM_OK && si != ATM_OK) first = si;
     }
     return first;
+}
+
+atm_status atm_measure_fp64_rate(void *cuda_stream, double *tflops)
+{
+    atm::last_error().clear();
+    if (!tflops) return atm::fail(ATM_ERR_INVALID_ARG, "null tflops");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
+    int dev = 0, sms = 0;
+    ATM_CK(cudaGetDevice(&dev));
+    ATM_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int blocks = 4 * sms, threads = 256, iters = 8192;
+    cudaEvent_t e0, e1;
+    ATM_CK(cudaEventCreate(&e0));
+    ATM_CK(cudaEventCreate(&e1));
+    float best = 0.f;
+    for (int rep = 0; rep < 4; ++rep) {
+        cudaEventRecord(e0, st);
+        fp64_fma_probe_kernel<<<blocks, threads, 0, st>>>(iters);
+        cudaEventRecord(e1, st);
+        cudaError_t e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return atm::fail(ATM_ERR_CUDA, "FP64 probe failed: %s", cudaGetErrorString(e));
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0 && (best == 0.f || ms < best)) best = ms;   // the first run is a warm-up
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *tflops = 2.0 * 8.0 * iters * (double)blocks * threads / (best * 1e-3) / 1e12;
+    return ATM_OK;
 }
 
 const char *atm_last_error(void)

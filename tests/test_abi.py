@@ -21,7 +21,7 @@ def atm():
 def declared_functions():
     text = open(os.path.join(ROOT, "include", "atm.h")).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    names = re.findall(r"\b(atm_[a-z_]+)\s*\(", text)
+    names = re.findall(r"\b(atm_[a-z0-9_]+)\s*\(", text)
     return sorted(set(names))
 
 

@@ -1,6 +1,7 @@
 """atm_apply_propagator_noalloc, the entry point for callers that may not
 allocate device memory (its scratch lives in a static device array of the
-library), against the regular workspace-based atm_apply_propagator.
+library), against the regular workspace-based atm_apply_propagator and against
+the FP64 oracle.
 
 Kept in a file that pytest collects last.  Runs alone in a fresh process as
 well as after the other tests: the first call on the device performs the
@@ -11,7 +12,9 @@ import numpy as np
 import pytest
 
 import atm_inputs as I
+import oracle
 import paper_2107_09596_gb300 as atm
+from helpers import pair, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -23,10 +26,16 @@ def _noalloc(lib, prob, desc, level, x, out, stream):
                                             ctypes.c_void_p(stream.cuda_stream))
 
 
-def test_noalloc_matches_apply_propagator_on_two_calls():
+@pytest.fixture(scope="module")
+def torch():
     import torch
     assert torch.cuda.is_available()
     atm._build.build()
+    atm.load()
+    return torch
+
+
+def test_noalloc_matches_apply_propagator_on_two_calls(torch):
     lib = atm.load()
     prob = atm.make_problem(atm.ALLEN_CAHN, 256, 256, dt=1e-4, nt_points=4097, eps=0.02)
     desc = atm.make_solver(atm.AT_MGRIT, m=(16, 16), k=8, nu=1, precision=atm.FP64)
@@ -45,11 +54,50 @@ def test_noalloc_matches_apply_propagator_on_two_calls():
         for s in range(x.shape[0]):
             rel = np.linalg.norm(g[s] - want[s]) / np.linalg.norm(want[s])
             assert rel <= 1e-13, (level, s, rel)
+    ref.close()
 
 
-def test_noalloc_rejects_requests_beyond_its_limit():
-    import torch
-    atm._build.build()
+def test_noalloc_matches_the_oracle_in_place(torch):
+    """Every level of a three-level Allen-Cahn hierarchy (PR-ADI fine step,
+    split-BE coarse steps with the exact reaction flow) on a 128 x 64 grid,
+    with in == out, against the oracle's propagators; two calls in a row."""
+    lib = atm.load()
+    oc, gp, gs = pair(kind="ac", nx=128, ny=64, lx=1.0, ly=0.5, dt=1e-4, nt=257, m=(4, 4), k=3)
+    stream = torch.cuda.current_stream()
+    for rep in range(2):
+        for level in range(3):
+            x = I.uniform_field((7, 64, 128), 30 + 3 * rep + level, -1.0, 1.0)
+            want = oracle.apply_prop(oc, level, x)
+            buf = torch.as_tensor(x, device="cuda:0")
+            st = _noalloc(lib, gp, gs, level, buf, buf, stream)
+            assert st == 0, lib.atm_last_error().decode()
+            torch.cuda.synchronize()
+            got = buf.cpu().numpy()
+            for s in range(x.shape[0]):
+                assert rel_l2(got[s], want[s]) <= 1e-13, (rep, level, s, rel_l2(got[s], want[s]))
+
+
+def test_noalloc_learned_description(torch):
+    """A learned coarse propagator description: level 2 runs (split-BE, as the
+    handle would), level 1 is rejected with a message naming the network."""
+    lib = atm.load()
+    oc, gp, gs = pair(kind="ac", nx=64, ny=64, dt=1e-4, nt=257, m=(4, 4), k=3)
+    gs.coarse_prop = atm.PROP_LEARNED
+    stream = torch.cuda.current_stream()
+    x = I.uniform_field((3, 64, 64), 40, -1.0, 1.0)
+    buf = torch.as_tensor(x, device="cuda:0")
+    out = torch.empty_like(buf)
+    st = _noalloc(lib, gp, gs, 2, buf, out, stream)
+    assert st == 0, lib.atm_last_error().decode()
+    torch.cuda.synchronize()
+    want = oracle.apply_prop(oc, 2, x)
+    assert rel_l2(out.cpu().numpy(), want) <= 1e-13
+    st = _noalloc(lib, gp, gs, 1, buf, out, stream)
+    assert atm.STATUS[st] == "ATM_ERR_UNSUPPORTED"
+    assert "learned" in lib.atm_last_error().decode()
+
+
+def test_noalloc_rejects_requests_beyond_its_limit(torch):
     lib = atm.load()
     stream = torch.cuda.current_stream()
     prob = atm.make_problem(atm.HEAT2D, 512, 512, dt=1e-4, nt_points=65)
