@@ -482,7 +482,8 @@ def make_desc(atm, w, algorithm, precision, profile, coarse="classical", sweep="
                            coarse_prop={"learned": atm.PROP_LEARNED, "correction": atm.PROP_LEARNED_CORRECTION}.get(
                                coarse, atm.PROP_SPLIT_BE),
                            sweep_kernel={"auto": atm.SWEEP_AUTO, "split": atm.SWEEP_SPLIT,
-                                         "fused": atm.SWEEP_FUSED, "chain": atm.SWEEP_CHAIN}[sweep],
+                                         "fused": atm.SWEEP_FUSED, "chain": atm.SWEEP_CHAIN,
+                                         "persistent": atm.SWEEP_PERSISTENT}[sweep],
                            cpoint_only=cpoint, inner_cycles=inner_cycles, nested=nested, fcycle=fcycle)
     return prob, desc
 
@@ -608,7 +609,7 @@ def main():
                     help="level-1 coarse propagator; 'learned' trains Psi_NN, 'correction' the network of "
                          "Psi_split + N first (untimed)")
     ap.add_argument("--train-steps", type=int, default=2500)
-    ap.add_argument("--sweep-kernel", choices=["auto", "split", "fused", "chain"], default="auto",
+    ap.add_argument("--sweep-kernel", choices=["auto", "split", "fused", "chain", "persistent"], default="auto",
                     help="2D propagator kernels (auto: level 0 autotuned at create time)")
     ap.add_argument("--storage", choices=["cpoint", "full"], default="cpoint",
                     help="level-0 storage: C-points only (default) or every time point")
@@ -671,7 +672,7 @@ def main():
     for _ in range(args.warmup):
         res = step()
     torch.cuda.synchronize(device)
-    prof0 = [solver.kernel_profile(i) for i in range(3)]
+    prof0 = [solver.kernel_profile(i) for i in range(4)]
     clocks = ClockSampler(device.index if device.index is not None else 0)
     barrier(dist, device)
     torch.cuda.synchronize(device)
@@ -694,7 +695,7 @@ def main():
     ms = e0.elapsed_time(e1) / args.steps
     ms = max_over_ranks(dist, ms, device)
     value = world * (w["nt"] - 1) / (ms / 1e3)
-    prof1 = [solver.kernel_profile(i) for i in range(3)]
+    prof1 = [solver.kernel_profile(i) for i in range(4)]
 
     # end to end through host buffers: u0 from pinned host memory in, the final
     # state and the residual history out, copies inside the timed region
@@ -738,9 +739,11 @@ def main():
     if args.precision == "fp32r":
         # the timed table is the FP64 residual pass of the outer loop (split kernels)
         sc = {"kernel": "split", "chunk": 0}
-    if sc["kernel"] == "fused":
-        name = (f"fused_sweep_kernel (level-0 propagator; cluster of {sc['ctas']} CTAs x {sc['threads']} threads, "
-                f"{sc['rows']}-row column segments)")
+    if sc["kernel"] in ("fused", "persistent"):
+        kname = "fused_persist_kernel" if sc["kernel"] == "persistent" else "fused_sweep_kernel"
+        name = (f"{kname} (level-0 propagator; cluster of {sc['ctas']} CTAs x {sc['threads']} threads, "
+                f"{sc['rows']}-row column segments" +
+                (f", {sc['chunk']} resident clusters)" if sc["kernel"] == "persistent" else ")"))
     else:
         name = "row_sweep_kernel+col_sweep_kernel (level-0 propagator" + (
             f", {sc['chunk']} states per launch pair)" if sc["chunk"] else ")")
@@ -751,8 +754,8 @@ def main():
         fpv = FLOPS_PER_VALUE[("row", "pr_react")] + FLOPS_PER_VALUE[("col", "pr")]
     traffic_db = load_json(os.path.join(ROOT, "profiles", "traffic.json"), {}) or {}
     tr = traffic_db.get(f"{args.workload}:{args.precision}:{args.storage}")
-    traffic = (tr["bytes_per_launch"] if tr and tr.get("source_hash") == kernel_source_hash(sc["kernel"] == "fused")
-               else None)
+    traffic = (tr["bytes_per_launch"] if tr and tr.get("source_hash") == kernel_source_hash(
+        sc["kernel"] in ("fused", "persistent")) else None)
     if args.precision in ("fp64", "fp32r"):
         flops = fpv * n_val * jobs
         achieved = flops / (avg_ms / 1e3) / 1e12
@@ -770,6 +773,23 @@ def main():
                 "peak_source": f"{pk['hbm_src']} STREAM copy (MEASURED_PEAKS.json)",
                 "algorithmic": f"read + write of {jobs} states of {n_val} fp32 values"}
 
+    roof32 = None
+    if args.precision == "fp32r" and prof1[3][1] > prof0[3][1]:
+        sci = solver.sweep_config(0)
+        avg32 = (prof1[3][0] - prof0[3][0]) / (prof1[3][1] - prof0[3][1])
+        nb = 3 * n_val * 4 * jobs
+        ach = nb / (avg32 / 1e3) / 1e9
+        tr32 = traffic_db.get(f"{args.workload}:fp32r_inner:{args.storage}")
+        roof32 = {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                  "frac": ach / pk["hbm_gbs"],
+                  "traffic": (tr32["bytes_per_launch"] if tr32 and tr32.get("source_hash") == kernel_source_hash(True)
+                              else None),
+                  "kernel": f"{sci['kernel']} level-0 propagator of the FP32 inner cycles (cluster of "
+                            f"{sci['ctas']} CTAs x {sci['threads']} threads)",
+                  "avg_launch_ms": avg32, "launches_timed": prof1[3][1] - prof0[3][1],
+                  "peak_source": f"{pk['hbm_src']} STREAM copy (MEASURED_PEAKS.json)",
+                  "algorithmic": f"3 fp32 streams per value (input, base of the increment, output) x {n_val} "
+                                 f"values x {jobs} states"}
     if rank == 0:
         cpu, err = None, None
         if world == 1 and not args.no_cpu_baseline and args.workload != "allen_cahn_1024":
@@ -804,7 +824,8 @@ def main():
                     cycles_with_network_before_fallback=[i for _, i in fallbacks]),
                 "kernels_per_level": [solver.sweep_config(l) for l in range(len(w["m"]) + 1)]
                 if args.algorithm != "seq" else [solver.sweep_config(0)],
-                "roofline": roof, "cpu_baseline": cpu, "err_vs_oracle": err, "clocks": clk}
+                "roofline": roof, "roofline_fp32_level0": roof32, "cpu_baseline": cpu, "err_vs_oracle": err,
+                "clocks": clk}
         print(json.dumps(line), flush=True)
     solver.close()
     if dist is not None:

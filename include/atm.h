@@ -102,7 +102,7 @@ enum { ATM_SEQUENTIAL = 0, ATM_MGRIT = 1, ATM_AT_MGRIT = 2 };
 enum { ATM_FP64 = 0, ATM_FP32 = 1, ATM_FP32_REFINED = 2 };
 
 /* 2D propagator kernels (atm_solver.sweep_kernel). */
-enum { ATM_SWEEP_AUTO = 0, ATM_SWEEP_SPLIT = 1, ATM_SWEEP_FUSED = 2, ATM_SWEEP_CHAIN = 3 };
+enum { ATM_SWEEP_AUTO = 0, ATM_SWEEP_SPLIT = 1, ATM_SWEEP_FUSED = 2, ATM_SWEEP_CHAIN = 3, ATM_SWEEP_PERSISTENT = 4 };
 
 #define ATM_MAX_LEVELS 8
 
@@ -147,7 +147,12 @@ typedef struct {
                                          split kernels elsewhere), ATM_SWEEP_CHAIN (as FUSED, and
                                          every F-relaxation runs as one launch in which a cluster
                                          applies an interval's m-1 steps to its state in shared
-                                         memory) */
+                                         memory), ATM_SWEEP_PERSISTENT (the persistent cluster
+                                         kernel on every level: as many clusters as fit on the GPU
+                                         walk the states of a launch, the next state's input
+                                         arriving in a second shared-memory tile while the current
+                                         one is solved).  ATM_SWEEP_AUTO times the split, fused
+                                         and persistent kernels at create time */
     int refine_inner_cycles;          /* ATM_FP32_REFINED: FP32 V-cycles on the correction per FP64
                                          residual, 1..16 (0: 5).  More cycles trade FP64 residual
                                          passes for FP32 cycles while the inner iteration still
@@ -281,7 +286,9 @@ long long atm_last_launch_count(const atm_handle *h);
  * atm_create (needs solver.profile = 1): `which` = 0 row sweeps (implicit in
  * x), 1 column sweeps (implicit in y), 2 whole propagator applications (row +
  * column sweeps of one launch table; the only one for heat1d, and the only
- * one when a sweep runs in several row/column chunks).
+ * one when a sweep runs in several row/column chunks), 3 (ATM_FP32_REFINED)
+ * whole level-0 propagator applications of the FP32 inner cycles (the last
+ * inner cycle of each refinement step; with the host loop only).
  * *total_ms = summed CUDA-event durations, *launches = sweeps timed. */
 atm_status atm_get_kernel_profile(const atm_handle *h, int which, double *total_ms, long long *launches);
 
@@ -290,7 +297,8 @@ atm_status atm_get_kernel_profile(const atm_handle *h, int which, double *total_
  *   cfg[0] kernel: 0 split row + column kernels, 1 fused cluster kernel,
  *          2 learned network, 3 1D line kernel, 4 chain kernel (F-relaxations),
  *          5 Gray-Scott Newton kernel (cfg[1] CTAs resident at most, cfg[2]
- *          threads per CTA, cfg[3] GMRES restart length);
+ *          threads per CTA, cfg[3] GMRES restart length), 6 persistent
+ *          cluster kernel (cfg[4] clusters in its grid);
  *   cfg[1] CTAs per state (fused: cluster size; split: column-kernel CTAs);
  *   cfg[2] threads per CTA (fused) or per column-kernel CTA (split);
  *   cfg[3] rows per column segment (fused) or per column-kernel thread (split);

@@ -86,7 +86,7 @@ atm_status check_args(const atm_problem *pb, const atm_solver *sv)
     if (!pb || !sv) return atm::fail(ATM_ERR_INVALID_ARG, "null problem or solver");
     if (sv->precision != ATM_FP64 && sv->precision != ATM_FP32 && sv->precision != ATM_FP32_REFINED)
         return atm::fail(ATM_ERR_INVALID_ARG, "unknown precision %d", sv->precision);
-    if (sv->sweep_kernel < ATM_SWEEP_AUTO || sv->sweep_kernel > ATM_SWEEP_CHAIN)
+    if (sv->sweep_kernel < ATM_SWEEP_AUTO || sv->sweep_kernel > ATM_SWEEP_PERSISTENT)
         return atm::fail(ATM_ERR_INVALID_ARG, "unknown sweep_kernel %d", sv->sweep_kernel);
     if (sv->refine_inner_cycles < 0 || sv->refine_inner_cycles > 16)
         return atm::fail(ATM_ERR_INVALID_ARG, "refine_inner_cycles must be in [0, 16]");
@@ -94,9 +94,10 @@ atm_status check_args(const atm_problem *pb, const atm_solver *sv)
 }
 
 // FP64 FMA throughput probe: every thread runs eight independent FMA chains
-// (enough independent work per SM to keep the FP64 pipe busy); an empty asm
-// statement consumes the result so that the chains are not removed.
-__global__ void __launch_bounds__(256) fp64_fma_probe_kernel(int iters)
+// (enough independent work per SM to keep the FP64 pipe busy).  The result is
+// stored only when `store` is set (never, in practice), which the compiler
+// cannot know, so the chains are kept.
+__global__ void __launch_bounds__(256) fp64_fma_probe_kernel(int iters, int store, double *sink)
 {
     double a[8];
 #pragma unroll
@@ -109,7 +110,7 @@ __global__ void __launch_bounds__(256) fp64_fma_probe_kernel(int iters)
     double t = 0.0;
 #pragma unroll
     for (int k = 0; k < 8; ++k) t += a[k];
-    asm volatile("" ::"d"(t));
+    if (store) sink[blockIdx.x * blockDim.x + threadIdx.x] = t;
 }
 
 }  // namespace
@@ -224,7 +225,7 @@ long long atm_last_launch_count(const atm_handle *h)
 
 atm_status atm_get_kernel_profile(const atm_handle *h, int which, double *total_ms, long long *launches)
 {
-    if (!h || !total_ms || !launches || which < 0 || which > 2)
+    if (!h || !total_ms || !launches || which < 0 || which > 3)
         return atm::fail(ATM_ERR_INVALID_ARG, "invalid argument");
     *total_ms = h->p->prof_ms[which];
     *launches = h->p->prof_n[which];
@@ -306,9 +307,10 @@ atm_status atm_measure_fp64_rate(void *cuda_stream, double *tflops)
     float best = 0.f;
     for (int rep = 0; rep < 4; ++rep) {
         cudaEventRecord(e0, st);
-        fp64_fma_probe_kernel<<<blocks, threads, 0, st>>>(iters);
+        fp64_fma_probe_kernel<<<blocks, threads, 0, st>>>(iters, 0, nullptr);
+        cudaError_t e = cudaGetLastError();
         cudaEventRecord(e1, st);
-        cudaError_t e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
         if (e != cudaSuccess) {
             cudaEventDestroy(e0);
             cudaEventDestroy(e1);

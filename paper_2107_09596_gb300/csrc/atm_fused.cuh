@@ -242,96 +242,61 @@ __device__ __forceinline__ void warp_line_solve2(float2 (&q)[C], const TriCoef<f
     for (int k = 0; k < C; ++k) q[k] = fma2(f2s(c.pw[C - k]), din, q[k]);
 }
 
-// C = nx / 32 values per lane in the row pass; G CTAs per cluster (state);
-// NT threads per CTA; LS rows per column segment.  Work goes in pairs: a warp
-// solves two adjacent rows at once, a thread two adjacent columns, each pair
-// with packed FP32x2 instructions.  R = ny / G rows per CTA; the column pass
-// has P = NT / (nx / 2) segments per CTA (or nx / (2 NT) column pairs per
-// thread, P = 1); R == P * LS.  cy must be built with chunk length LS.
-template <int C, int G, int NT, int LS, bool PR, bool REACT>
-__global__ void __launch_bounds__(NT) fused_sweep_kernel(const __grid_constant__ SweepArgs<float> a)
-{
-    constexpr int NW = NT / 32;
-    constexpr int NX = 32 * C;
-    constexpr int NXP = NX / 2;                 // column pairs
-    constexpr int P = NT >= NXP ? NT / NXP : 1;
-    constexpr int XPT = NT >= NXP ? 1 : NXP / NT;
-    constexpr int R = P * LS;
-    constexpr int S = G * P;                    // segments per column
-    constexpr int V = C >= 4 ? 4 : C;           // values per shared-memory access in the row pass
-    constexpr int NY = G * R;
-    constexpr int RPI = NT * 4 / NX;            // rows per pass of the CTA over 16-byte pieces
+// Launch-shape constants of the fused kernels.  C = nx / 32 values per lane
+// in the row pass; G CTAs per cluster (state); NT threads per CTA; LS rows per
+// column segment.  Work goes in pairs: a warp solves two adjacent rows at
+// once, a thread two adjacent columns, each pair with packed FP32x2
+// instructions.  R = ny / G rows per CTA; the column pass has P = NT / (nx / 2)
+// segments per CTA (or nx / (2 NT) column pairs per thread, P = 1);
+// R == P * LS.  cy must be built with chunk length LS.
+template <int C, int G, int NT, int LS>
+struct FzShape {
+    static constexpr int NW = NT / 32;
+    static constexpr int NX = 32 * C;
+    static constexpr int NXP = NX / 2;                 // column pairs
+    static constexpr int P = NT >= NXP ? NT / NXP : 1;
+    static constexpr int XPT = NT >= NXP ? 1 : NXP / NT;
+    static constexpr int R = P * LS;
+    static constexpr int S = G * P;                    // segments per column
+    static constexpr int V = C >= 4 ? 4 : C;           // values per shared-memory access in the row pass
+    static constexpr int NY = G * R;
+    static constexpr int RPI = NT * 4 / NX;            // rows per pass of the CTA over 16-byte pieces
+    static constexpr size_t TILE = (size_t)(R + 2) * NX;   // floats of one tile (R rows + 2 halo rows)
     static_assert(R % (2 * NW) == 0, "rows per CTA must be a multiple of twice the warps");
     static_assert((NT * 4) % NX == 0 && (NY & (NY - 1)) == 0, "whole rows per pass, power-of-two ny");
     static_assert(S <= 32, "at most 32 segments per column");
     static_assert(LS <= kMaxChunk, "segment longer than the power table");
+};
 
-    extern __shared__ __align__(16) unsigned char fz_smem[];
-    float *tile = reinterpret_cast<float *>(fz_smem);                       // (R + 2) rows of NX
-    float2 *ce = reinterpret_cast<float2 *>(tile + (size_t)(R + 2) * NX);   // [P][NXP] forward carries
-    float2 *cb = ce + (size_t)P * NXP;                                      // [P][NXP] backward carries
-    float2 *dn = cb + (size_t)P * NXP;                                      // [P][NXP] final backward carries
-    __shared__ double sh[32];
-
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int rank = G > 1 ? (int)cg::this_cluster().block_rank() : 0;
-    const Job<float> jb = a.jobs[blockIdx.y];
-    const int r0 = rank * R;
-    // this thread's 16-byte column piece in every pass over rows
-    const int px = (threadIdx.x * 4) % NX, prow = (threadIdx.x * 4) / NX, pxs = fz_swz(px);
-
-    // 1. load (with halo rows for PR) and react; tile row t = state row r0 - 1 + t.
-    //    Every 16-byte piece of the CTA's rows is requested before any arrives.
-    {
-        const int t_lo = PR ? 0 : 1, t_hi = PR ? R + 2 : R + 1;
-        if (!(REACT && jb.base)) {
-            for (int t = t_lo + prow; t < t_hi; t += RPI) {
-                const int gy = (r0 - 1 + t) & (NY - 1);
-                fz_cp_async16(tile + (size_t)t * NX + pxs, jb.in + (size_t)gy * NX + px);
-            }
-            fz_cp_async_wait_all();
-            if (REACT) {
-                // the same pieces as this thread copied: no barrier needed before
-                for (int t = t_lo + prow; t < t_hi; t += RPI) {
-                    float4 *q4 = reinterpret_cast<float4 *>(tile + (size_t)t * NX + pxs);
-                    const float4 v = *q4;
-                    const float2 lo = react2(make_float2(v.x, v.y), a.react, a.nsub);
-                    const float2 hi = react2(make_float2(v.z, v.w), a.react, a.nsub);
-                    *q4 = make_float4(lo.x, lo.y, hi.x, hi.y);
-                }
-            }
+// Reaction of this thread's own 16-byte pieces of tile rows t_lo .. t_hi - 1
+// (tile row t = state row r0 - 1 + t), in place: the plain reaction, or the
+// increment around a base whose rows sit at the same places of `btile`.
+template <int NX, int RPI, bool INCR>
+__device__ __forceinline__ void fz_react_own(float *tile, const float *btile, const SweepArgs<float> &a, int t_lo,
+                                             int t_hi, int prow, int pxs)
+{
+    for (int t = t_lo + prow; t < t_hi; t += RPI) {
+        float4 *q4 = reinterpret_cast<float4 *>(tile + (size_t)t * NX + pxs);
+        const float4 v = *q4;
+        if constexpr (INCR) {
+            const float4 bb = *reinterpret_cast<const float4 *>(btile + (size_t)t * NX + pxs);
+            *q4 = make_float4(react_delta(bb.x, v.x, a.react, a.nsub), react_delta(bb.y, v.y, a.react, a.nsub),
+                              react_delta(bb.z, v.z, a.react, a.nsub), react_delta(bb.w, v.w, a.react, a.nsub));
         } else {
-            // increments around a base: both streams through registers, U pieces in flight
-            constexpr int U = 4;
-            for (int t0 = t_lo + prow; t0 < t_hi; t0 += RPI * U) {
-                float4 v[U], b[U];
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const int t = t0 + u * RPI;
-                    if (t < t_hi) {
-                        const size_t go = (size_t)((r0 - 1 + t) & (NY - 1)) * NX + px;
-                        v[u] = fz_ld4(jb.in + go);
-                        b[u] = fz_ld4(jb.base + go);
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const int t = t0 + u * RPI;
-                    if (t < t_hi) {
-                        const float4 r = make_float4(react_delta(b[u].x, v[u].x, a.react, a.nsub),
-                                                     react_delta(b[u].y, v[u].y, a.react, a.nsub),
-                                                     react_delta(b[u].z, v[u].z, a.react, a.nsub),
-                                                     react_delta(b[u].w, v[u].w, a.react, a.nsub));
-                        *reinterpret_cast<float4 *>(tile + (size_t)t * NX + pxs) = r;
-                    }
-                }
-            }
+            const float2 lo = react2(make_float2(v.x, v.y), a.react, a.nsub);
+            const float2 hi = react2(make_float2(v.z, v.w), a.react, a.nsub);
+            *q4 = make_float4(lo.x, lo.y, hi.x, hi.y);
         }
     }
-    __syncthreads();
+}
 
-    // 2. row pass: warp w takes tile rows t, t+1 with t = 1 + 2 (g NW + w);
-    //    results go to rows t-1, t (the rows above), read-before-write per group
+// Row pass: warp w takes tile rows t, t+1 with t = 1 + 2 (g NW + w); results
+// go to rows t-1, t (the rows above), read-before-write per group.
+template <int C, int G, int NT, int LS, bool PR>
+__device__ __forceinline__ void fz_row_pass(float *tile, const SweepArgs<float> &a, int lane, int warp)
+{
+    using Z = FzShape<C, G, NT, LS>;
+    constexpr int V = Z::V, NX = Z::NX, NW = Z::NW, R = Z::R;
     const int x0 = lane * C;
     const float2 rx0 = f2s(a.rx0), rx1 = f2s(a.rx1), cy0 = f2s(a.cy0), cy1 = f2s(a.cy1);
 #pragma unroll 1
@@ -383,11 +348,20 @@ __global__ void __launch_bounds__(NT) fused_sweep_kernel(const __grid_constant__
             fz_store<V>(tile + (size_t)t * NX, x0 + i, hi);
         }
     }
-    __syncthreads();
+}
 
-    // 3. column pass on pairs of columns: rows [p LS, p LS + LS) of columns
-    //    (x, x + 1), global segment s = rank P + p
-    const TriCoef<float> &c = a.cy;
+// Column pass on pairs of columns: rows [p LS, p LS + LS) of columns
+// (x, x + 1), global segment s = rank P + p.  Segment carries are combined
+// across the cluster through distributed shared memory; ends with a cluster
+// barrier after which no peer reads this CTA's carries any more.  Leaves the
+// final backward carries in dn (the fix-up rho^(LS-k) din is applied in the
+// epilogue).
+template <int C, int G, int NT, int LS>
+__device__ __forceinline__ void fz_col_pass(float *tile, float2 *ce, float2 *cb, float2 *dn, const TriCoef<float> &c,
+                                            int rank)
+{
+    using Z = FzShape<C, G, NT, LS>;
+    constexpr int NX = Z::NX, NXP = Z::NXP, P = Z::P, XPT = Z::XPT, S = Z::S;
     const float2 rho = f2s(c.rho), mls = f2s(c.scan[0]), inv1m = f2s(c.inv1m);
     const int p = NT >= NXP ? threadIdx.x / NXP : 0;
     const int xb = NT >= NXP ? threadIdx.x % NXP : threadIdx.x;
@@ -432,7 +406,7 @@ __global__ void __launch_bounds__(NT) fused_sweep_kernel(const __grid_constant__
     if constexpr (G > 1) cg::this_cluster().sync(); else __syncthreads();
 #pragma unroll 1
     for (int xi = 0; xi < XPT; ++xi) {
-        const int xp = xb + xi * NT, xs = fz_swz(2 * xp);
+        const int xp = xb + xi * NT;
         float2 tot = f2s(0.f), pre = f2s(0.f);
 #pragma unroll
         for (int j = S - 1; j >= 0; --j) {
@@ -442,31 +416,237 @@ __global__ void __launch_bounds__(NT) fused_sweep_kernel(const __grid_constant__
             if (j == s) pre = tot;
             tot = fma2(mls, tot, ev);
         }
-        // the fix-up x += rho^(LS-k) din is applied in the epilogue
         dn[p * NXP + xp] = fma2(f2s(c.chunk_pw[S - 1 - s]), mul2(tot, inv1m), pre);
     }
     // no CTA leaves (or reuses its carries) while a peer may still read them
     if constexpr (G > 1) cg::this_cluster().sync(); else __syncthreads();
+}
 
-    // 4. epilogue: tile row j = state row r0 + j, finished with the last
-    //    column fix-up rho^(LS-k) din (k = row within its segment)
+// Epilogue: tile row j = state row r0 + j, finished with the last column
+// fix-up rho^(LS-k) din (k = row within its segment); returns this thread's
+// share of sum r^2.
+template <int C, int G, int NT, int LS>
+__device__ __forceinline__ double fz_output(const Job<float> &jb, const float *tile, const float2 *dn,
+                                            const TriCoef<float> &c, int r0, int prow, int px, int pxs, int neg)
+{
+    using Z = FzShape<C, G, NT, LS>;
+    constexpr int NX = Z::NX, NXP = Z::NXP, R = Z::R, RPI = Z::RPI;
     double acc = 0.0;
     if (!jb.g && !jb.h && !jb.sub && jb.out) {
         // plain store of (+-)Phi
         for (int j = prow; j < R; j += RPI) {
             const float4 v = fz_col_final<NX, NXP, LS>(tile, dn, c, j, px, pxs);
-            const float4 o = a.neg ? make_float4(-v.x, -v.y, -v.z, -v.w) : v;
+            const float4 o = neg ? make_float4(-v.x, -v.y, -v.z, -v.w) : v;
             *reinterpret_cast<float4 *>(jb.out + (size_t)(r0 + j) * NX + px) = o;
         }
     } else if (jb.sub) {
-        fz_epilogue<NX, NXP, R, LS, RPI, true>(jb, tile, dn, c, r0, prow, px, pxs, a.neg, acc);
+        fz_epilogue<NX, NXP, R, LS, RPI, true>(jb, tile, dn, c, r0, prow, px, pxs, neg, acc);
     } else {
-        fz_epilogue<NX, NXP, R, LS, RPI, false>(jb, tile, dn, c, r0, prow, px, pxs, a.neg, acc);
+        fz_epilogue<NX, NXP, R, LS, RPI, false>(jb, tile, dn, c, r0, prow, px, pxs, neg, acc);
     }
+    return acc;
+}
+
+// One application of Phi per state: grid (G, states), one cluster per state.
+template <int C, int G, int NT, int LS, bool PR, bool REACT>
+__global__ void __launch_bounds__(NT) fused_sweep_kernel(const __grid_constant__ SweepArgs<float> a)
+{
+    using Z = FzShape<C, G, NT, LS>;
+    constexpr int NX = Z::NX, NXP = Z::NXP, P = Z::P, R = Z::R, NY = Z::NY, RPI = Z::RPI;
+
+    extern __shared__ __align__(16) unsigned char fz_smem[];
+    float *tile = reinterpret_cast<float *>(fz_smem);                       // (R + 2) rows of NX
+    float2 *ce = reinterpret_cast<float2 *>(tile + Z::TILE);                // [P][NXP] forward carries
+    float2 *cb = ce + (size_t)P * NXP;                                      // [P][NXP] backward carries
+    float2 *dn = cb + (size_t)P * NXP;                                      // [P][NXP] final backward carries
+    __shared__ double sh[32];
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int rank = G > 1 ? (int)cg::this_cluster().block_rank() : 0;
+    const Job<float> jb = a.jobs[blockIdx.y];
+    const int r0 = rank * R;
+    // this thread's 16-byte column piece in every pass over rows
+    const int px = (threadIdx.x * 4) % NX, prow = (threadIdx.x * 4) / NX, pxs = fz_swz(px);
+
+    // 1. load (with halo rows for PR) and react; tile row t = state row r0 - 1 + t.
+    //    Every 16-byte piece of the CTA's rows is requested before any arrives.
+    {
+        const int t_lo = PR ? 0 : 1, t_hi = PR ? R + 2 : R + 1;
+        if (!(REACT && jb.base)) {
+            for (int t = t_lo + prow; t < t_hi; t += RPI) {
+                const int gy = (r0 - 1 + t) & (NY - 1);
+                fz_cp_async16(tile + (size_t)t * NX + pxs, jb.in + (size_t)gy * NX + px);
+            }
+            fz_cp_async_wait_all();
+            // the same pieces as this thread copied: no barrier needed before
+            if (REACT) fz_react_own<NX, RPI, false>(tile, nullptr, a, t_lo, t_hi, prow, pxs);
+        } else {
+            // increments around a base: both streams through registers, U pieces in flight
+            constexpr int U = 4;
+            for (int t0 = t_lo + prow; t0 < t_hi; t0 += RPI * U) {
+                float4 v[U], b[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int t = t0 + u * RPI;
+                    if (t < t_hi) {
+                        const size_t go = (size_t)((r0 - 1 + t) & (NY - 1)) * NX + px;
+                        v[u] = fz_ld4(jb.in + go);
+                        b[u] = fz_ld4(jb.base + go);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int t = t0 + u * RPI;
+                    if (t < t_hi) {
+                        const float4 r = make_float4(react_delta(b[u].x, v[u].x, a.react, a.nsub),
+                                                     react_delta(b[u].y, v[u].y, a.react, a.nsub),
+                                                     react_delta(b[u].z, v[u].z, a.react, a.nsub),
+                                                     react_delta(b[u].w, v[u].w, a.react, a.nsub));
+                        *reinterpret_cast<float4 *>(tile + (size_t)t * NX + pxs) = r;
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+
+    // 2. row pass, 3. column pass (cluster), 4. epilogue
+    fz_row_pass<C, G, NT, LS, PR>(tile, a, lane, warp);
+    __syncthreads();
+    fz_col_pass<C, G, NT, LS>(tile, ce, cb, dn, a.cy, rank);
+    const double acc = fz_output<C, G, NT, LS>(jb, tile, dn, a.cy, r0, prow, px, pxs, a.neg);
     if (a.partials) {
         const double tsum = block_sum(acc, sh);
         if (threadIdx.x == 0) a.partials[(size_t)blockIdx.y * G + rank] = tsum;
     }
+}
+
+// Shared-memory bytes of a persistent launch: two tiles (the state being
+// solved and the next one arriving) and the carry arrays.
+__host__ __device__ constexpr size_t persist_smem_bytes(int nx, int R, int P)
+{
+    return 2 * (size_t)(R + 2) * nx * sizeof(float) + 3 * (size_t)P * nx * sizeof(float);
+}
+
+// L2 prefetch of `bytes` contiguous bytes (16-byte aligned, multiple of 16).
+__device__ __forceinline__ void fz_prefetch_l2(const void *p, unsigned bytes)
+{
+    asm volatile("{\n\t.reg .u64 ga;\n\tcvta.to.global.u64 ga, %0;\n\t"
+                 "cp.async.bulk.prefetch.L2.global [ga], %1;\n\t}" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// L2 prefetch of the rows of a state that one CTA reads: its own R rows from
+// r0 and (halo) the rows above and below, periodic in y.  Threads 0..2 issue.
+template <int NX, int NY, int R>
+__device__ __forceinline__ void fz_prefetch_rows(const float *st, int r0, bool halo)
+{
+    if (!st) return;
+    const int t = threadIdx.x;
+    if (t == 0) fz_prefetch_l2(st + (size_t)r0 * NX, (unsigned)(R * NX * sizeof(float)));
+    if (halo && t == 1) fz_prefetch_l2(st + (size_t)((r0 + NY - 1) & (NY - 1)) * NX, (unsigned)(NX * sizeof(float)));
+    if (halo && t == 2) fz_prefetch_l2(st + (size_t)((r0 + R) & (NY - 1)) * NX, (unsigned)(NX * sizeof(float)));
+}
+
+// This thread's pieces of the input rows of a state (tile row t = state row
+// r0 - 1 + t) requested into `dst` as one cp.async group.
+template <int NX, int NY, int RPI>
+__device__ __forceinline__ void fz_request(float *dst, const float *src, int r0, int t_lo, int t_hi, int prow,
+                                           int px, int pxs)
+{
+    for (int t = t_lo + prow; t < t_hi; t += RPI) {
+        const int gy = (r0 - 1 + t) & (NY - 1);
+        fz_cp_async16(dst + (size_t)t * NX + pxs, src + (size_t)gy * NX + px);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// One state of fused_persist_kernel: its input is in (or arriving in)
+// `tile`; `other` is free.  Kept out of line so that the register allocation
+// of one state's work is that of fused_sweep_kernel (inlined into the job loop,
+// loop-invariant coefficient loads would be hoisted and held in registers
+// across states).
+template <int C, int G, int NT, int LS, bool PR, bool REACT>
+__device__ __noinline__ void fz_persist_job(const SweepArgs<float> &a, int job, int nxt, float *tile, float *other,
+                                            float2 *ce, float2 *cb, float2 *dn, double *sh)
+{
+    using Z = FzShape<C, G, NT, LS>;
+    constexpr int NX = Z::NX, R = Z::R, NY = Z::NY, RPI = Z::RPI;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int rank = G > 1 ? (int)cg::this_cluster().block_rank() : 0;
+    const int r0 = rank * R;
+    const int px = (threadIdx.x * 4) % NX, prow = (threadIdx.x * 4) / NX, pxs = fz_swz(px);
+    const int t_lo = PR ? 0 : 1, t_hi = PR ? R + 2 : R + 1;
+    const Job<float> jb = a.jobs[job];
+    const bool incr = REACT && jb.base;
+    // every thread is done with `other` (the previous state's tile)
+    __syncthreads();
+    if (incr) fz_request<NX, NY, RPI>(other, jb.base, r0, t_lo, t_hi, prow, px, pxs);
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    // own pieces only (the same as this thread requested): no barrier before
+    if (incr) fz_react_own<NX, RPI, true>(tile, other, a, t_lo, t_hi, prow, pxs);
+    else if (REACT) fz_react_own<NX, RPI, false>(tile, nullptr, a, t_lo, t_hi, prow, pxs);
+    __syncthreads();
+    // the next state's input into the other tile, its remaining operands into L2
+    if (nxt >= 0) {
+        const Job<float> jn = a.jobs[nxt];
+        fz_request<NX, NY, RPI>(other, jn.in, r0, t_lo, t_hi, prow, px, pxs);
+        if (REACT) fz_prefetch_rows<NX, NY, R>(jn.base, r0, PR);
+        if (threadIdx.x == 32) {
+            const unsigned rb = (unsigned)(R * NX * sizeof(float));
+            const size_t ro = (size_t)r0 * NX;
+            if (jn.g) fz_prefetch_l2(jn.g + ro, rb);
+            if (jn.h) fz_prefetch_l2(jn.h + ro, rb);
+            if (jn.sub) fz_prefetch_l2(jn.sub + ro, rb);
+        }
+    }
+    fz_row_pass<C, G, NT, LS, PR>(tile, a, lane, warp);
+    __syncthreads();
+    fz_col_pass<C, G, NT, LS>(tile, ce, cb, dn, a.cy, rank);
+    const double acc = fz_output<C, G, NT, LS>(jb, tile, dn, a.cy, r0, prow, px, pxs, a.neg);
+    if (a.partials) {
+        const double tsum = block_sum(acc, sh);
+        if (threadIdx.x == 0) a.partials[(size_t)job * G + rank] = tsum;
+    }
+}
+
+// Persistent form of fused_sweep_kernel: grid (G, clusters), as many clusters
+// as fit on the device at once; cluster y applies Phi to states y, y + gridDim.y,
+// ...  While state i is solved, the next state's input rows arrive in the
+// second tile (cp.async, issued before the row pass of state i) and its other
+// operands (base, addends, subtrahend) are prefetched into L2, so that the
+// loads of a state overlap the arithmetic of the one before.  Results equal
+// fused_sweep_kernel's (the same phases in the same order).  Registers are
+// capped so that the CTAs the shared memory allows stay resident (MINB per SM).
+template <int C, int G, int NT, int LS, bool PR, bool REACT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) fused_persist_kernel(const __grid_constant__ SweepArgs<float> a, int njobs)
+{
+    using Z = FzShape<C, G, NT, LS>;
+    constexpr int NX = Z::NX, NXP = Z::NXP, P = Z::P, R = Z::R, NY = Z::NY, RPI = Z::RPI;
+
+    extern __shared__ __align__(16) unsigned char fz_smem[];
+    float *tiles = reinterpret_cast<float *>(fz_smem);                      // 2 x (R + 2) rows of NX
+    float2 *ce = reinterpret_cast<float2 *>(tiles + 2 * Z::TILE);
+    float2 *cb = ce + (size_t)P * NXP;
+    float2 *dn = cb + (size_t)P * NXP;
+    __shared__ double sh[32];
+
+    const int stride = gridDim.y;
+    int job = blockIdx.y;
+    if (job < njobs) {
+        const int rank = G > 1 ? (int)cg::this_cluster().block_rank() : 0;
+        const int px = (threadIdx.x * 4) % NX, prow = (threadIdx.x * 4) / NX;
+        fz_request<NX, NY, RPI>(tiles, a.jobs[job].in, rank * R, PR ? 0 : 1, PR ? R + 2 : R + 1, prow, px,
+                                fz_swz(px));
+    }
+    int cur = 0;
+#pragma unroll 1
+    for (; job < njobs; job += stride) {
+        const int nxt = job + stride < njobs ? job + stride : -1;
+        fz_persist_job<C, G, NT, LS, PR, REACT>(a, job, nxt, tiles + (size_t)cur * Z::TILE,
+                                                tiles + (size_t)(cur ^ 1) * Z::TILE, ce, cb, dn, sh);
+        cur ^= 1;
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
 }  // namespace atm

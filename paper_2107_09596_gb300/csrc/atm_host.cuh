@@ -134,23 +134,32 @@ template <typename T>
 struct FusedVariant {
     SweepFn<T> fn = nullptr;
     void (*cfn)(SweepArgs<T>, int) = nullptr;   // chain kernel (chain shapes only)
+    void (*pfn)(SweepArgs<T>, int) = nullptr;   // persistent kernel (persistent shapes only)
     int G = 1, NT = 256, LS = 16;
     size_t smem = 0;
+    int nclusters = 0;                          // persistent: clusters resident at once (the grid)
     TriCoef<T> cy{};
 };
 
 // Fused launch shapes for an nx x ny grid (none in FP64, whose sweeps are
-// bound by the FP64 pipe, not by the intermediate's traffic).  The first
-// entry is the default; the level-0 autotuner times them all.
+// bound by the FP64 pipe, not by the intermediate's traffic): one launch
+// per state (`kind` 0), the persistent kernel (1), both (2), or the chain
+// kernel (3).  The first entry is the default; the autotuner times them all.
 template <typename T>
-inline std::vector<FusedVariant<T>> fused_variants(int nx, int ny, bool pr, bool react, double ay, bool chains = false)
+inline std::vector<FusedVariant<T>> fused_variants(int nx, int ny, bool pr, bool react, double ay, int kind)
 {
     std::vector<FusedVariant<T>> v;
     if constexpr (sizeof(T) == 4) {
-        for (const FusedShape &f : chains ? chain_shapes(nx, ny, pr, react) : fused_shapes(nx, ny, pr, react)) {
+        std::vector<FusedShape> shapes;
+        if (kind == 3) shapes = chain_shapes(nx, ny, pr, react);
+        if (kind == 0 || kind == 2) shapes = fused_shapes(nx, ny, pr, react);
+        if (kind == 1 || kind == 2)
+            for (const FusedShape &f : persist_shapes(nx, ny, pr, react)) shapes.push_back(f);
+        for (const FusedShape &f : shapes) {
             FusedVariant<T> fv;
             fv.fn = f.fn;
             fv.cfn = f.cfn;
+            fv.pfn = f.pfn;
             fv.G = f.G;
             fv.NT = f.NT;
             fv.LS = f.LS;
@@ -255,8 +264,10 @@ inline LevelOp<T> make_level_op(const atm_problem &pb, const atm_solver &sv, int
     // padded tile rows: 16 bytes after every 128 bytes (see row_sweep_kernel)
     const size_t pitch = (size_t)pb.nx + (size_t)(pb.nx * sizeof(T) / 128) * (16 / sizeof(T));
     op.row_smem = pr ? (size_t)(op.rows_per_cta + 2) * pitch * sizeof(T) : 0;
-    if (sv.sweep_kernel != ATM_SWEEP_SPLIT) op.fused = fused_variants<T>(pb.nx, pb.ny, pr, react, ay);
-    if (sv.sweep_kernel == ATM_SWEEP_CHAIN) op.chains = fused_variants<T>(pb.nx, pb.ny, pr, react, ay, true);
+    if (sv.sweep_kernel != ATM_SWEEP_SPLIT)
+        op.fused = fused_variants<T>(pb.nx, pb.ny, pr, react, ay,
+                                     sv.sweep_kernel == ATM_SWEEP_PERSISTENT ? 1 : sv.sweep_kernel == ATM_SWEEP_AUTO ? 2 : 0);
+    if (sv.sweep_kernel == ATM_SWEEP_CHAIN) op.chains = fused_variants<T>(pb.nx, pb.ny, pr, react, ay, 3);
     return op;
 }
 
@@ -301,8 +312,10 @@ struct PlanBase {
     cudaStream_t st = nullptr;
     std::vector<double> hist;
     long long launches = 0;
-    double prof_ms[3] = {0, 0, 0};   // row sweeps, column sweeps, whole propagator applications
-    long long prof_n[3] = {0, 0, 0};
+    // row sweeps, column sweeps, whole propagator applications, and (refined
+    // mode) whole applications of the FP32 inner cycles' level-0 sweeps
+    double prof_ms[4] = {0, 0, 0, 0};
+    long long prof_n[4] = {0, 0, 0, 0};
     int chunk = 0;                    // states per row+column launch pair on level 0 (0 = all)
     float tuned_ms = 0;               // autotuned sweep time
     virtual ~PlanBase() {}
@@ -605,7 +618,8 @@ struct Plan : PlanBase {
         Lv.chz = Lv.chains.empty() ? -1 : 0;
         // fused on coarse levels by default, and on level 0 when asked for
         // (ATM_SWEEP_AUTO lets the autotuner decide level 0 at create time)
-        Lv.fz = (!Lv.fused.empty() && (l > 0 || sv.sweep_kernel == ATM_SWEEP_FUSED || sv.sweep_kernel == ATM_SWEEP_CHAIN))
+        Lv.fz = (!Lv.fused.empty() && (l > 0 || sv.sweep_kernel == ATM_SWEEP_FUSED || sv.sweep_kernel == ATM_SWEEP_CHAIN ||
+                                        sv.sweep_kernel == ATM_SWEEP_PERSISTENT))
                     ? 0 : -1;
     }
 
@@ -1162,7 +1176,9 @@ struct Plan : PlanBase {
         build_phases();
         nprof = 0;
         if (sv.profile) {
-            Phase &ph = role == ROLE_OUTER ? resid_full : (sv.algorithm == ATM_SEQUENTIAL) ? seq : passA;
+            Phase &ph = role == ROLE_OUTER ? resid_full
+                        : role == ROLE_INNER ? inner_cycle
+                        : (sv.algorithm == ATM_SEQUENTIAL) ? seq : passA;
             for (LaunchRec &r : ph)
                 if (r.type == L_SWEEP && r.level == 0 && nprof < 64) r.prof_slot = nprof++;
         }
@@ -1306,6 +1322,32 @@ struct Plan : PlanBase {
             a.partials = part;
             Lv.row<<<dim3(1, njobs), 32, 0, st>>>(a);
             if (prof) cudaEventRecordWithFlags(pev[4 * slot + 3], st, cudaEventRecordExternal);
+            return;
+        }
+        if (Lv.fz >= 0 && Lv.fused[Lv.fz].pfn) {
+            // persistent: the resident clusters walk all states of the launch
+            const FusedVariant<T> &fv = Lv.fused[Lv.fz];
+            a.cy = fv.cy;
+            a.jobs = djobs;
+            a.partials = part;
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(fv.G, njobs < fv.nclusters ? njobs : fv.nclusters);
+            cfg.blockDim = dim3(fv.NT);
+            cfg.dynamicSmemBytes = fv.smem;
+            cfg.stream = st;
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = fv.G;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            if (cudaLaunchKernelEx(&cfg, fv.pfn, a, njobs) != cudaSuccess) launch_failed = true;
+            if (prof) {
+                cudaEventRecordWithFlags(pev[4 * slot + 1], st, cudaEventRecordExternal);
+                cudaEventRecordWithFlags(pev[4 * slot + 2], st, cudaEventRecordExternal);
+                cudaEventRecordWithFlags(pev[4 * slot + 3], st, cudaEventRecordExternal);
+            }
             return;
         }
         if (Lv.fz >= 0) {
@@ -1570,8 +1612,8 @@ struct Plan : PlanBase {
     atm_status prepare_shapes(std::vector<FusedVariant<T>> &shapes, bool chain, int *fz = nullptr)
     {
         std::vector<FusedVariant<T>> keep;
-        for (const FusedVariant<T> &fv : shapes) {
-            const void *fn = chain ? (const void *)fv.cfn : (const void *)fv.fn;
+        for (FusedVariant<T> fv : shapes) {
+            const void *fn = chain ? (const void *)fv.cfn : fv.pfn ? (const void *)fv.pfn : (const void *)fv.fn;
             ATM_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fv.smem));
             // the whole unified L1/shared array as shared memory: room for 3 CTAs of ~70 KB
             ATM_CK(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
@@ -1592,6 +1634,7 @@ struct Plan : PlanBase {
                 cudaGetLastError();
                 nclusters = 0;
             }
+            fv.nclusters = nclusters;
             if (nclusters > 0) keep.push_back(fv);
         }
         shapes = keep;
@@ -2197,7 +2240,8 @@ struct Plan : PlanBase {
             cfg[0] = 4; cfg[1] = f.G; cfg[2] = f.NT; cfg[3] = f.LS;
         } else if (Lv.fz >= 0) {
             const FusedVariant<T> &f = Lv.fused[Lv.fz];
-            cfg[0] = 1; cfg[1] = f.G; cfg[2] = f.NT; cfg[3] = f.LS;
+            cfg[0] = f.pfn ? 6 : 1; cfg[1] = f.G; cfg[2] = f.NT; cfg[3] = f.LS;
+            if (f.pfn) cfg[4] = f.nclusters;
         } else {
             cfg[0] = 0; cfg[1] = pb.nx / 32; cfg[2] = 32 * Lv.col_warps; cfg[3] = Lv.col_chunk;
             cfg[4] = level == 0 ? chunk : 0;
@@ -2278,7 +2322,6 @@ struct RefinedPlan : PlanBase {
         inner.pb = p;
         inner.sv = s;
         inner.sv.use_graph = 0;
-        inner.sv.profile = 0;
         inner.role = ROLE_INNER;
         inner.st = stream;
         const size_t nsp = (p.kind == ATM_HEAT1D) ? (size_t)p.nx : (size_t)p.nx * p.ny;
@@ -2447,6 +2490,7 @@ struct RefinedPlan : PlanBase {
             double r = 0;
             ATM_TRY(outer.read_norm(&r));
             if (outer.nprof) outer.collect_profile();
+            if (inner.nprof) inner.collect_profile();
             hist.push_back(r);
             ++it;
             if (r < rmin) rmin = r;
@@ -2473,6 +2517,8 @@ struct RefinedPlan : PlanBase {
             prof_ms[q] = outer.prof_ms[q];
             prof_n[q] = outer.prof_n[q];
         }
+        prof_ms[3] = inner.prof_ms[2];
+        prof_n[3] = inner.prof_n[2];
         if (res) *res = R;
         return status;
     }

@@ -45,8 +45,9 @@ def sequential():
     return u[::M0].copy()
 
 
-def test_bench_path_matches_the_oracle_sequential_solution(torch, sequential):
-    prob, desc = bench.make_desc(atm, W, "at", atm.FP32_REFINED, profile=True, cpoint=True)
+@pytest.mark.parametrize("sweep", ["auto", "persistent"])
+def test_bench_path_matches_the_oracle_sequential_solution(torch, sequential, sweep):
+    prob, desc = bench.make_desc(atm, W, "at", atm.FP32_REFINED, profile=True, cpoint=True, sweep=sweep)
     s = atm.Solver(prob, desc)
     s.set_initial_condition(torch.as_tensor(bench.initial_condition(W, 0), device="cuda:0"))
     res = s.solve()
