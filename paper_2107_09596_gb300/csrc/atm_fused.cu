@@ -24,23 +24,25 @@ void add_shape(std::vector<FusedShape> &v, bool pr, bool react)
 
 // MINB: CTAs per SM that the shape's shared memory allows (registers are
 // capped to match).
-template <int C, int G, int NT, int LS>
+template <int C, int G, int NT, int LS, bool DB>
 void add_persist(std::vector<FusedShape> &v, bool pr, bool react)
 {
     constexpr int NXP = 16 * C;
     constexpr int PP = NT >= NXP ? NT / NXP : 1;
-    constexpr size_t SM = persist_smem_bytes(32 * C, PP * LS, PP) + 1024;
+    constexpr size_t SM = persist_smem_bytes(32 * C, PP * LS, PP, DB) + 1024;
     constexpr int BY_SMEM = (int)((227 * 1024) / SM);
     constexpr int BY_THREADS = 2048 / NT;
     constexpr int M0 = BY_SMEM < BY_THREADS ? BY_SMEM : BY_THREADS;
     constexpr int MINB = M0 < 1 ? 1 : (M0 > 4 ? 4 : M0);
     FusedShape f;
-    if (pr) f.pfn = react ? fused_persist_kernel<C, G, NT, LS, true, true, MINB> : fused_persist_kernel<C, G, NT, LS, true, false, MINB>;
-    else f.pfn = react ? fused_persist_kernel<C, G, NT, LS, false, true, MINB> : fused_persist_kernel<C, G, NT, LS, false, false, MINB>;
+    if (pr) f.pfn = react ? fused_persist_kernel<C, G, NT, LS, true, true, MINB, DB>
+                          : fused_persist_kernel<C, G, NT, LS, true, false, MINB, DB>;
+    else f.pfn = react ? fused_persist_kernel<C, G, NT, LS, false, true, MINB, DB>
+                       : fused_persist_kernel<C, G, NT, LS, false, false, MINB, DB>;
     f.G = G;
     f.NT = NT;
     f.LS = LS;
-    f.smem = persist_smem_bytes(32 * C, PP * LS, PP);
+    f.smem = persist_smem_bytes(32 * C, PP * LS, PP, DB);
     v.push_back(f);
 }
 
@@ -88,23 +90,26 @@ std::vector<FusedShape> chain_shapes(int nx, int ny, bool pr, bool react)
 
 std::vector<FusedShape> persist_shapes(int nx, int ny, bool pr, bool react)
 {
+    // single-buffered shapes first (the residency of the one-launch-per-state
+    // kernel), then double-buffered ones
     std::vector<FusedShape> v;
     if (nx == 64 && ny == 64) {
-        add_persist<2, 1, 256, 8>(v, pr, react);
-        add_persist<2, 2, 256, 4>(v, pr, react);
+        add_persist<2, 1, 256, 8, false>(v, pr, react);
+        add_persist<2, 2, 256, 4, true>(v, pr, react);
     }
     if (nx == 128 && ny == 128) {
-        add_persist<4, 2, 256, 16>(v, pr, react);
-        add_persist<4, 4, 256, 8>(v, pr, react);
+        add_persist<4, 2, 256, 16, false>(v, pr, react);
+        add_persist<4, 4, 256, 8, true>(v, pr, react);
     }
     if (nx == 256 && ny == 256) {
-        add_persist<8, 8, 256, 16>(v, pr, react);
-        add_persist<8, 16, 256, 8>(v, pr, react);
-        add_persist<8, 8, 512, 8>(v, pr, react);
-        add_persist<8, 4, 256, 32>(v, pr, react);
+        add_persist<8, 4, 256, 32, false>(v, pr, react);
+        add_persist<8, 8, 256, 16, false>(v, pr, react);
+        add_persist<8, 4, 512, 16, false>(v, pr, react);
+        add_persist<8, 8, 256, 16, true>(v, pr, react);
     }
     if (nx == 512 && ny == 512) {
-        add_persist<16, 16, 512, 16>(v, pr, react);
+        add_persist<16, 16, 256, 32, false>(v, pr, react);
+        add_persist<16, 16, 512, 16, true>(v, pr, react);
     }
     return v;
 }

@@ -290,6 +290,39 @@ __device__ __forceinline__ void fz_react_own(float *tile, const float *btile, co
     }
 }
 
+// Increments around a base (the reaction increment of the refined mode's
+// inner cycles): input and base of this thread's pieces through registers, U
+// pieces in flight, the increment stored to the tile.
+template <int NX, int NY, int RPI>
+__device__ __forceinline__ void fz_load_incr(float *tile, const Job<float> &jb, const SweepArgs<float> &a, int r0,
+                                             int t_lo, int t_hi, int prow, int px, int pxs)
+{
+    constexpr int U = 4;
+    for (int t0 = t_lo + prow; t0 < t_hi; t0 += RPI * U) {
+        float4 v[U], b[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int t = t0 + u * RPI;
+            if (t < t_hi) {
+                const size_t go = (size_t)((r0 - 1 + t) & (NY - 1)) * NX + px;
+                v[u] = fz_ld4(jb.in + go);
+                b[u] = fz_ld4(jb.base + go);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int t = t0 + u * RPI;
+            if (t < t_hi) {
+                const float4 r = make_float4(react_delta(b[u].x, v[u].x, a.react, a.nsub),
+                                             react_delta(b[u].y, v[u].y, a.react, a.nsub),
+                                             react_delta(b[u].z, v[u].z, a.react, a.nsub),
+                                             react_delta(b[u].w, v[u].w, a.react, a.nsub));
+                *reinterpret_cast<float4 *>(tile + (size_t)t * NX + pxs) = r;
+            }
+        }
+    }
+}
+
 // Row pass: warp w takes tile rows t, t+1 with t = 1 + 2 (g NW + w); results
 // go to rows t-1, t (the rows above), read-before-write per group.
 template <int C, int G, int NT, int LS, bool PR>
@@ -481,31 +514,7 @@ __global__ void __launch_bounds__(NT) fused_sweep_kernel(const __grid_constant__
             // the same pieces as this thread copied: no barrier needed before
             if (REACT) fz_react_own<NX, RPI, false>(tile, nullptr, a, t_lo, t_hi, prow, pxs);
         } else {
-            // increments around a base: both streams through registers, U pieces in flight
-            constexpr int U = 4;
-            for (int t0 = t_lo + prow; t0 < t_hi; t0 += RPI * U) {
-                float4 v[U], b[U];
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const int t = t0 + u * RPI;
-                    if (t < t_hi) {
-                        const size_t go = (size_t)((r0 - 1 + t) & (NY - 1)) * NX + px;
-                        v[u] = fz_ld4(jb.in + go);
-                        b[u] = fz_ld4(jb.base + go);
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const int t = t0 + u * RPI;
-                    if (t < t_hi) {
-                        const float4 r = make_float4(react_delta(b[u].x, v[u].x, a.react, a.nsub),
-                                                     react_delta(b[u].y, v[u].y, a.react, a.nsub),
-                                                     react_delta(b[u].z, v[u].z, a.react, a.nsub),
-                                                     react_delta(b[u].w, v[u].w, a.react, a.nsub));
-                        *reinterpret_cast<float4 *>(tile + (size_t)t * NX + pxs) = r;
-                    }
-                }
-            }
+            fz_load_incr<NX, NY, RPI>(tile, jb, a, r0, t_lo, t_hi, prow, px, pxs);
         }
     }
     __syncthreads();
@@ -521,11 +530,11 @@ __global__ void __launch_bounds__(NT) fused_sweep_kernel(const __grid_constant__
     }
 }
 
-// Shared-memory bytes of a persistent launch: two tiles (the state being
-// solved and the next one arriving) and the carry arrays.
-__host__ __device__ constexpr size_t persist_smem_bytes(int nx, int R, int P)
+// Shared-memory bytes of a persistent launch: one or (DB) two tiles (the
+// state being solved and the next one arriving) and the carry arrays.
+__host__ __device__ constexpr size_t persist_smem_bytes(int nx, int R, int P, bool db)
 {
-    return 2 * (size_t)(R + 2) * nx * sizeof(float) + 3 * (size_t)P * nx * sizeof(float);
+    return (db ? 2 : 1) * (size_t)(R + 2) * nx * sizeof(float) + 3 * (size_t)P * nx * sizeof(float);
 }
 
 // L2 prefetch of `bytes` contiguous bytes (16-byte aligned, multiple of 16).
@@ -536,12 +545,12 @@ __device__ __forceinline__ void fz_prefetch_l2(const void *p, unsigned bytes)
 }
 
 // L2 prefetch of the rows of a state that one CTA reads: its own R rows from
-// r0 and (halo) the rows above and below, periodic in y.  Threads 0..2 issue.
+// r0 and (halo) the rows above and below, periodic in y.  Threads t0..t0+2 issue.
 template <int NX, int NY, int R>
-__device__ __forceinline__ void fz_prefetch_rows(const float *st, int r0, bool halo)
+__device__ __forceinline__ void fz_prefetch_rows(const float *st, int r0, bool halo, int t0)
 {
     if (!st) return;
-    const int t = threadIdx.x;
+    const int t = threadIdx.x - t0;
     if (t == 0) fz_prefetch_l2(st + (size_t)r0 * NX, (unsigned)(R * NX * sizeof(float)));
     if (halo && t == 1) fz_prefetch_l2(st + (size_t)((r0 + NY - 1) & (NY - 1)) * NX, (unsigned)(NX * sizeof(float)));
     if (halo && t == 2) fz_prefetch_l2(st + (size_t)((r0 + R) & (NY - 1)) * NX, (unsigned)(NX * sizeof(float)));
@@ -565,7 +574,7 @@ __device__ __forceinline__ void fz_request(float *dst, const float *src, int r0,
 // of one state's work is that of fused_sweep_kernel (inlined into the job loop,
 // loop-invariant coefficient loads would be hoisted and held in registers
 // across states).
-template <int C, int G, int NT, int LS, bool PR, bool REACT>
+template <int C, int G, int NT, int LS, bool PR, bool REACT, bool DB>
 __device__ __noinline__ void fz_persist_job(const SweepArgs<float> &a, int job, int nxt, float *tile, float *other,
                                             float2 *ce, float2 *cb, float2 *dn, double *sh)
 {
@@ -578,19 +587,32 @@ __device__ __noinline__ void fz_persist_job(const SweepArgs<float> &a, int job, 
     const int t_lo = PR ? 0 : 1, t_hi = PR ? R + 2 : R + 1;
     const Job<float> jb = a.jobs[job];
     const bool incr = REACT && jb.base;
-    // every thread is done with `other` (the previous state's tile)
+    // every thread is done with `other` (the previous state's tile), or with
+    // `tile` (single buffer: the previous state)
     __syncthreads();
-    if (incr) fz_request<NX, NY, RPI>(other, jb.base, r0, t_lo, t_hi, prow, px, pxs);
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
-    // own pieces only (the same as this thread requested): no barrier before
-    if (incr) fz_react_own<NX, RPI, true>(tile, other, a, t_lo, t_hi, prow, pxs);
-    else if (REACT) fz_react_own<NX, RPI, false>(tile, nullptr, a, t_lo, t_hi, prow, pxs);
+    if constexpr (DB) {
+        if (incr) fz_request<NX, NY, RPI>(other, jb.base, r0, t_lo, t_hi, prow, px, pxs);
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        // own pieces only (the same as this thread requested): no barrier before
+        if (incr) fz_react_own<NX, RPI, true>(tile, other, a, t_lo, t_hi, prow, pxs);
+        else if (REACT) fz_react_own<NX, RPI, false>(tile, nullptr, a, t_lo, t_hi, prow, pxs);
+    } else {
+        if (incr) {
+            fz_load_incr<NX, NY, RPI>(tile, jb, a, r0, t_lo, t_hi, prow, px, pxs);
+        } else {
+            fz_request<NX, NY, RPI>(tile, jb.in, r0, t_lo, t_hi, prow, px, pxs);
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+            if (REACT) fz_react_own<NX, RPI, false>(tile, nullptr, a, t_lo, t_hi, prow, pxs);
+        }
+    }
     __syncthreads();
-    // the next state's input into the other tile, its remaining operands into L2
+    // the next state's input into the other tile (double buffer) or into L2
+    // (single buffer), its remaining operands into L2
     if (nxt >= 0) {
         const Job<float> jn = a.jobs[nxt];
-        fz_request<NX, NY, RPI>(other, jn.in, r0, t_lo, t_hi, prow, px, pxs);
-        if (REACT) fz_prefetch_rows<NX, NY, R>(jn.base, r0, PR);
+        if constexpr (DB) fz_request<NX, NY, RPI>(other, jn.in, r0, t_lo, t_hi, prow, px, pxs);
+        else if (threadIdx.x >= 64 && threadIdx.x < 96) fz_prefetch_rows<NX, NY, R>(jn.in, r0, PR, 64);
+        if (REACT) fz_prefetch_rows<NX, NY, R>(jn.base, r0, PR, 0);
         if (threadIdx.x == 32) {
             const unsigned rb = (unsigned)(R * NX * sizeof(float));
             const size_t ro = (size_t)r0 * NX;
@@ -611,28 +633,29 @@ __device__ __noinline__ void fz_persist_job(const SweepArgs<float> &a, int job, 
 
 // Persistent form of fused_sweep_kernel: grid (G, clusters), as many clusters
 // as fit on the device at once; cluster y applies Phi to states y, y + gridDim.y,
-// ...  While state i is solved, the next state's input rows arrive in the
-// second tile (cp.async, issued before the row pass of state i) and its other
-// operands (base, addends, subtrahend) are prefetched into L2, so that the
-// loads of a state overlap the arithmetic of the one before.  Results equal
+// ...  While state i is solved, the next state's input rows arrive in a
+// second tile (DB: cp.async, issued before the row pass of state i; costs a
+// second tile of shared memory) or in L2 (single buffer: a bulk prefetch),
+// and its other operands (base, addends, subtrahend) are prefetched into L2,
+// so that the loads of a state overlap the arithmetic of the one before.  Results equal
 // fused_sweep_kernel's (the same phases in the same order).  Registers are
 // capped so that the CTAs the shared memory allows stay resident (MINB per SM).
-template <int C, int G, int NT, int LS, bool PR, bool REACT, int MINB>
+template <int C, int G, int NT, int LS, bool PR, bool REACT, int MINB, bool DB>
 __global__ void __launch_bounds__(NT, MINB) fused_persist_kernel(const __grid_constant__ SweepArgs<float> a, int njobs)
 {
     using Z = FzShape<C, G, NT, LS>;
     constexpr int NX = Z::NX, NXP = Z::NXP, P = Z::P, R = Z::R, NY = Z::NY, RPI = Z::RPI;
 
     extern __shared__ __align__(16) unsigned char fz_smem[];
-    float *tiles = reinterpret_cast<float *>(fz_smem);                      // 2 x (R + 2) rows of NX
-    float2 *ce = reinterpret_cast<float2 *>(tiles + 2 * Z::TILE);
+    float *tiles = reinterpret_cast<float *>(fz_smem);                      // (1 or 2) x (R + 2) rows of NX
+    float2 *ce = reinterpret_cast<float2 *>(tiles + (DB ? 2 : 1) * Z::TILE);
     float2 *cb = ce + (size_t)P * NXP;
     float2 *dn = cb + (size_t)P * NXP;
     __shared__ double sh[32];
 
     const int stride = gridDim.y;
     int job = blockIdx.y;
-    if (job < njobs) {
+    if (DB && job < njobs) {
         const int rank = G > 1 ? (int)cg::this_cluster().block_rank() : 0;
         const int px = (threadIdx.x * 4) % NX, prow = (threadIdx.x * 4) / NX;
         fz_request<NX, NY, RPI>(tiles, a.jobs[job].in, rank * R, PR ? 0 : 1, PR ? R + 2 : R + 1, prow, px,
@@ -642,9 +665,9 @@ __global__ void __launch_bounds__(NT, MINB) fused_persist_kernel(const __grid_co
 #pragma unroll 1
     for (; job < njobs; job += stride) {
         const int nxt = job + stride < njobs ? job + stride : -1;
-        fz_persist_job<C, G, NT, LS, PR, REACT>(a, job, nxt, tiles + (size_t)cur * Z::TILE,
-                                                tiles + (size_t)(cur ^ 1) * Z::TILE, ce, cb, dn, sh);
-        cur ^= 1;
+        fz_persist_job<C, G, NT, LS, PR, REACT, DB>(a, job, nxt, tiles + (size_t)cur * Z::TILE,
+                                                    tiles + (size_t)(cur ^ 1) * Z::TILE, ce, cb, dn, sh);
+        if (DB) cur ^= 1;
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
 }

@@ -1179,8 +1179,9 @@ struct Plan : PlanBase {
             Phase &ph = role == ROLE_OUTER ? resid_full
                         : role == ROLE_INNER ? inner_cycle
                         : (sv.algorithm == ATM_SEQUENTIAL) ? seq : passA;
+            const int cap = role == ROLE_INNER ? 16 : 64;
             for (LaunchRec &r : ph)
-                if (r.type == L_SWEEP && r.level == 0 && nprof < 64) r.prof_slot = nprof++;
+                if (r.type == L_SWEEP && r.level == 0 && nprof < cap) r.prof_slot = nprof++;
         }
         d_jobs = take<Job<T>>(jobs.size() + 1);
         d_ajobs = take<AxpyJob<T>>(ajobs.size() + 1);
@@ -1343,11 +1344,7 @@ struct Plan : PlanBase {
             cfg.attrs = at;
             cfg.numAttrs = 1;
             if (cudaLaunchKernelEx(&cfg, fv.pfn, a, njobs) != cudaSuccess) launch_failed = true;
-            if (prof) {
-                cudaEventRecordWithFlags(pev[4 * slot + 1], st, cudaEventRecordExternal);
-                cudaEventRecordWithFlags(pev[4 * slot + 2], st, cudaEventRecordExternal);
-                cudaEventRecordWithFlags(pev[4 * slot + 3], st, cudaEventRecordExternal);
-            }
+            if (prof) cudaEventRecordWithFlags(pev[4 * slot + 3], st, cudaEventRecordExternal);
             return;
         }
         if (Lv.fz >= 0) {
@@ -1371,11 +1368,7 @@ struct Plan : PlanBase {
                 cfg.numAttrs = 1;
                 if (cudaLaunchKernelEx(&cfg, fv.fn, a) != cudaSuccess) launch_failed = true;
             }
-            if (prof) {
-                cudaEventRecordWithFlags(pev[4 * slot + 1], st, cudaEventRecordExternal);
-                cudaEventRecordWithFlags(pev[4 * slot + 2], st, cudaEventRecordExternal);
-                cudaEventRecordWithFlags(pev[4 * slot + 3], st, cudaEventRecordExternal);
-            }
+            if (prof) cudaEventRecordWithFlags(pev[4 * slot + 3], st, cudaEventRecordExternal);
             return;
         }
         const int cs = chunk_size(l, njobs);
@@ -2369,7 +2362,13 @@ struct RefinedPlan : PlanBase {
         outer.convert_to_T_other(outer.lv[0].u, inner.ubase, n);
         outer.convert_to_T_other(outer.r_full, inner.lv[0].g, n);
         cudaMemsetAsync(inner.lv[0].u, 0, n * sizeof(float), st);
-        for (int c = 0; c < inner_cycles(); ++c) inner.run(inner.inner_cycle);
+        // profile events (if any) only in the last inner cycle: fewer event nodes
+        const bool ne = inner.no_events;
+        for (int c = 0; c < inner_cycles(); ++c) {
+            inner.no_events = ne || c + 1 < inner_cycles();
+            inner.run(inner.inner_cycle);
+        }
+        inner.no_events = ne;
         int blocks = (int)((n + 255) / 256);
         if (blocks > 4096) blocks = 4096;
         refine_update_kernel<<<blocks, 256, 0, st>>>(outer.lv[0].u, inner.lv[0].u, n);
