@@ -47,6 +47,13 @@ WORKLOADS = {
                             tol=1e-2, max_iter=30),
 }
 
+# Arithmetic forms (--precision): FP64; FP32; FP32 propagation inside the FP64
+# refinement loop; the same with the FP64 residual pass's fine propagator in
+# float-float (pairs of FP32, ~48-bit significands); FP64 with that fine
+# propagator.
+PRECISIONS = {"fp64": lambda a: a.FP64, "fp32": lambda a: a.FP32, "fp32r": lambda a: a.FP32_REFINED,
+              "fp32rf": lambda a: a.FP32_REFINED_FF, "fp64f": lambda a: a.FP64_FF}
+
 # Textbook flops per grid value of one sweep kernel:
 # PR explicit term 5, periodic tridiagonal solve 7 (Thomas 5 + rank-one
 # periodic correction 2), split-BE right-hand side 0, reaction substep 5,
@@ -603,8 +610,9 @@ def main():
                     help="gray_scott_128: only one level-0 and one level-1 Newton launch on 255 states "
                          "(the profiling case)")
     ap.add_argument("--algorithm", choices=["at", "mgrit", "seq"], default="at")
-    ap.add_argument("--precision", choices=["fp64", "fp32", "fp32r"], default="fp32r",
-                    help="fp32r: FP32 propagation with FP64 refinement (the fastest form that reaches 1e-8)")
+    ap.add_argument("--precision", choices=sorted(PRECISIONS), default="fp32r",
+                    help="fp32r: FP32 propagation with FP64 refinement; fp32rf: the same with the FP64 residual "
+                         "pass in float-float (pairs of FP32); fp64f: FP64 with the fine propagator in float-float")
     ap.add_argument("--coarse", choices=["classical", "learned", "correction"], default="classical",
                     help="level-1 coarse propagator; 'learned' trains Psi_NN, 'correction' the network of "
                          "Psi_split + N first (untimed)")
@@ -650,7 +658,7 @@ def main():
     device = torch.device("cuda", local)
     torch.cuda.set_device(device)
     atm._build.build()
-    prec = {"fp64": atm.FP64, "fp32": atm.FP32, "fp32r": atm.FP32_REFINED}[args.precision]
+    prec = PRECISIONS[args.precision](atm)
     learned_info = None
     if args.coarse in ("learned", "correction"):
         nn_params, learned_info = train_learned(atm, w, device, args.train_steps,
@@ -715,81 +723,90 @@ def main():
     e2e_ms = max_over_ranks(dist, e2e_ms, device)
     state_bytes = int(np.prod(shape)) * 8
 
-    # roofline of the level-0 propagator application (row + column sweep of
-    # every state of one launch table), event-timed during the timed steps
+    # rooflines of the event-timed level-0 propagator launch tables (every
+    # state of one launch): the solver's level-0 sweeps (FP64, FP32) or, in
+    # the refined modes, the FP64 residual pass and the FP32 inner cycles'
+    # level-0 sweeps; `roofline` is the group with the larger share of the step
+    refined = args.precision in ("fp32r", "fp32rf")
     fp64_rate = None
     if args.precision in ("fp64", "fp32r"):
         fp64_rate = atm.measure_fp64_rate(solver.stream)
     pk = peaks(fp64_rate)
     n_val = int(np.prod(shape))
     # states per profiled launch table: the level-0 relaxation launches cover
-    # every interval; in the refined mode the profiled table is the FP64
-    # residual of every time point
+    # every interval; in the refined mode with full storage the FP64 pass
+    # takes the residual of every time point
     jobs = {"allen_cahn_256": 256, "heat1d_127": 128, "allen_cahn_1024": 2048}[args.workload]
-    if args.precision == "fp32r" and args.storage == "full":
+    if refined and args.storage == "full":
         jobs = w["nt"] - 1
     if args.algorithm == "seq":
         jobs = 1
-    tot = prof1[2][0] - prof0[2][0]
-    cnt = prof1[2][1] - prof0[2][1]
-    avg_ms = tot / max(cnt, 1)
-    if not avg_ms > 0:
-        raise RuntimeError("kernel profile recorded no launches")
-    sc = solver.sweep_config(0)
-    if args.precision == "fp32r":
-        # the timed table is the FP64 residual pass of the outer loop (split kernels)
-        sc = {"kernel": "split", "chunk": 0}
-    if sc["kernel"] in ("fused", "persistent"):
-        kname = "fused_persist_kernel" if sc["kernel"] == "persistent" else "fused_sweep_kernel"
-        name = (f"{kname} (level-0 propagator; cluster of {sc['ctas']} CTAs x {sc['threads']} threads, "
-                f"{sc['rows']}-row column segments" +
-                (f", {sc['chunk']} resident clusters)" if sc["kernel"] == "persistent" else ")"))
-    else:
-        name = "row_sweep_kernel+col_sweep_kernel (level-0 propagator" + (
-            f", {sc['chunk']} states per launch pair)" if sc["chunk"] else ")")
-    if w["kind"] == "heat1d":
-        fpv = FLOPS_PER_VALUE[("row", "heat1d")]
-        name = "row_sweep_kernel (level-0 propagator)"
-    else:
-        fpv = FLOPS_PER_VALUE[("row", "pr_react")] + FLOPS_PER_VALUE[("col", "pr")]
     traffic_db = load_json(os.path.join(ROOT, "profiles", "traffic.json"), {}) or {}
-    tr = traffic_db.get(f"{args.workload}:{args.precision}:{args.storage}")
-    traffic = (tr["bytes_per_launch"] if tr and tr.get("source_hash") == kernel_source_hash(
-        sc["kernel"] in ("fused", "persistent")) else None)
-    if args.precision in ("fp64", "fp32r"):
-        flops = fpv * n_val * jobs
-        achieved = flops / (avg_ms / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": pk["fp64_tflops"], "unit": "TFLOP/s",
-                "frac": achieved / pk["fp64_tflops"], "traffic": traffic, "kernel": name,
-                "avg_launch_ms": avg_ms, "launches_timed": cnt,
-                "peak_source": pk["fp64_src"], "frac_of_derived_peak": achieved / FP64_DERIVED_TFLOPS,
-                "algorithmic": f"{fpv} flop/value x {n_val} values x {jobs} states"}
-    else:
-        nbytes = 2 * n_val * 4 * jobs
-        achieved = nbytes / (avg_ms / 1e3) / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / pk["hbm_gbs"], "traffic": traffic, "kernel": name,
-                "avg_launch_ms": avg_ms, "launches_timed": cnt,
-                "peak_source": f"{pk['hbm_src']} STREAM copy (MEASURED_PEAKS.json)",
-                "algorithmic": f"read + write of {jobs} states of {n_val} fp32 values"}
 
-    roof32 = None
-    if args.precision == "fp32r" and prof1[3][1] > prof0[3][1]:
-        sci = solver.sweep_config(0)
-        avg32 = (prof1[3][0] - prof0[3][0]) / (prof1[3][1] - prof0[3][1])
-        nb = 3 * n_val * 4 * jobs
-        ach = nb / (avg32 / 1e3) / 1e9
-        tr32 = traffic_db.get(f"{args.workload}:fp32r_inner:{args.storage}")
-        roof32 = {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                  "frac": ach / pk["hbm_gbs"],
-                  "traffic": (tr32["bytes_per_launch"] if tr32 and tr32.get("source_hash") == kernel_source_hash(True)
-                              else None),
-                  "kernel": f"{sci['kernel']} level-0 propagator of the FP32 inner cycles (cluster of "
-                            f"{sci['ctas']} CTAs x {sci['threads']} threads)",
-                  "avg_launch_ms": avg32, "launches_timed": prof1[3][1] - prof0[3][1],
-                  "peak_source": f"{pk['hbm_src']} STREAM copy (MEASURED_PEAKS.json)",
-                  "algorithmic": f"3 fp32 streams per value (input, base of the increment, output) x {n_val} "
-                                 f"values x {jobs} states"}
+    def stored_traffic(key, fused):
+        tr = traffic_db.get(key)
+        return tr["bytes_per_launch"] if tr and tr.get("source_hash") == kernel_source_hash(fused) else None
+
+    def kernel_name(sc, what):
+        k = sc["kernel"]
+        if k in ("fused", "persistent"):
+            kn = "fused_persist_kernel" if k == "persistent" else "fused_sweep_kernel"
+            return (f"{kn} ({what}; cluster of {sc['ctas']} CTAs x {sc['threads']} threads, {sc['rows']}-row "
+                    f"column segments" + (f", {sc['chunk']} resident clusters)" if k == "persistent" else ")"))
+        if k == "float-float":
+            return (f"df_sweep_kernel ({what}, float-float; cluster of {sc['ctas']} CTAs x {sc['threads']} "
+                    f"threads, {sc['rows']}-row column segments)")
+        if w["kind"] == "heat1d":
+            return f"row_sweep_kernel ({what})"
+        return f"row_sweep_kernel+col_sweep_kernel ({what}" + (
+            f", {sc['chunk']} states per launch pair)" if sc.get("chunk") else ")")
+
+    def roofline(which, sc, what, fp64_pipe, streams, desc, traffic_key, per_step_factor):
+        tot = prof1[which][0] - prof0[which][0]
+        cnt = prof1[which][1] - prof0[which][1]
+        if cnt <= 0 or not tot > 0:
+            return None
+        avg = tot / cnt
+        fusedk = sc["kernel"] in ("fused", "persistent")
+        base = {"kernel": kernel_name(sc, what), "avg_launch_ms": avg, "launches_timed": cnt,
+                "traffic": stored_traffic(traffic_key, fusedk),
+                "share_of_step": tot / args.steps * per_step_factor / ms}
+        if fp64_pipe:
+            fpv = (FLOPS_PER_VALUE[("row", "heat1d")] if w["kind"] == "heat1d" else
+                   FLOPS_PER_VALUE[("row", "pr_react")] + FLOPS_PER_VALUE[("col", "pr")])
+            ach = fpv * n_val * jobs / (avg / 1e3) / 1e12
+            return dict(base, bound="alu", achieved=ach, peak=pk["fp64_tflops"], unit="TFLOP/s",
+                        frac=ach / pk["fp64_tflops"], peak_source=pk["fp64_src"],
+                        frac_of_derived_peak=ach / FP64_DERIVED_TFLOPS,
+                        algorithmic=f"{fpv} flop/value x {n_val} values x {jobs} states")
+        nb = streams * n_val * jobs
+        ach = nb / (avg / 1e3) / 1e9
+        return dict(base, bound="hbm", achieved=ach, peak=pk["hbm_gbs"], unit="GB/s", frac=ach / pk["hbm_gbs"],
+                    peak_source=f"{pk['hbm_src']} STREAM copy (MEASURED_PEAKS.json)",
+                    algorithmic=f"{desc} x {n_val} values x {jobs} states")
+
+    if refined:
+        sco = solver.sweep_config(-1)
+        ff = args.precision == "fp32rf"
+        r_outer = roofline(2, sco, "FP64 residual pass, level-0 propagator", not ff, 20,
+                           "20 bytes per value (fp64 input, fp64 output, fp32 copy of the output)",
+                           f"{args.workload}:{args.precision}:{args.storage}", 1.0)
+        r_inner = roofline(3, solver.sweep_config(0), "FP32 inner cycles, level-0 propagator", False, 12,
+                           "12 bytes per value (fp32 input, base of the increment, output)",
+                           f"{args.workload}:fp32r_inner:{args.storage}",
+                           float(args.inner_cycles or 5))
+        cands = [r for r in (r_outer, r_inner) if r]
+    else:
+        fp64p = args.precision == "fp64"
+        sb = 8 if args.precision in ("fp64", "fp64f") else 4
+        cands = [r for r in [roofline(2, solver.sweep_config(0), "level-0 propagator", fp64p, 2 * sb,
+                                      f"{2 * sb} bytes per value (input, output)",
+                                      f"{args.workload}:{args.precision}:{args.storage}", 1.0)] if r]
+    if not cands:
+        raise RuntimeError("kernel profile recorded no launches")
+    cands.sort(key=lambda r: -r["share_of_step"])
+    roof = cands[0]
+    roof_other = cands[1] if len(cands) > 1 else None
     if rank == 0:
         cpu, err = None, None
         if world == 1 and not args.no_cpu_baseline and args.workload != "allen_cahn_1024":
@@ -799,7 +816,8 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": {"fp64": "f64", "fp32": "f32", "fp32r": "f32+f64"}[args.precision],
+                "dtype": {"fp64": "f64", "fp32": "f32", "fp32r": "f32+f64", "fp64f": "f32x2",
+                          "fp32rf": "f32+f32x2"}[args.precision],
                 "data": "synthetic",
                 "config": {"workload": args.workload,
                            **{k: (list(v) if isinstance(v, tuple) else v) for k, v in w.items()},
@@ -807,10 +825,11 @@ def main():
                            "algorithm": args.algorithm, "parallelism": f"{world} independent problems",
                            "sweep_kernel": args.sweep_kernel, "storage": args.storage, "nested": args.nested,
                            "cycle": "F" if args.fcycle else "V",
-                           "inner_cycles": (args.inner_cycles or 5) if args.precision == "fp32r" else None,
+                           "inner_cycles": (args.inner_cycles or 5) if refined else None,
                            "l2": "working set larger than L2 (workspace %.2f GB; one level-0 launch reads and "
                                  "writes %.0f MB)" % (atm.workspace_size(prob, desc) / 1e9,
                                                       2 * jobs * n_val * (4 if args.precision == "fp32" else 8) / 1e6)},
+                "precision": args.precision,
                 "iterations": int(np.median(iters)), "time_to_solution_ms": ms,
                 "final_residual": float(res["final_residual"]),
                 "residual_history": [float(v) for v in solver.residual_history()][:64],
@@ -824,7 +843,7 @@ def main():
                     cycles_with_network_before_fallback=[i for _, i in fallbacks]),
                 "kernels_per_level": [solver.sweep_config(l) for l in range(len(w["m"]) + 1)]
                 if args.algorithm != "seq" else [solver.sweep_config(0)],
-                "roofline": roof, "roofline_fp32_level0": roof32, "cpu_baseline": cpu, "err_vs_oracle": err,
+                "roofline": roof, "roofline_other": roof_other, "cpu_baseline": cpu, "err_vs_oracle": err,
                 "clocks": clk}
         print(json.dumps(line), flush=True)
     solver.close()

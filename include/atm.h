@@ -98,8 +98,15 @@ enum { ATM_SEQUENTIAL = 0, ATM_MGRIT = 1, ATM_AT_MGRIT = 2 };
 
 /* Arithmetic of the sweep: FP64 throughout; FP32 throughout (residual norm
  * accumulated in FP64); FP32 propagation inside an FP64 defect-correction
- * loop (FP64 residual, correction and norm). */
-enum { ATM_FP64 = 0, ATM_FP32 = 1, ATM_FP32_REFINED = 2 };
+ * loop (FP64 residual, correction and norm).  The _FF forms evaluate the
+ * fine (level-0) propagator of the FP64 arithmetic in float-float: each value
+ * an unevaluated sum of two FP32 numbers (about 48 significant bits, relative
+ * rounding ~2^-48 per operation against FP64's 2^-53), run on the FP32 pipes,
+ * with FP64 storage, FP64 inputs and outputs and FP64 norms; ATM_FP64_FF is
+ * ATM_FP64 with that fine propagator, ATM_FP32_REFINED_FF is ATM_FP32_REFINED
+ * whose FP64 residual pass uses it.  Available for the 2D periodic problems on
+ * 64^2, 128^2, 256^2 and 512^2 grids (the FP64 kernels elsewhere). */
+enum { ATM_FP64 = 0, ATM_FP32 = 1, ATM_FP32_REFINED = 2, ATM_FP64_FF = 3, ATM_FP32_REFINED_FF = 4 };
 
 /* 2D propagator kernels (atm_solver.sweep_kernel). */
 enum { ATM_SWEEP_AUTO = 0, ATM_SWEEP_SPLIT = 1, ATM_SWEEP_FUSED = 2, ATM_SWEEP_CHAIN = 3, ATM_SWEEP_PERSISTENT = 4 };
@@ -131,7 +138,8 @@ typedef struct {
     int coarse_reaction;              /* Allen-Cahn reaction on levels >= 1: ATM_REACT_EXACT or ATM_REACT_SUBSTEPS */
     double tol;                       /* stop when the residual 2-norm <= tol */
     int max_iter;                     /* maximum V-cycles */
-    int precision;                    /* ATM_FP64 | ATM_FP32 | ATM_FP32_REFINED */
+    int precision;                    /* ATM_FP64 | ATM_FP32 | ATM_FP32_REFINED | ATM_FP64_FF |
+                                         ATM_FP32_REFINED_FF */
     int use_graph;                    /* 0: direct launches; 1: each cycle is a captured CUDA graph
                                          (the host reads the residual after every cycle); 2: the
                                          whole solve is one graph launch whose conditional WHILE
@@ -298,12 +306,14 @@ atm_status atm_get_kernel_profile(const atm_handle *h, int which, double *total_
  *          2 learned network, 3 1D line kernel, 4 chain kernel (F-relaxations),
  *          5 Gray-Scott Newton kernel (cfg[1] CTAs resident at most, cfg[2]
  *          threads per CTA, cfg[3] GMRES restart length), 6 persistent
- *          cluster kernel (cfg[4] clusters in its grid);
+ *          cluster kernel (cfg[4] clusters in its grid), 7 float-float
+ *          cluster kernel (the _FF precisions' fine propagator);
  *   cfg[1] CTAs per state (fused: cluster size; split: column-kernel CTAs);
  *   cfg[2] threads per CTA (fused) or per column-kernel CTA (split);
  *   cfg[3] rows per column segment (fused) or per column-kernel thread (split);
  *   cfg[4] level 0, split: states per row/column launch pair (0 = all).
- * The refined mode reports its FP32 inner cycle. */
+ * The refined modes report their FP32 inner cycle; level -1 there gives the
+ * FP64 residual pass's level-0 kernel. */
 atm_status atm_get_sweep_config(const atm_handle *h, int level, int *cfg);
 
 /* Gray-Scott (ATM_GRAY_SCOTT): counters of the nonlinear solves since

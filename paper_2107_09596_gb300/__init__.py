@@ -19,7 +19,7 @@ HEAT1D, HEAT2D, ALLEN_CAHN, GRAY_SCOTT = 0, 1, 2, 3
 PROP_SPLIT_BE, PROP_PR_ADI, PROP_LEARNED, PROP_LEARNED_CORRECTION = 0, 1, 2, 3
 REACT_EXACT, REACT_SUBSTEPS = 0, 1
 SEQUENTIAL, MGRIT, AT_MGRIT = 0, 1, 2
-FP64, FP32, FP32_REFINED = 0, 1, 2
+FP64, FP32, FP32_REFINED, FP64_FF, FP32_REFINED_FF = 0, 1, 2, 3, 4
 SWEEP_AUTO, SWEEP_SPLIT, SWEEP_FUSED, SWEEP_CHAIN, SWEEP_PERSISTENT = 0, 1, 2, 3, 4
 STAGE_F_RELAX, STAGE_C_RELAX, STAGE_RESTRICT, STAGE_COARSEST, STAGE_CORRECT = range(5)
 ARRAY_U, ARRAY_V, ARRAY_R, ARRAY_G = range(4)
@@ -357,7 +357,8 @@ class Solver:
         """Kernels of a level's propagator: dict(kernel, ctas, threads, rows, chunk)."""
         cfg = (ctypes.c_int * 5)()
         _check(load().atm_get_sweep_config(self.handle, level, cfg))
-        names = {0: "split", 1: "fused", 2: "learned", 3: "line1d", 4: "chain", 5: "newton", 6: "persistent"}
+        names = {0: "split", 1: "fused", 2: "learned", 3: "line1d", 4: "chain", 5: "newton", 6: "persistent",
+                 7: "float-float"}
         return dict(kernel=names.get(cfg[0], str(cfg[0])), ctas=cfg[1], threads=cfg[2], rows=cfg[3], chunk=cfg[4])
 
     def newton_stats(self):

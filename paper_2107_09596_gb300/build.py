@@ -22,7 +22,7 @@ NVCC_FLAGS = [
 
 
 def sources():
-    return [os.path.join(SRC_DIR, f) for f in ("atm_api.cu", "atm_noalloc.cu", "atm_nn.cu", "atm_fused.cu")]
+    return [os.path.join(SRC_DIR, f) for f in ("atm_api.cu", "atm_noalloc.cu", "atm_nn.cu", "atm_fused.cu", "atm_df.cu")]
 
 
 def _newest_input() -> float:

@@ -84,7 +84,7 @@ atm_status refined_create(const atm_problem *pb, const atm_solver *sv, void *ws,
 atm_status check_args(const atm_problem *pb, const atm_solver *sv)
 {
     if (!pb || !sv) return atm::fail(ATM_ERR_INVALID_ARG, "null problem or solver");
-    if (sv->precision != ATM_FP64 && sv->precision != ATM_FP32 && sv->precision != ATM_FP32_REFINED)
+    if (sv->precision < ATM_FP64 || sv->precision > ATM_FP32_REFINED_FF)
         return atm::fail(ATM_ERR_INVALID_ARG, "unknown precision %d", sv->precision);
     if (sv->sweep_kernel < ATM_SWEEP_AUTO || sv->sweep_kernel > ATM_SWEEP_PERSISTENT)
         return atm::fail(ATM_ERR_INVALID_ARG, "unknown sweep_kernel %d", sv->sweep_kernel);
@@ -122,8 +122,9 @@ atm_status atm_workspace_size(const atm_problem *prob, const atm_solver *solver,
     atm::last_error().clear();
     ATM_TRY(check_args(prob, solver));
     if (!bytes) return atm::fail(ATM_ERR_INVALID_ARG, "null bytes");
-    if (solver->precision == ATM_FP32_REFINED) return refined_size(prob, solver, bytes);
-    return solver->precision == ATM_FP64 ? plan_size<double>(prob, solver, bytes) : plan_size<float>(prob, solver, bytes);
+    if (solver->precision == ATM_FP32_REFINED || solver->precision == ATM_FP32_REFINED_FF)
+        return refined_size(prob, solver, bytes);
+    return solver->precision != ATM_FP32 ? plan_size<double>(prob, solver, bytes) : plan_size<float>(prob, solver, bytes);
 }
 
 atm_status atm_create(const atm_problem *prob, const atm_solver *solver, void *d_workspace, size_t bytes,
@@ -136,9 +137,9 @@ atm_status atm_create(const atm_problem *prob, const atm_solver *solver, void *d
     if (!d_workspace) return atm::fail(ATM_ERR_INVALID_ARG, "null workspace");
     if (reinterpret_cast<uintptr_t>(d_workspace) % 256 != 0)
         return atm::fail(ATM_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
-    if (solver->precision == ATM_FP32_REFINED)
+    if (solver->precision == ATM_FP32_REFINED || solver->precision == ATM_FP32_REFINED_FF)
         return refined_create(prob, solver, d_workspace, bytes, cuda_stream, out);
-    return solver->precision == ATM_FP64
+    return solver->precision != ATM_FP32
                ? plan_create<double>(prob, solver, d_workspace, bytes, cuda_stream, out)
                : plan_create<float>(prob, solver, d_workspace, bytes, cuda_stream, out);
 }

@@ -18,6 +18,7 @@
 #include "atm_kernels.cuh"
 #include "atm_gs.cuh"
 #include "atm_fused.h"
+#include "atm_df.h"
 #include "atm_nn.h"
 
 namespace atm {
@@ -171,6 +172,35 @@ inline std::vector<FusedVariant<T>> fused_variants(int nx, int ny, bool pr, bool
     return v;
 }
 
+// A double as a float-float pair (x = hi, y = lo).
+inline float2 ff_pair(double v)
+{
+    const float h = (float)v;
+    return make_float2(h, (float)(v - (double)h));
+}
+
+// The factorised line operator L with chunk length `chunk` in float-float.
+inline DFCoef to_df_coef(const LineCoef &L)
+{
+    DFCoef c;
+    std::memset(&c, 0, sizeof(c));
+    c.rho = ff_pair(L.rho);
+    for (int i = 0; i <= kMaxChunk; ++i) c.pw[i] = ff_pair(std::pow(L.rho, (double)i));
+    for (int j = 0; j < 6; ++j) c.scan[j] = ff_pair(std::pow(L.rho, (double)L.chunk * (double)(1 << j)));
+    for (int j = 0; j <= 32; ++j) c.chunk_pw[j] = ff_pair(std::pow(L.rho, (double)L.chunk * (double)j));
+    c.inv1m = ff_pair(1.0 / (1.0 - std::pow(L.rho, (double)L.n)));
+    return c;
+}
+
+// One launch shape of the float-float fine propagator and its column
+// coefficients (built for the shape's segment length).
+struct DFVariant {
+    void (*fn)(DFArgs) = nullptr;
+    int G = 1, NT = 256, LS = 16;
+    size_t smem = 0;
+    DFCoef cy{};
+};
+
 }  // namespace atm
 
 namespace atm {
@@ -186,14 +216,20 @@ struct LevelOp {
     bool learned = false;        // the level's propagator is the learned Psi_NN
     std::vector<FusedVariant<T>> fused;   // fused whole-propagator launch shapes (may be empty)
     std::vector<FusedVariant<T>> chains;  // chain-kernel shapes (ATM_SWEEP_CHAIN)
+    std::vector<DFVariant> df;            // float-float shapes (fine level of the FP64 float-float modes)
+    DFArgs dfa{};                         // their arguments (column coefficients per shape)
 };
 
 // Build the level-l propagator of (pb, sv): step D = dt * m_0 * .. * m_{l-1};
 // heat1d backward Euler; 2D PR-ADI or split-BE ADI; Allen-Cahn reaction by
 // explicit substeps or (coarse levels, ATM_REACT_EXACT) the exact flow.
 // d_w: device table for the 1D rank-one vector (filled by the caller).
+// The float-float kernel takes explicit reaction substeps only (the fine
+// level's reaction is always that).
+inline bool nsub_ok_for_df(const atm_problem &, bool react, int nsub) { return !react || nsub >= 1; }
+
 template <typename T>
-inline LevelOp<T> make_level_op(const atm_problem &pb, const atm_solver &sv, int l, const T *d_w)
+inline LevelOp<T> make_level_op(const atm_problem &pb, const atm_solver &sv, int l, const T *d_w, bool df_fine = false)
 {
     LevelOp<T> op;
     double D = pb.dt;
@@ -258,6 +294,31 @@ inline LevelOp<T> make_level_op(const atm_problem &pb, const atm_solver &sv, int
     }
     op.row = row_kernel<T>(C, false, pr, react);
     op.col = col_kernel<T>(CY, pb.ny / CY, pr);
+    if (l == 0 && df_fine && (nsub_ok_for_df(pb, react, a.nsub))) {
+        for (const DFShape &f : df_shapes(pb.nx, pb.ny, pr, react)) {
+            DFVariant v;
+            v.fn = f.fn;
+            v.G = f.G;
+            v.NT = f.NT;
+            v.LS = f.LS;
+            v.smem = f.smem;
+            v.cy = to_df_coef(make_line(ay, pb.ny, true, f.LS));
+            op.df.push_back(v);
+        }
+        DFArgs &d = op.dfa;
+        d.cx = to_df_coef(cx);
+        if (pr) {
+            d.rx0 = ff_pair((1.0 - 2.0 * ay) / cx.kappa);
+            d.rx1 = ff_pair(ay / cx.kappa);
+            d.cy0 = ff_pair((1.0 - 2.0 * ax) / cy.kappa);
+            d.cy1 = ff_pair(ax / cy.kappa);
+        } else {
+            d.rx0 = ff_pair(1.0 / cx.kappa);
+            d.cy0 = ff_pair(1.0 / cy.kappa);
+        }
+        d.react = react ? ff_pair((D / nsub) / (pb.eps * pb.eps)) : make_float2(0.f, 0.f);
+        d.nsub = react ? nsub : 0;
+    }
     op.rows_per_cta = 8;
     op.col_chunk = CY;
     op.col_warps = pb.ny / CY;
@@ -354,6 +415,9 @@ struct Level {
     int fz = -1;                 // selected fused shape (-1: split row/column kernels)
     std::vector<FusedVariant<T>> chains;  // chain-kernel shapes
     int chz = -1;                // selected chain shape (-1: F-relaxation step by step)
+    std::vector<DFVariant> df;   // float-float shapes (level 0 of the FP64 float-float modes)
+    int dfz = -1;                // selected float-float shape (-1: none)
+    DFArgs dfa{};
     bool gs = false;             // Gray-Scott: the Newton kernel applies the propagator
     GsArgs gsa{};
 };
@@ -480,6 +544,13 @@ struct Plan : PlanBase {
     }
     // Number of level-0 states held in memory.
     int ustates() const { return cpo ? lv[0].NC : lv[0].N; }
+    // The fine propagator in float-float arithmetic: FP64 plans of ATM_FP64_FF,
+    // and the FP64 pass of ATM_FP32_REFINED_FF.
+    bool ff_fine() const
+    {
+        return sizeof(T) == sizeof(double) &&
+               (sv.precision == ATM_FP64_FF || (role == ROLE_OUTER && sv.precision == ATM_FP32_REFINED_FF));
+    }
     // With C-point storage, is the level-0 interval i followed by a C-point?
     // (F-points after the last C-point feed nothing and are not computed.)
     bool full_interval(int i) const { return (i + 1) * lv[0].m <= lv[0].N - 1; }
@@ -598,7 +669,7 @@ struct Plan : PlanBase {
             setup_gs_level(l);
             return;
         }
-        LevelOp<T> op = make_level_op<T>(pb, sv, l, Lv.dir_w);
+        LevelOp<T> op = make_level_op<T>(pb, sv, l, Lv.dir_w, l == 0 && ff_fine());
         if (op.learned) {
             atm_solver cs = sv;
             cs.coarse_prop = ATM_PROP_SPLIT_BE;
@@ -616,6 +687,9 @@ struct Plan : PlanBase {
         Lv.fused = op.fused;
         Lv.chains = op.chains;
         Lv.chz = Lv.chains.empty() ? -1 : 0;
+        Lv.df = op.df;
+        Lv.dfa = op.dfa;
+        Lv.dfz = Lv.df.empty() ? -1 : 0;
         // fused on coarse levels by default, and on level 0 when asked for
         // (ATM_SWEEP_AUTO lets the autotuner decide level 0 at create time)
         Lv.fz = (!Lv.fused.empty() && (l > 0 || sv.sweep_kernel == ATM_SWEEP_FUSED || sv.sweep_kernel == ATM_SWEEP_CHAIN ||
@@ -628,6 +702,7 @@ struct Plan : PlanBase {
     {
         if (is1d || isgs) return 1;
         if (l < (int)lv.size() && lv[l].learned) return pb.nx * pb.ny / nn::kNNTile;
+        if (l < (int)lv.size() && lv[l].dfz >= 0) return lv[l].df[lv[l].dfz].G;
         if (l < (int)lv.size() && lv[l].fz >= 0) return lv[l].fused[lv[l].fz].G;
         return pb.nx / 32;
     }
@@ -639,9 +714,12 @@ struct Plan : PlanBase {
         int b = blocks_per_job(l);
         if (is1d || isgs || (l < (int)lv.size() && lv[l].learned)) return b;
         if (b < pb.nx / 32) b = pb.nx / 32;
-        if (l < (int)lv.size())
+        if (l < (int)lv.size()) {
             for (const FusedVariant<T> &f : lv[l].fused)
                 if (f.G > b) b = f.G;
+            for (const DFVariant &f : lv[l].df)
+                if (f.G > b) b = f.G;
+        }
         return b;
     }
 
@@ -1179,7 +1257,7 @@ struct Plan : PlanBase {
             Phase &ph = role == ROLE_OUTER ? resid_full
                         : role == ROLE_INNER ? inner_cycle
                         : (sv.algorithm == ATM_SEQUENTIAL) ? seq : passA;
-            const int cap = role == ROLE_INNER ? 16 : 64;
+            const int cap = 64;
             for (LaunchRec &r : ph)
                 if (r.type == L_SWEEP && r.level == 0 && nprof < cap) r.prof_slot = nprof++;
         }
@@ -1212,7 +1290,7 @@ struct Plan : PlanBase {
         for (const LaunchRec &r : ph) {
             if (r.type == L_CHAIN) n += (r.njobs + 32767) / 32768;
             else if (r.type != L_SWEEP || is1d || isgs) n += 1;
-            else if (lv[r.level].learned || lv[r.level].fz >= 0) {
+            else if (lv[r.level].learned || lv[r.level].fz >= 0 || lv[r.level].dfz >= 0) {
                 n += sweep_pairs(r.level, r.njobs);
                 if (lv[r.level].learned && hybrid) n += 2 * ((r.njobs + midcap - 1) / midcap);
             }
@@ -1325,6 +1403,36 @@ struct Plan : PlanBase {
             if (prof) cudaEventRecordWithFlags(pev[4 * slot + 3], st, cudaEventRecordExternal);
             return;
         }
+        if (Lv.dfz >= 0) {
+            if constexpr (sizeof(T) == sizeof(double)) {
+                const DFVariant &dv = Lv.df[Lv.dfz];
+                DFArgs d = Lv.dfa;
+                d.cy = dv.cy;
+                d.neg = neg;
+                for (int j0 = 0; j0 < njobs; j0 += 32768) {
+                    const int nj = njobs - j0 < 32768 ? njobs - j0 : 32768;
+                    d.jobs = djobs + j0;
+                    d.partials = part ? part + (size_t)j0 * dv.G : nullptr;
+                    cudaLaunchConfig_t cfg = {};
+                    cfg.gridDim = dim3(dv.G, nj);
+                    cfg.blockDim = dim3(dv.NT);
+                    cfg.dynamicSmemBytes = dv.smem;
+                    cfg.stream = st;
+                    cudaLaunchAttribute at[1];
+                    at[0].id = cudaLaunchAttributeClusterDimension;
+                    at[0].val.clusterDim.x = dv.G;
+                    at[0].val.clusterDim.y = 1;
+                    at[0].val.clusterDim.z = 1;
+                    cfg.attrs = at;
+                    cfg.numAttrs = 1;
+                    if (cudaLaunchKernelEx(&cfg, dv.fn, d) != cudaSuccess) launch_failed = true;
+                }
+            } else {
+                launch_failed = true;
+            }
+            if (prof) cudaEventRecordWithFlags(pev[4 * slot + 3], st, cudaEventRecordExternal);
+            return;
+        }
         if (Lv.fz >= 0 && Lv.fused[Lv.fz].pfn) {
             // persistent: the resident clusters walk all states of the launch
             const FusedVariant<T> &fv = Lv.fused[Lv.fz];
@@ -1395,7 +1503,7 @@ struct Plan : PlanBase {
             const int ch = maxbatch < nn::kInferChunk ? maxbatch : nn::kInferChunk;
             return 5 * ((njobs + ch - 1) / ch);   // counted as kernels / 2 by kernels_in
         }
-        if (lv[l].fz >= 0) return (njobs + 32767) / 32768;   // counted once by kernels_in
+        if (lv[l].fz >= 0 || lv[l].dfz >= 0) return (njobs + 32767) / 32768;   // counted once by kernels_in
         const int cs = chunk_size(l, njobs);
         return (njobs + cs - 1) / cs;
     }
@@ -1439,17 +1547,22 @@ struct Plan : PlanBase {
             }
         chunk = 0;
         if (is1d || isgs || recs.empty() || lv[0].learned) return ATM_OK;
-        struct Cand { int fz, chunk; };
+        struct Cand { int fz, chunk, dfz; };
         std::vector<Cand> cands;
         const bool tune_fz = sv.sweep_kernel == ATM_SWEEP_AUTO && !lv[0].fused.empty();
-        if (lv[0].fz < 0 || tune_fz) {
-            cands.push_back({-1, 0});
-            if (maxjobs > 64)
-                for (int c : {64, 128, 256, 512})
-                    if (c < maxjobs) cands.push_back({-1, c});
+        if (!lv[0].df.empty()) {
+            // float-float mode: its shapes only
+            for (int k = 0; k < (int)lv[0].df.size(); ++k) cands.push_back({-1, 0, k});
+        } else {
+            if (lv[0].fz < 0 || tune_fz) {
+                cands.push_back({-1, 0, -1});
+                if (maxjobs > 64)
+                    for (int c : {64, 128, 256, 512})
+                        if (c < maxjobs) cands.push_back({-1, c, -1});
+            }
+            if (tune_fz)
+                for (int k = 0; k < (int)lv[0].fused.size(); ++k) cands.push_back({k, 0, -1});
         }
-        if (tune_fz)
-            for (int k = 0; k < (int)lv[0].fused.size(); ++k) cands.push_back({k, 0});
         if (cands.empty()) return ATM_OK;   // fused shape fixed by the caller
         float best = 1e30f;
         Cand bc = cands[0];
@@ -1459,6 +1572,7 @@ struct Plan : PlanBase {
         for (const Cand &cd : cands) {
             if (cands.size() == 1) break;
             lv[0].fz = cd.fz;
+            lv[0].dfz = cd.dfz;
             chunk = cd.chunk;
             launch_failed = false;
             for (const LaunchRec *r : recs)
@@ -1481,6 +1595,7 @@ struct Plan : PlanBase {
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         lv[0].fz = bc.fz;
+        lv[0].dfz = bc.dfz;
         chunk = bc.chunk;
         tuned_ms = best < 1e30f ? best / 2 : 0.f;
         ATM_CK(cudaGetLastError());
@@ -1494,8 +1609,8 @@ struct Plan : PlanBase {
         int dev = 0;
         cudaGetDevice(&dev);
         char b[512];
-        int n = std::snprintf(b, sizeof(b), "d%d T%zu r%d k%d %dx%d nt%d alg%d L%d nu%d k%d fp%d cp%d sk%d cr%d cpo%d m",
-                              dev, sizeof(T), role, pb.kind, pb.nx, pb.ny, pb.nt_points, sv.algorithm, L, sv.nu, sv.k,
+        int n = std::snprintf(b, sizeof(b), "d%d T%zu p%d r%d k%d %dx%d nt%d alg%d L%d nu%d k%d fp%d cp%d sk%d cr%d cpo%d m",
+                              dev, sizeof(T), sv.precision, role, pb.kind, pb.nx, pb.ny, pb.nt_points, sv.algorithm, L, sv.nu, sv.k,
                               sv.fine_prop, sv.coarse_prop, sv.sweep_kernel, sv.coarse_reaction,
                               (int)cpo + 2 * (base_store != nullptr) + 4 * (fp32_out != nullptr));
         for (int l = 0; l + 1 < L && n < (int)sizeof(b) - 8; ++l) n += std::snprintf(b + n, sizeof(b) - n, "_%d", sv.m[l]);
@@ -1593,6 +1708,38 @@ struct Plan : PlanBase {
 
     // Shared-memory and cluster-size attributes of the fused kernels; shapes
     // that cannot be resident on this device are dropped.
+    atm_status prepare_df(int l)
+    {
+        Level<T> &Lv = lv[l];
+        std::vector<DFVariant> keep;
+        for (const DFVariant &dv : Lv.df) {
+            const void *fn = (const void *)dv.fn;
+            ATM_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dv.smem));
+            ATM_CK(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+            if (dv.G > 8) ATM_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(dv.G, 1);
+            cfg.blockDim = dim3(dv.NT);
+            cfg.dynamicSmemBytes = dv.smem;
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = dv.G;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            int nclusters = 0;
+            if (cudaOccupancyMaxActiveClusters(&nclusters, fn, &cfg) != cudaSuccess) {
+                cudaGetLastError();
+                nclusters = 0;
+            }
+            if (nclusters > 0) keep.push_back(dv);
+        }
+        Lv.df = keep;
+        Lv.dfz = keep.empty() ? -1 : 0;
+        return ATM_OK;
+    }
+
     atm_status prepare_fused(int l)
     {
         Level<T> &Lv = lv[l];
@@ -1695,6 +1842,7 @@ struct Plan : PlanBase {
         for (int l = 0; l < L; ++l) {
             if (lv[l].learned) continue;
             ATM_TRY(prepare_fused(l));
+            ATM_TRY(prepare_df(l));
             if (lv[l].row_smem > 48 * 1024)
                 ATM_CK(cudaFuncSetAttribute((const void *)lv[l].row, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)lv[l].row_smem));
@@ -1728,10 +1876,11 @@ struct Plan : PlanBase {
         {
             std::lock_guard<std::mutex> lk(tune_cache().mu);
             auto it = tune_cache().choice.find(tkey);
-            if (it != tune_cache().choice.end() && (int)it->second.size() == 2 * L + 1) {
+            if (it != tune_cache().choice.end() && (int)it->second.size() == 3 * L + 1) {
                 chunk = it->second[0];
                 for (int l = 0; l < L; ++l) lv[l].fz = it->second[1 + l];
                 for (int l = 0; l < L; ++l) lv[l].chz = it->second[1 + L + l];
+                for (int l = 0; l < L; ++l) lv[l].dfz = it->second[1 + 2 * L + l];
                 cached = true;
             }
         }
@@ -1754,6 +1903,7 @@ struct Plan : PlanBase {
             std::vector<int> ch(1, chunk);
             for (int l = 0; l < L; ++l) ch.push_back(lv[l].fz);
             for (int l = 0; l < L; ++l) ch.push_back(lv[l].chz);
+            for (int l = 0; l < L; ++l) ch.push_back(lv[l].dfz);
             std::lock_guard<std::mutex> lk(tune_cache().mu);
             tune_cache().choice[tkey] = ch;
         }
@@ -2228,6 +2378,9 @@ struct Plan : PlanBase {
             cfg[0] = 3; cfg[1] = 1; cfg[2] = 32;
         } else if (Lv.learned) {
             cfg[0] = 2;
+        } else if (Lv.dfz >= 0) {
+            const DFVariant &f = Lv.df[Lv.dfz];
+            cfg[0] = 7; cfg[1] = f.G; cfg[2] = f.NT; cfg[3] = f.LS;
         } else if (Lv.chz >= 0) {
             const FusedVariant<T> &f = Lv.chains[Lv.chz];
             cfg[0] = 4; cfg[1] = f.G; cfg[2] = f.NT; cfg[3] = f.LS;
@@ -2615,7 +2768,10 @@ struct RefinedPlan : PlanBase {
         return inner.level_io(level, array, t0, count, buf, write);
     }
     int level_points(int level) const override { return inner.level_points(level); }
-    atm_status sweep_config(int level, int *cfg) const override { return inner.sweep_config(level, cfg); }
+    atm_status sweep_config(int level, int *cfg) const override
+    {
+        return level == -1 ? outer.sweep_config(0, cfg) : inner.sweep_config(level, cfg);
+    }
 };
 
 }  // namespace atm

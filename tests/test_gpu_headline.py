@@ -45,9 +45,10 @@ def sequential():
     return u[::M0].copy()
 
 
-@pytest.mark.parametrize("sweep", ["auto", "persistent"])
-def test_bench_path_matches_the_oracle_sequential_solution(torch, sequential, sweep):
-    prob, desc = bench.make_desc(atm, W, "at", atm.FP32_REFINED, profile=True, cpoint=True, sweep=sweep)
+@pytest.mark.parametrize("prec, sweep", [("fp32r", "auto"), ("fp32r", "persistent"), ("fp32rf", "auto")])
+def test_bench_path_matches_the_oracle_sequential_solution(torch, sequential, prec, sweep):
+    prob, desc = bench.make_desc(atm, W, "at", bench.PRECISIONS[prec](atm), profile=True, cpoint=True,
+                                 sweep=sweep)
     s = atm.Solver(prob, desc)
     s.set_initial_condition(torch.as_tensor(bench.initial_condition(W, 0), device="cuda:0"))
     res = s.solve()
