@@ -9,7 +9,10 @@ A step is one full solve to ||r||_2 <= 1e-8 from the zero guess: every row of
 the sweep (relaxation, residual, restriction, local chains, correction, norm,
 cycle control).  value = fine time steps resolved per second
 = ranks * (nt - 1) / time-to-solution.  Default arithmetic: FP32 propagation
-inside the FP64 refinement loop (FP64 residual of every point and FP64 norm).
+inside the FP64 refinement loop (FP64 iterate, residual, update and norm),
+the residual pass's fine propagator evaluated in float-float (pairs of FP32,
+~48-bit significands, on the FP32 pipes); the line states the error of the
+result against the oracle's FP64 sequential solution.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl atm|reference]
 """
@@ -610,7 +613,7 @@ def main():
                     help="gray_scott_128: only one level-0 and one level-1 Newton launch on 255 states "
                          "(the profiling case)")
     ap.add_argument("--algorithm", choices=["at", "mgrit", "seq"], default="at")
-    ap.add_argument("--precision", choices=sorted(PRECISIONS), default="fp32r",
+    ap.add_argument("--precision", choices=sorted(PRECISIONS), default="fp32rf",
                     help="fp32r: FP32 propagation with FP64 refinement; fp32rf: the same with the FP64 residual "
                          "pass in float-float (pairs of FP32); fp64f: FP64 with the fine propagator in float-float")
     ap.add_argument("--coarse", choices=["classical", "learned", "correction"], default="classical",
