@@ -439,31 +439,28 @@ def max_over_ranks(dist, value, device=None):
     return float(t.item())
 
 
-def train_learned(atm, w, device, steps, seeds=(101, 102, 103, 104, 105), batch=8, correction=False):
-    """Psi_NN for the workload's level-1 step (m_0 fine steps): pairs (u_t, u_{t+m_0})
-    of fine trajectories from other seeds, produced by the library's sequential
-    stepping (the states that F-relaxation generates at convergence), then Adam.
-    correction: train the network on Phi^m0(u) - Psi_split(u) + u, for the
-    corrected propagator Psi_split(u) + N(u)."""
+def train_learned(atm, w, device, steps, seeds=tuple(range(101, 117)), cycles=(1, 2, 3, 5, 8), batch=8,
+                  correction=False):
+    """Psi_NN for the workload's level-1 step (m_0 fine steps), trained by Adam
+    on the pairs (u_C, Phi^m0 u_C) that the method's own F-relaxation generates
+    in the first cycles of FP32 AT-MGRIT solves of other seeds
+    (training.method_pairs: after c cycles, the C-points of the iterate and
+    their F-relaxation).  correction: train the network on
+    Phi^m0(u) - Psi_split(u) + u, for the corrected propagator Psi_split(u) + N(u)."""
     import torch
-    m0 = w["m"][0]
-    prob, desc = make_desc(atm, w, "seq", atm.FP32, profile=False)
-    seq = atm.Solver(prob, desc, device=device)
-    ins, outs = [], []
-    for sd in seeds:
-        seq.set_initial_condition(torch.as_tensor(initial_condition(w, sd), dtype=torch.float64, device=device))
-        seq.solve()
-        traj = seq.solution().to(torch.float32)
-        ins.append(traj[:-m0].clone())
-        outs.append(traj[m0:].clone())
-        del traj
-    seq.close()
-    inputs = torch.cat(ins).contiguous()
-    targets = torch.cat(outs).contiguous()
-    del ins, outs
+    from paper_2107_09596_gb300.training import method_pairs
+    prob, _ = make_desc(atm, w, "at", atm.FP32, profile=False)
+
+    def desc(c):
+        _, d = make_desc(atm, w, "at", atm.FP32, profile=False)
+        d.tol, d.max_iter = 0.0, c
+        return d
+
+    u0s = [torch.as_tensor(initial_condition(w, sd), dtype=torch.float64, device=device) for sd in seeds]
+    inputs, targets = method_pairs(prob, desc, u0s, cycles, device=device)
     if correction:
-        prob, desc = make_desc(atm, w, "at", atm.FP64, profile=False)
-        cl = atm.Solver(prob, desc, device=device)
+        prob, d64 = make_desc(atm, w, "at", atm.FP64, profile=False)
+        cl = atm.Solver(prob, d64, device=device)
         for i in range(0, inputs.shape[0], 64):
             x = inputs[i:i + 64].to(torch.float64)
             targets[i:i + 64] -= (cl.apply_propagator(1, x) - x).to(torch.float32)
@@ -475,8 +472,9 @@ def train_learned(atm, w, device, steps, seeds=(101, 102, 103, 104, 105), batch=
     perm = torch.randperm(inputs.shape[0], generator=torch.Generator().manual_seed(0)).to(device)
     inputs, targets = inputs[perm].contiguous(), targets[perm].contiguous()
     hist, res = net.train(params, adam, inputs, targets, steps=steps, batch=batch, lr=1e-3, log_every=250)
-    return params, {"pairs": int(inputs.shape[0]), "steps": steps, "batch": batch,
-                    "loss_first": float(hist[0]), "loss_last": float(hist[-1]),
+    return params, {"pairs": int(inputs.shape[0]), "data": f"method F-relaxation pairs: seeds {seeds[0]}-"
+                    f"{seeds[-1]}, iterates after {list(cycles)} FP32 AT-MGRIT cycles", "steps": steps,
+                    "batch": batch, "loss_first": float(hist[0]), "loss_last": float(hist[-1]),
                     "train_ms": res["time_ms"]}
 
 

@@ -104,8 +104,10 @@ enum { ATM_SEQUENTIAL = 0, ATM_MGRIT = 1, ATM_AT_MGRIT = 2 };
  * rounding ~2^-48 per operation against FP64's 2^-53), run on the FP32 pipes,
  * with FP64 storage, FP64 inputs and outputs and FP64 norms; ATM_FP64_FF is
  * ATM_FP64 with that fine propagator, ATM_FP32_REFINED_FF is ATM_FP32_REFINED
- * whose FP64 residual pass uses it.  Available for the 2D periodic problems on
- * 64^2, 128^2, 256^2 and 512^2 grids (the FP64 kernels elsewhere). */
+ * whose FP64 residual pass uses it.  Float-float keeps FP32's exponent range:
+ * values below ~1e-23 in magnitude lose relative precision (not absolute).
+ * Available for the 2D periodic problems on 64^2, 128^2, 256^2 and 512^2 grids
+ * (the FP64 kernels elsewhere). */
 enum { ATM_FP64 = 0, ATM_FP32 = 1, ATM_FP32_REFINED = 2, ATM_FP64_FF = 3, ATM_FP32_REFINED_FF = 4 };
 
 /* 2D propagator kernels (atm_solver.sweep_kernel). */

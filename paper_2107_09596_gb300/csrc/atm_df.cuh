@@ -4,6 +4,10 @@
 // (about 48 significant bits), so that the work runs on the FP32 pipes (64
 // times GB300's FP64 rate) instead of the FP64 pipe.  Inputs and outputs are
 // FP64; the conversions FP64 <-> float-float are integer bit operations.
+// Float-float keeps FP32's exponent range: values above ~2^-78 (1e-23) carry
+// the full ~48 bits; below, the low parts' rounding errors underflow (absolute
+// errors stay below the FP32 subnormal range), which leaves O(1) states and
+// their residuals unaffected.
 //
 // The kernel has the layout of fused_sweep_kernel (atm_fused.cuh): a cluster
 // of G CTAs holds one state in shared memory (two tiles: the hi and the lo

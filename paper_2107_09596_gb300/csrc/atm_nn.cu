@@ -49,6 +49,8 @@ atm_status prepare_training()
     ATM_TRY((set_smem_attr<float, IN_BF16, 16, EPI_LAST>()));
     ATM_TRY((set_smem_attr<float, IN_F32, 32, EPI_BWD>()));
     ATM_TRY((set_smem_attr<float, IN_BF16, 32, EPI_BWD>()));
+    ATM_CK(cudaFuncSetAttribute((const void *)wgrad_umma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kWgSmem));
     return ATM_OK;
 }
 
@@ -275,7 +277,7 @@ static atm_status backward_train(TrainBufs &t, const float *u, const float *targ
     int cur = 0;
     for (int l = 3; l >= 1; --l) {
         wgrad_ptrs(l, &dW, &db);
-        wgrad_kernel<32, 32><<<wg, 256, 0, st>>>(t.dzf, nullptr, t.h[l - 1], H, W, span, dW, db);
+        wgrad_umma_kernel<<<wg, kTile, kWgSmem, st>>>(t.h[l - 1], t.dzb[cur], H, W, span, dW, db, t.err);
         a.in_bf16 = t.dzb[cur];
         a.w = t.net.bwd[l];
         a.z_prev = t.z[l - 1];

@@ -19,7 +19,10 @@
 //
 // Backward-data is the same kernel: the gather offset is negated and the
 // weights are packed transposed (B[c][tap * C_out + o] = W[o][c][tap]).
-// Weight gradients are dot products over all pixels and run on the CUDA cores.
+// Weight gradients of the inner layers are GEMMs over pixels on the tensor
+// cores (wgrad_umma_kernel); those of the first and last layer (one input or
+// one output channel, 2% of the gradient work) are dot products on the CUDA
+// cores.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -406,6 +409,160 @@ __global__ void __launch_bounds__(256) wgrad_kernel(const float *dz, const float
         if (idx < NOUT) atomicAdd(dW + idx, acc[i]);
     }
     if (t < COUT) atomicAdd(db + t, bacc);
+}
+
+// Weight and bias gradients of an inner layer (32 -> 32 channels) on the
+// tensor cores.  With k = tap * 32 + c and X[p][k] = x[p + offset(tap)][c]:
+//   dW^T[k][o] = sum_p X[p][k] dz[p][o],   db[o] = sum_p dz[p][o],
+// a GEMM whose reduction runs over pixels: D[M = k][N = o] += A[M][K = p]
+// B[N][K]^T, tcgen05.mma kind::f16 (BF16 x BF16 -> FP32 in TMEM) with
+// M = 128 (three M-tiles: k < 288, then row 288 of ones, whose product is the
+// bias gradient, and zero rows), N = 32, K = 16 pixels per instruction.  x and
+// dz are BF16 [img][p][32] (the layer input and the bfloat16 copy of the
+// output gradient); a tile of 128 pixels is staged transposed (pixels
+// contiguous) into the K-major no-swizzle core layout of conv_umma_kernel.
+// A CTA walks `span` pixels of one image, accumulating in TMEM, and adds its
+// sums to dW, db (FP32 atomics, once per CTA).  Waits are bounded as in
+// conv_umma_kernel (time-out: error flag, TMEM still freed).
+constexpr int kWgMT = 3;                            // M-tiles: 288 weights + the bias row, padded
+constexpr size_t kWgA = (size_t)kWgMT * kTile * kTile * 2;   // A operand: 3 x 128 rows x 128 pixels
+constexpr size_t kWgB = (size_t)kCh * kTile * 2;             // B operand: 32 rows x 128 pixels
+constexpr size_t kWgSmem = kWgA + kWgB;
+
+__device__ __forceinline__ void put_bf16_tile(unsigned char *tile, int rows, int row, int k, __nv_bfloat16 v)
+{
+    *reinterpret_cast<__nv_bfloat16 *>(tile + chunk_off(row, k >> 3, rows) + (k & 7) * 2) = v;
+}
+
+static __global__ void __launch_bounds__(kTile) wgrad_umma_kernel(const __nv_bfloat16 *x, const __nv_bfloat16 *dz,
+                                                                  int H, int W, int span, float *dW, float *db,
+                                                                  int *err)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char *sA = smem;            // M-tile mt at sA + mt * kTile * kTile * 2
+    unsigned char *sB = smem + kWgA;
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tslot;
+    const int t = threadIdx.x, warp = t >> 5;
+    const int img = blockIdx.y;
+    const size_t P = (size_t)H * W;
+    const int p_begin = blockIdx.x * span;
+    constexpr size_t MT = (size_t)kTile * kTile * 2;
+
+    // padding rows of the last M-tile: row 288 - 256 = 32 is the ones row, rows 33..127 zero
+    {
+        unsigned char *a2 = sA + 2 * MT;
+        const __nv_bfloat16 one = __float2bfloat16_rn(1.0f), zero = __float2bfloat16_rn(0.0f);
+        for (int i = t; i < (kTile - 32) * kTile; i += kTile) {
+            const int row = 32 + i / kTile, k = i % kTile;
+            put_bf16_tile(a2, kTile, row, k, row == 32 ? one : zero);
+        }
+    }
+    if (t == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(smem_u32(&tslot)));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = tslot;
+
+    uint32_t ok = 1;
+    const int ntiles = span / kTile;
+#pragma unroll 1
+    for (int it = 0; it < ntiles && ok; ++it) {
+        // stage the tile: thread t owns pixel p = p0 + t (column t of every operand row)
+        const int p = p_begin + it * kTile + t;
+        const int y = p / W, xx = p - y * W;
+        {
+            const uint4 *src = reinterpret_cast<const uint4 *>(dz + ((size_t)img * P + p) * kCh);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const uint4 v = src[j];
+                const __nv_bfloat16 *e = reinterpret_cast<const __nv_bfloat16 *>(&v);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) put_bf16_tile(sB, kCh, 8 * j + q, t, e[q]);
+            }
+        }
+#pragma unroll 1
+        for (int tap = 0; tap < 9; ++tap) {
+            const int yy = (y + tap / 3 - 1 + H) % H, xn = (xx + tap % 3 - 1 + W) % W;
+            const uint4 *src = reinterpret_cast<const uint4 *>(x + ((size_t)img * P + (size_t)yy * W + xn) * kCh);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const uint4 v = src[j];
+                const __nv_bfloat16 *e = reinterpret_cast<const __nv_bfloat16 *>(&v);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int k = tap * kCh + 8 * j + q;            // row of the transposed operand
+                    put_bf16_tile(sA + (size_t)(k / kTile) * MT, kTile, k % kTile, t, e[q]);
+                }
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;");
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        if (t == 0) {
+            const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+#pragma unroll 1
+            for (int s = 0; s < kTile / 16; ++s) {
+                const uint64_t bd = umma_desc(b0 + s * (kCh * 32));
+#pragma unroll 1
+                for (int mt = 0; mt < kWgMT; ++mt) {
+                    const uint64_t ad = umma_desc(a0 + (uint32_t)(mt * MT) + s * (kTile * 32));
+                    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                                 " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                                 ::"r"(tmem + (uint32_t)(mt * kCh)), "l"(ad), "l"(bd), "r"(umma_idesc(kTile, kCh)),
+                                   "r"((uint32_t)(it > 0 || s > 0)));
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         ::"r"(smem_u32(&mbar)));
+        }
+        // the MMAs read the staged tile: wait for them before the next tile overwrites it
+        uint32_t done = 0;
+        for (int w = 0; w < (1 << 24) && !done; ++w) {
+            asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                         " selp.u32 %0, 1, 0, p;\n}\n" : "=r"(done) : "r"(smem_u32(&mbar)), "r"((uint32_t)(it & 1)));
+        }
+        ok = __syncthreads_and(done);
+        asm volatile("tcgen05.fence::after_thread_sync;");
+    }
+    if (!ok && t == 0 && err) atomicExch(err, 1);
+    if (ok) {
+        // D row t of M-tile mt: k = mt * 128 + t; columns o = 0..31
+#pragma unroll 1
+        for (int mt = 0; mt < kWgMT; ++mt) {
+            uint32_t v[kCh];
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(mt * kCh);
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                         "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                         : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                           "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                           "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]),
+                           "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]),
+                           "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                         : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;");
+            const int k = mt * kTile + t;
+            if (k < 9 * kCh) {
+                const int tap = k / kCh, c = k % kCh;
+#pragma unroll
+                for (int o = 0; o < kCh; ++o) atomicAdd(dW + (o * kCh + c) * 9 + tap, __uint_as_float(v[o]));
+            } else if (k == 9 * kCh) {
+#pragma unroll
+                for (int o = 0; o < kCh; ++o) atomicAdd(db + o, __uint_as_float(v[o]));
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem));
 }
 
 // MSE of out against target over n values: per-CTA partial sums of diff^2 and

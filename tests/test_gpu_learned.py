@@ -1,8 +1,10 @@
 """The learned coarse propagator on the GPU against its FP64 oracle
 (oracle/nn.py).  The GPU rounds every tensor-core operand to bfloat16 and
 accumulates in FP32; the comparisons below feed the oracle the same
-bfloat16-rounded operands (layer inputs, stored activations, weights, and the
-data-gradient inputs) so that the remaining difference is FP32 accumulation
+bfloat16-rounded operands (layer inputs, stored activations, weights, the
+data-gradient inputs, and the output gradients of the inner layers, which
+their tensor-core weight-gradient GEMM takes in bfloat16) so that the
+remaining difference is FP32 accumulation
 order: relative L2 <= 1e-3 for the network output increment and <= 2e-3 for
 the gradients (summed over 8192 pixels with FP32 atomics)."""
 import numpy as np
@@ -58,7 +60,10 @@ def emu_grads(params, u, target):
     for li in range(len(params) - 1, -1, -1):
         w, b = params[li]
         x = u[:, None] if li == 0 else hs[li]
-        _, dw, db = onn.conv3x3_backward(x, bf(w), dz)
+        # inner layers: the weight gradient is a tensor-core GEMM on the
+        # bfloat16 copy of dz; first and last layer: FP32 dz on CUDA cores
+        inner = 0 < li < len(params) - 1
+        _, dw, db = onn.conv3x3_backward(x, bf(w), bf(dz) if inner else dz)
         grads[li] = (dw, db)
         if li > 0:
             dx, _, _ = onn.conv3x3_backward(x, bf(w), bf(dz))
@@ -247,3 +252,59 @@ def test_learned_correction_gain_over_classical(torch):
           f"\n  classical log10 r: {np.round(np.log10(b2.residual_history()), 1)}")
     assert ra["converged"] and rb["converged"]
     assert rel_l2(a2.solution().cpu().numpy(), oracle.sequential(oc2, u0)) <= 1e-8
+
+
+def test_method_pairs_give_a_coarse_propagator_that_beats_the_classical_one(torch):
+    """Training data from the method itself (training.method_pairs): after
+    c = 1, 2, 3, 5 cycles of FP64 AT-MGRIT (64^2, 257 points, m = (16, 4),
+    k = 3, FCF) from the zero guess, the level-0 C-points and their
+    F-relaxation Phi^16, for seeds 1-6.  The corrected propagator
+    Psi_split + N, N trained on Phi^16(u) - Psi_split(u), is closer to Phi^16
+    than the classical Psi_split on the held-out seed's pairs of the same
+    cycles (the gain, printed), and a solve with it converges to the
+    sequential solution without falling back to the classical propagator."""
+    from paper_2107_09596_gb300.training import method_pairs
+    kw = dict(kind="ac", nx=64, ny=64, dt=1e-4, nt=257, m=(16, 4), k=3, nu=1, tol=1e-9, max_iter=60)
+    oc, gp, gs_cl = pair(**kw)
+    _, _, gs_h = pair(coarse_prop=atm.PROP_LEARNED_CORRECTION, **kw)
+
+    def desc(c):
+        _, _, d = pair(**dict(kw, tol=0.0, max_iter=c))
+        return d
+
+    cycles = (1, 2, 3, 5)
+    u0s = [torch.as_tensor(I.uniform_field((64, 64), sd), device="cuda:0") for sd in range(1, 7)]
+    ins, outs = method_pairs(gp, desc, u0s, cycles)
+    assert ins.shape == (6 * len(cycles) * 16, 64, 64)
+    cl = atm.Solver(gp, gs_cl)
+    # the pairs are the oracle's Phi^16 of the GPU's C-points (spot check)
+    x = ins[::37].cpu().numpy().astype(np.float64)
+    y = x.copy()
+    for _ in range(16):
+        y = oracle.apply_prop(oc, 0, y)
+    assert rel_l2(outs[::37].cpu().numpy(), y) <= 1e-6
+    psi = classical_psi(torch, cl, ins.cpu().numpy().astype(np.float64))
+    target = (outs.cpu().numpy() - psi + ins.cpu().numpy()).astype(np.float32)
+    net = atm.LearnedCoarse()
+    params = torch.as_tensor(flat(onn.init_params(6)), dtype=torch.float32, device="cuda:0")
+    adam = torch.zeros(2 * net.nparams, dtype=torch.float32, device="cuda:0")
+    perm = np.random.default_rng(2).permutation(len(ins))
+    net.train(params, adam, ins[perm].contiguous(), torch.as_tensor(target[perm], device="cuda:0"), steps=600,
+              batch=8, lr=1e-3, log_every=100)
+    hu, hy = method_pairs(gp, desc, [torch.as_tensor(I.uniform_field((64, 64), 0), device="cuda:0")], cycles)
+    hu, hy = hu.cpu().numpy().astype(np.float64), hy.cpu().numpy().astype(np.float64)
+    h = atm.Solver(gp, gs_h)
+    h.set_learned_coarse(params)
+    e_cl = rel_l2(classical_psi(torch, cl, hu), hy)
+    e_h = rel_l2(classical_psi(torch, h, hu), hy)
+    print(f"\nheld-out method pairs: classical {e_cl:.3e}, corrected {e_h:.3e}")
+    assert e_h < 0.5 * e_cl, (e_cl, e_h)
+    u0 = I.uniform_field((64, 64), 0)
+    for s in (h, cl):
+        s.set_initial_condition(torch.as_tensor(u0, device="cuda:0"))
+    r_h, r_cl = h.solve(), cl.solve()
+    print(f"three levels: corrected {r_h['iterations']} cycles (fallback {r_h['fallback']}), classical "
+          f"{r_cl['iterations']}\n  corrected log10 r: {np.round(np.log10(h.residual_history()), 1)}"
+          f"\n  classical log10 r: {np.round(np.log10(cl.residual_history()), 1)}")
+    assert r_h["converged"] and not r_h["fallback"], r_h
+    assert rel_l2(h.solution().cpu().numpy(), oracle.sequential(oc, u0)) <= 1e-8
