@@ -1529,10 +1529,61 @@ struct Plan : PlanBase {
         cudaGetLastError();
     }
 
+    // Time `body` (kernel launches on st) as the solve runs it: captured into a
+    // CUDA graph, one warm-up replay, then the fastest of three timed replays.
+    // Falls back to timing direct launches on the legacy stream (no capture
+    // there).  Returns false when a launch of the body failed.
+    template <typename F>
+    bool time_body(F &&body, cudaEvent_t e0, cudaEvent_t e1, float *ms)
+    {
+        launch_failed = false;
+        *ms = 0.f;
+        if (st == nullptr) {
+            body();
+            cudaEventRecord(e0, st);
+            body();
+            cudaEventRecord(e1, st);
+            cudaEventSynchronize(e1);
+            cudaEventElapsedTime(ms, e0, e1);
+            const bool ok = !launch_failed && cudaGetLastError() == cudaSuccess;
+            launch_failed = false;
+            return ok;
+        }
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t ge = nullptr;
+        bool ok = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (ok) {
+            const bool ne = no_events;
+            no_events = true;
+            body();
+            no_events = ne;
+            ok = cudaStreamEndCapture(st, &g) == cudaSuccess && !launch_failed;
+        }
+        if (ok) ok = cudaGraphInstantiate(&ge, g, 0) == cudaSuccess;
+        if (g) cudaGraphDestroy(g);
+        float best = 1e30f;
+        if (ok) ok = cudaGraphLaunch(ge, st) == cudaSuccess && cudaStreamSynchronize(st) == cudaSuccess;
+        for (int r = 0; r < 3 && ok; ++r) {
+            cudaEventRecord(e0, st);
+            ok = cudaGraphLaunch(ge, st) == cudaSuccess;
+            cudaEventRecord(e1, st);
+            ok = ok && cudaEventSynchronize(e1) == cudaSuccess;
+            float t = 0.f;
+            cudaEventElapsedTime(&t, e0, e1);
+            if (ok && t < best) best = t;
+        }
+        if (ge) cudaGraphExecDestroy(ge);
+        cudaGetLastError();
+        launch_failed = false;
+        *ms = best;
+        return ok;
+    }
+
     // Autotuner for the level-0 chunk size: times every level-0 sweep of `ph`
     // in order (the dependent steps of a relaxation pass, so that inputs come
-    // from where a real cycle finds them) for each candidate, with CUDA events
-    // over 2 repetitions after a warm-up, and keeps the fastest.  Runs on the
+    // from where a real cycle finds them) for each candidate, two repetitions
+    // captured as a CUDA graph (as the solve replays them: launch overheads of
+    // a graph, not of direct launches), and keeps the fastest.  Runs on the
     // state present at create time (zero), for which the sweeps write zeros.
     // The same timing also chooses, with ATM_SWEEP_AUTO, between the split
     // row/column kernels (each chunk size) and each fused launch shape.
@@ -1574,22 +1625,13 @@ struct Plan : PlanBase {
             lv[0].fz = cd.fz;
             lv[0].dfz = cd.dfz;
             chunk = cd.chunk;
-            launch_failed = false;
-            for (const LaunchRec *r : recs)
-                launch_sweep(0, d_jobs + r->job_index, r->njobs, r->neg, r->partials);
-            cudaEventRecord(e0, st);
-            for (int rep = 0; rep < 2; ++rep)
-                for (const LaunchRec *r : recs)
-                    launch_sweep(0, d_jobs + r->job_index, r->njobs, r->neg, r->partials);
-            cudaEventRecord(e1, st);
-            cudaEventSynchronize(e1);
             float ms = 0;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (launch_failed) {   // a launch shape the device cannot schedule
-                launch_failed = false;
-                cudaGetLastError();
-                continue;
-            }
+            const bool ok = time_body([&] {
+                for (int rep = 0; rep < 2; ++rep)
+                    for (const LaunchRec *r : recs)
+                        launch_sweep(0, d_jobs + r->job_index, r->njobs, r->neg, r->partials);
+            }, e0, e1, &ms);
+            if (!ok) continue;   // a launch shape the device cannot schedule
             if (ms < best) { best = ms; bc = cd; }
         }
         cudaEventDestroy(e0);
@@ -1621,7 +1663,8 @@ struct Plan : PlanBase {
 
     // Coarse-level kernel choice (ATM_SWEEP_AUTO): for each level l >= 1 with
     // fused shapes, time the level's sweeps of `ph` with the split kernels and
-    // with each fused shape (warm-up, then three repetitions) and keep the fastest.
+    // with each fused shape (three repetitions as a captured graph) and keep
+    // the fastest.
     // The coarse launches are short and latency-bound, so the shape with the
     // most CTAs per state often wins there.
     atm_status autotune_coarse(const Phase &ph)
@@ -1640,21 +1683,13 @@ struct Plan : PlanBase {
             int bk = lv[l].fz;
             for (int k = -1; k < (int)lv[l].fused.size(); ++k) {
                 lv[l].fz = k;
-                launch_failed = false;
-                for (const LaunchRec *r : recs) launch_sweep(l, d_jobs + r->job_index, r->njobs, r->neg, r->partials);
-                cudaEventRecord(e0, st);
-                for (int rep = 0; rep < 3; ++rep)
-                    for (const LaunchRec *r : recs)
-                        launch_sweep(l, d_jobs + r->job_index, r->njobs, r->neg, r->partials);
-                cudaEventRecord(e1, st);
-                cudaEventSynchronize(e1);
                 float ms = 0;
-                cudaEventElapsedTime(&ms, e0, e1);
-                if (launch_failed) {
-                    launch_failed = false;
-                    cudaGetLastError();
-                    continue;
-                }
+                const bool ok = time_body([&] {
+                    for (int rep = 0; rep < 3; ++rep)
+                        for (const LaunchRec *r : recs)
+                            launch_sweep(l, d_jobs + r->job_index, r->njobs, r->neg, r->partials);
+                }, e0, e1, &ms);
+                if (!ok) continue;
                 if (ms < best) { best = ms; bk = k; }
             }
             lv[l].fz = bk;
@@ -1682,20 +1717,12 @@ struct Plan : PlanBase {
             int bk = lv[l].chz;
             for (int k = 0; k < (int)lv[l].chains.size(); ++k) {
                 lv[l].chz = k;
-                launch_failed = false;
-                for (const LaunchRec *r : recs) launch_chain(l, d_jobs + r->job_index, r->njobs, r->steps);
-                cudaEventRecord(e0, st);
-                for (int rep = 0; rep < 2; ++rep)
-                    for (const LaunchRec *r : recs) launch_chain(l, d_jobs + r->job_index, r->njobs, r->steps);
-                cudaEventRecord(e1, st);
-                cudaEventSynchronize(e1);
                 float ms = 0;
-                cudaEventElapsedTime(&ms, e0, e1);
-                if (launch_failed) {
-                    launch_failed = false;
-                    cudaGetLastError();
-                    continue;
-                }
+                const bool ok = time_body([&] {
+                    for (int rep = 0; rep < 2; ++rep)
+                        for (const LaunchRec *r : recs) launch_chain(l, d_jobs + r->job_index, r->njobs, r->steps);
+                }, e0, e1, &ms);
+                if (!ok) continue;
                 if (ms < best) { best = ms; bk = k; }
             }
             lv[l].chz = bk;
