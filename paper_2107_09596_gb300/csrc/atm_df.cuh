@@ -130,7 +130,13 @@ __device__ __forceinline__ void df_split(double x, float &hi, float &lo)
         hi = __uint_as_float((hw & 0x80000000u) | ((((rh & 0x7fffffffu) - (896u << 20)) << 3) | (rl >> 29)));
         const int rem = ((int)(lw << 3)) >> 3;   // x - hi in units of 2^(e - 1075), |rem| <= 2^28
         const float scale = __uint_as_float((hw & 0x80000000u) | ((unsigned)(e - 948) << 23));
-        lo = __fmul_rn(__int2float_rn(rem), scale);
+        // rem as FP32 without a conversion instruction: rem = qh 2^14 + ql,
+        // |qh| <= 2^14, 0 <= ql < 2^14, each exact through the 1.5 * 2^23
+        // bias; one fused multiply-add rounds the sum to 24 bits
+        const int qh = rem >> 14, ql = rem & 0x3fff;
+        const float fh = __fsub_rn(__int_as_float(0x4b400000 + qh), 12582912.f);
+        const float fl = __fsub_rn(__int_as_float(0x4b400000 + ql), 12582912.f);
+        lo = __fmul_rn(__fmaf_rn(fh, 16384.f, fl), scale);
         return;
     }
     hi = __double2float_rn(x);
@@ -242,12 +248,13 @@ __device__ __forceinline__ void df_col_final(const float *th, const float *tl, c
 }
 
 // One application of the fine propagator per state at FP64 accuracy (see the
-// file comment).  Grid (G, states), one cluster per state.  Job semantics as
+// file comment).  Grid (G, states), one cluster per state; registers capped
+// so that the MINB CTAs per SM that the shared memory allows stay resident.  Job semantics as
 // for the other sweep kernels: val = (+-)Phi(in) + g + h; out = val; outf =
 // fp32(val); with sub: r = val - sub, out2 = r, sum r^2 per CTA.  Jobs carry
 // no base (the FP64 pass of the refined mode never uses increments).
-template <int C, int G, int NT, int LS, bool PR, bool REACT>
-__global__ void __launch_bounds__(NT) df_sweep_kernel(const __grid_constant__ DFArgs a)
+template <int C, int G, int NT, int LS, bool PR, bool REACT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) df_sweep_kernel(const __grid_constant__ DFArgs a)
 {
     using Z = FzShape<C, G, NT, LS>;
     constexpr int NW = Z::NW, NX = Z::NX, NXP = Z::NXP, P = Z::P, XPT = Z::XPT, R = Z::R, S = Z::S, NY = Z::NY,
@@ -270,7 +277,7 @@ __global__ void __launch_bounds__(NT) df_sweep_kernel(const __grid_constant__ DF
     // 1. load (FP64 -> float-float), react; tile row t = state row r0 - 1 + t
     {
         const int t_lo = PR ? 0 : 1, t_hi = PR ? R + 2 : R + 1;
-        constexpr int U = 2;
+        constexpr int U = 4;
         for (int t0 = t_lo + prow; t0 < t_hi; t0 += RPI * U) {
             float4 h[U], l[U];
 #pragma unroll
