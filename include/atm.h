@@ -117,7 +117,7 @@ enum { ATM_SWEEP_AUTO = 0, ATM_SWEEP_SPLIT = 1, ATM_SWEEP_FUSED = 2, ATM_SWEEP_C
 
 typedef struct {
     int kind;          /* ATM_HEAT1D | ATM_HEAT2D | ATM_ALLEN_CAHN | ATM_GRAY_SCOTT */
-    int nx, ny;        /* grid; ny ignored for heat1d.  2D: nx, ny powers of two in [32, 512] (FP32: 1024); Gray-Scott: 8..512 */
+    int nx, ny;        /* grid; ny ignored for heat1d.  2D: nx, ny powers of two in [32, 1024]; Gray-Scott: 8..512 */
     double lx, ly;     /* domain lengths */
     double dt;         /* fine time step */
     int nt_points;     /* number of time points including t_0 (>= 2) */

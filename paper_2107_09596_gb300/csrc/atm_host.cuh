@@ -124,6 +124,9 @@ inline SweepFn<T> col_kernel(int CY, int W, bool pr)
     if (CY == 32 && W == 16) return col_pick<T, 32, 16>(pr);
     if constexpr (sizeof(T) == 4) {
         if (CY == 64 && W == 16) return col_pick<T, 64, 16>(pr);
+    } else {
+        // 1024 FP64 rows: 32 warps of 32 rows (a 1024-thread CTA; register-limited, it spills)
+        if (CY == 32 && W == 32) return col_pick<T, 32, 32>(pr);
     }
     return nullptr;
 }
@@ -264,7 +267,7 @@ inline LevelOp<T> make_level_op(const atm_problem &pb, const atm_solver &sv, int
     const double f = pr ? 0.5 * D : D;
     const double ax = f / (dx * dx), ay = f / (dy * dy);
     const int C = pb.nx / 32;
-    const int CY = pb.ny <= 256 ? 16 : pb.ny / 16;
+    const int CY = pb.ny <= 256 ? 16 : (sizeof(T) == 8 && pb.ny == 1024) ? 32 : pb.ny / 16;
     LineCoef cx = make_line(ax, pb.nx, true, C);
     LineCoef cy = make_line(ay, pb.ny, true, CY);
     a.cx = to_coef<T>(cx, nullptr);
@@ -577,9 +580,8 @@ struct Plan : PlanBase {
         } else if (is1d) {
             if (pb.nx < 2 || pb.nx > 2048) return fail(ATM_ERR_INVALID_ARG, "heat1d needs 2 <= nx <= 2048");
         } else {
-            const int nmax = sizeof(T) == 4 ? 1024 : 512;
-            if (!pow2_in(pb.nx, 32, nmax) || !pow2_in(pb.ny, 32, nmax))
-                return fail(ATM_ERR_INVALID_ARG, "2D grids need nx, ny powers of two in [32, %d] for this precision", nmax);
+            if (!pow2_in(pb.nx, 32, 1024) || !pow2_in(pb.ny, 32, 1024))
+                return fail(ATM_ERR_INVALID_ARG, "2D grids need nx, ny powers of two in [32, 1024]");
         }
         if (sv.algorithm < ATM_SEQUENTIAL || sv.algorithm > ATM_AT_MGRIT) return fail(ATM_ERR_INVALID_ARG, "unknown algorithm");
         if (sv.algorithm != ATM_SEQUENTIAL) {
@@ -1591,8 +1593,9 @@ struct Plan : PlanBase {
     {
         std::vector<const LaunchRec *> recs;
         int maxjobs = 0;
+        // (sequential stepping: the first 64 steps stand for the chain)
         for (const LaunchRec &r : ph)
-            if (r.type == L_SWEEP && r.level == 0) {
+            if (r.type == L_SWEEP && r.level == 0 && recs.size() < 64) {
                 recs.push_back(&r);
                 if (r.njobs > maxjobs) maxjobs = r.njobs;
             }
@@ -1912,8 +1915,9 @@ struct Plan : PlanBase {
             }
         }
         if (!cached) {
-            if (sv.algorithm != ATM_SEQUENTIAL || role == ROLE_OUTER)
-                ATM_TRY(autotune_chunk(role == ROLE_OUTER ? resid_full : role == ROLE_INNER ? inner_cycle : passA));
+            ATM_TRY(autotune_chunk(role == ROLE_OUTER   ? resid_full
+                                   : role == ROLE_INNER ? inner_cycle
+                                   : sv.algorithm == ATM_SEQUENTIAL ? seq : passA));
             if (L > 1 && role != ROLE_OUTER) {
                 // coarse arrays hold whatever the workspace held: zero them before timing
                 for (int l = 1; l < L; ++l) {

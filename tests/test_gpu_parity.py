@@ -47,6 +47,7 @@ PROP_CASES = {
                                coarse_reaction=atm.REACT_SUBSTEPS),
     "ac_pr_512x32": dict(kind="ac", nx=512, ny=32, dt=1e-4, nt=65, m=(4, 4), k=3),
     "ac_pr_32x512": dict(kind="ac", nx=32, ny=512, dt=1e-4, nt=65, m=(4, 4), k=3),
+    "ac_pr_1024": dict(kind="ac", nx=1024, ny=1024, dt=2.5e-5, nt=65, m=(4, 4), k=3),
 }
 
 
