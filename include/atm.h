@@ -393,6 +393,12 @@ atm_status atm_train_learned_coarse(float *d_params, float *d_adam, const float 
 /* Give a handle created with coarse_prop = ATM_PROP_LEARNED its network
  * (device FP32 parameters, copied into the handle's workspace).  Required
  * before atm_solve on such a handle.  Not available in the refined mode.
+ * The handle's copy of the output layer's bias is shifted so that the network
+ * maps the zero state to zero, Psi_NN(0) = 0 = Phi^m(0) (the heat and
+ * Allen-Cahn steps keep zero at zero; the first cycles give the coarse level
+ * mostly zero states): the network's output for the zero state is a constant
+ * field (circular convolutions of a constant are constant), computed once here
+ * by the inference kernels.  The caller's parameters are not changed.
  * Fallback: such a handle keeps the classical split-BE ADI propagator for
  * level 1 too.  Every atm_solve starts with the network; when a cycle gives a
  * non-finite residual or one above 1e3 times the smallest so far, it restores

@@ -7,19 +7,18 @@ namespace atm {
 
 namespace {
 
-// SB: the base of increments staged in a second tile (its shared memory added).
-template <int C, int G, int NT, int LS, bool SB = false>
+template <int C, int G, int NT, int LS>
 void add_shape(std::vector<FusedShape> &v, bool pr, bool react)
 {
     FusedShape f;
-    if (pr) f.fn = react ? fused_sweep_kernel<C, G, NT, LS, true, true, SB> : fused_sweep_kernel<C, G, NT, LS, true, false, SB>;
-    else f.fn = react ? fused_sweep_kernel<C, G, NT, LS, false, true, SB> : fused_sweep_kernel<C, G, NT, LS, false, false, SB>;
+    if (pr) f.fn = react ? fused_sweep_kernel<C, G, NT, LS, true, true> : fused_sweep_kernel<C, G, NT, LS, true, false>;
+    else f.fn = react ? fused_sweep_kernel<C, G, NT, LS, false, true> : fused_sweep_kernel<C, G, NT, LS, false, false>;
     f.G = G;
     f.NT = NT;
     f.LS = LS;
     constexpr int NXP = 16 * C;
     constexpr int P = NT >= NXP ? NT / NXP : 1;
-    f.smem = fused_smem_bytes(32 * C, P * LS, P) + (SB ? (size_t)(P * LS + 2) * 32 * C * sizeof(float) : 0);
+    f.smem = fused_smem_bytes(32 * C, P * LS, P);
     v.push_back(f);
 }
 
@@ -137,11 +136,6 @@ std::vector<FusedShape> fused_shapes(int nx, int ny, bool pr, bool react)
         add_shape<8, 8, 256, 16>(v, pr, react);
         add_shape<8, 4, 512, 16>(v, pr, react);
         add_shape<8, 16, 256, 8>(v, pr, react);
-        if (react) {
-            add_shape<8, 8, 256, 16, true>(v, pr, react);
-            add_shape<8, 16, 256, 8, true>(v, pr, react);
-            add_shape<8, 8, 512, 8, true>(v, pr, react);
-        }
     }
     if (nx == 512 && ny == 512) {
         add_shape<16, 16, 256, 32>(v, pr, react);

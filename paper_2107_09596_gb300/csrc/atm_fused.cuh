@@ -481,10 +481,7 @@ __device__ __forceinline__ double fz_output(const Job<float> &jb, const float *t
 }
 
 // One application of Phi per state: grid (G, states), one cluster per state.
-// SB: increments around a base stage the base rows in a second tile by
-// cp.async, so that every input and base piece of the CTA is in flight at
-// once (otherwise both go through registers, four pieces at a time).
-template <int C, int G, int NT, int LS, bool PR, bool REACT, bool SB = false>
+template <int C, int G, int NT, int LS, bool PR, bool REACT>
 __global__ void __launch_bounds__(NT) fused_sweep_kernel(const __grid_constant__ SweepArgs<float> a)
 {
     using Z = FzShape<C, G, NT, LS>;
@@ -492,8 +489,7 @@ __global__ void __launch_bounds__(NT) fused_sweep_kernel(const __grid_constant__
 
     extern __shared__ __align__(16) unsigned char fz_smem[];
     float *tile = reinterpret_cast<float *>(fz_smem);                       // (R + 2) rows of NX
-    float *btile = tile + Z::TILE;                                          // SB: base rows
-    float2 *ce = reinterpret_cast<float2 *>(tile + (SB ? 2 : 1) * Z::TILE); // [P][NXP] forward carries
+    float2 *ce = reinterpret_cast<float2 *>(tile + Z::TILE);                // [P][NXP] forward carries
     float2 *cb = ce + (size_t)P * NXP;                                      // [P][NXP] backward carries
     float2 *dn = cb + (size_t)P * NXP;                                      // [P][NXP] final backward carries
     __shared__ double sh[32];
@@ -517,14 +513,6 @@ __global__ void __launch_bounds__(NT) fused_sweep_kernel(const __grid_constant__
             fz_cp_async_wait_all();
             // the same pieces as this thread copied: no barrier needed before
             if (REACT) fz_react_own<NX, RPI, false>(tile, nullptr, a, t_lo, t_hi, prow, pxs);
-        } else if constexpr (SB) {
-            for (int t = t_lo + prow; t < t_hi; t += RPI) {
-                const size_t go = (size_t)((r0 - 1 + t) & (NY - 1)) * NX + px;
-                fz_cp_async16(tile + (size_t)t * NX + pxs, jb.in + go);
-                fz_cp_async16(btile + (size_t)t * NX + pxs, jb.base + go);
-            }
-            fz_cp_async_wait_all();
-            fz_react_own<NX, RPI, true>(tile, btile, a, t_lo, t_hi, prow, pxs);
         } else {
             fz_load_incr<NX, NY, RPI>(tile, jb, a, r0, t_lo, t_hi, prow, px, pxs);
         }

@@ -2439,6 +2439,27 @@ struct Plan : PlanBase {
         if (!d_params) return fail(ATM_ERR_INVALID_ARG, "null parameters");
         ATM_CK(cudaMemcpyAsync(nn_params, d_params, (size_t)nn::param_count() * sizeof(float), cudaMemcpyDeviceToDevice, st));
         ATM_TRY(nn::pack(nn_params, &net, st));
+        // Psi_NN(0) = 0, as Phi^m(0) = 0 for the heat and Allen-Cahn steps (the
+        // first cycles feed the coarse level mostly zero states): the network's
+        // output for the zero state is a constant field c (a constant input stays
+        // constant through circular convolutions), computed here by the
+        // inference kernels themselves; the handle's copy of the last bias is
+        // lowered by c.  Scratch: two states of the snapshot array.
+        {
+            const size_t nst = (size_t)nsp;
+            ATM_CK(cudaMemsetAsync(snapshot, 0, 2 * nst * sizeof(T), st));
+            Job<T> j = job(snapshot, snapshot + nst);
+            ATM_CK(cudaMemcpyAsync(d_dyn, &j, sizeof(Job<T>), cudaMemcpyHostToDevice, st));
+            ATM_TRY(nn::infer_jobs<T>(net, d_dyn, 1, 0, nullptr, pb.ny, pb.nx, nn_scratch, 1, nn_err, st, nullptr));
+            T c = 0;
+            ATM_CK(cudaMemcpyAsync(&c, snapshot + nst, sizeof(T), cudaMemcpyDeviceToHost, st));
+            float b = 0;
+            float *bias = nn_params + nn::last_bias_offset();
+            ATM_CK(cudaMemcpyAsync(&b, bias, sizeof(float), cudaMemcpyDeviceToHost, st));
+            ATM_CK(cudaStreamSynchronize(st));
+            b -= (float)c;
+            ATM_CK(cudaMemcpyAsync(bias, &b, sizeof(float), cudaMemcpyHostToDevice, st));
+        }
         ATM_CK(cudaStreamSynchronize(st));
         net_ready = true;
         return ATM_OK;

@@ -68,6 +68,8 @@ atm_status check_grid(int H, int W)
 
 int param_count() { return kParams; }
 
+int last_bias_offset() { return layer_offset(kLayers - 1) + layer_wsize(kLayers - 1); }
+
 size_t packed_bytes() { return align256((size_t)packed_total() * 2); }
 
 void carve_packed(void *base, Net *net)

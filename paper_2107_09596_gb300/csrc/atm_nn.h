@@ -21,6 +21,7 @@ struct Net {
 };
 
 int param_count();
+int last_bias_offset();                                   // index of the output layer's bias
 size_t packed_bytes();                                   // all packed operands
 size_t infer_scratch_bytes(int chunk, int H, int W);      // activations for `chunk` images
 size_t train_scratch_bytes(int batch, int H, int W);

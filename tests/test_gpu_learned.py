@@ -308,3 +308,29 @@ def test_method_pairs_give_a_coarse_propagator_that_beats_the_classical_one(torc
           f"\n  classical log10 r: {np.round(np.log10(cl.residual_history()), 1)}")
     assert r_h["converged"] and not r_h["fallback"], r_h
     assert rel_l2(h.solution().cpu().numpy(), oracle.sequential(oc, u0)) <= 1e-8
+
+
+def test_installed_network_maps_zero_to_zero(torch):
+    """A handle's Psi_NN keeps the zero state at zero (as Phi^m does for the
+    heat and Allen-Cahn steps): the output layer's bias of the handle's copy is
+    shifted by the network's constant output for the zero state.  States away
+    from zero move by that constant only: Psi_NN(u) - Psi_NN(0) equals the
+    standalone network's u + N(u) - N(0)."""
+    oc, gp, gs = pair(kind="ac", nx=64, ny=64, dt=1e-4, nt=257, m=(16, 4), k=3, nu=1,
+                      coarse_prop=atm.PROP_LEARNED)
+    params = make_params(7)
+    p = torch.as_tensor(flat(params), dtype=torch.float32, device="cuda:0")
+    s = atm.Solver(gp, gs)
+    s.set_learned_coarse(p)
+    z = torch.zeros((1, 64, 64), dtype=torch.float64, device="cuda:0")
+    net = atm.LearnedCoarse()
+    c = float(net.apply(p, torch.zeros((1, 64, 64), dtype=torch.float32)).cpu().numpy().mean())
+    assert abs(c) > 1e-3                     # the raw network does not keep zero
+    assert float(s.apply_propagator(1, z).abs().max()) <= 1e-6 * max(1.0, abs(c))
+    u = I.uniform_field((2, 64, 64), 11, -1.0, 1.0)
+    got = s.apply_propagator(1, torch.as_tensor(u, device="cuda:0")).cpu().numpy()
+    raw = net.apply(p, torch.as_tensor(u, dtype=torch.float32)).cpu().numpy().astype(np.float64)
+    assert rel_l2(got - u, raw - u.astype(np.float32) - c) <= 1e-3
+    # and the caller's parameters are unchanged
+    assert np.array_equal(p.cpu().numpy(), flat(params).astype(np.float32))
+    s.close()
