@@ -630,6 +630,11 @@ def main():
     ap.add_argument("--nested", action="store_true", help="nested iteration: start from the coarse hierarchy")
     ap.add_argument("--fcycle", action="store_true", help="F-cycles instead of V-cycles")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tune-cache-out", default=None,
+                    help="write the autotuner's kernel choices of this run to this file")
+    ap.add_argument("--tune-cache-in", default=None,
+                    help="use the kernel choices recorded in this file (e.g. a profiler run replaying the kernels "
+                         "of a timed run)")
     args = ap.parse_args()
     if args.workload == "batch64":
         run_batch(args)
@@ -660,6 +665,9 @@ def main():
     torch.cuda.set_device(device)
     atm._build.build()
     prec = PRECISIONS[args.precision](atm)
+    if args.tune_cache_in:
+        with open(args.tune_cache_in) as fh:
+            atm.tune_cache_import(fh.read())
     learned_info = None
     if args.coarse in ("learned", "correction"):
         nn_params, learned_info = train_learned(atm, w, device, args.train_steps,
@@ -847,6 +855,9 @@ def main():
                 "roofline": roof, "roofline_other": roof_other, "cpu_baseline": cpu, "err_vs_oracle": err,
                 "clocks": clk}
         print(json.dumps(line), flush=True)
+    if args.tune_cache_out and rank == 0:
+        with open(args.tune_cache_out, "w") as fh:
+            fh.write(atm.tune_cache_export())
     solver.close()
     if dist is not None:
         dist.destroy_process_group()

@@ -452,6 +452,20 @@ atm_status atm_apply_propagator_noalloc(const atm_problem *prob, const atm_solve
  * nothing. */
 atm_status atm_measure_fp64_rate(void *cuda_stream, double *tflops);
 
+/* Kernel choices of the create-time autotuner (the paper has no counterpart).
+ * Handles of the same configuration share them for the life of the process
+ * (the same kernels, bit-identical results).  Export writes them as text,
+ * one line per configuration ("key<TAB>v,v,...", NUL-terminated) into buf;
+ * *len receives the bytes needed (call with buf = NULL to ask); a buffer
+ * shorter than that returns ATM_ERR_INVALID_ARG.  Import adds such text to
+ * the process's choices (replacing configurations it names), so that a later
+ * atm_create of those configurations skips the timing and uses the recorded
+ * kernels: a second process (a profiler run, a service restart) then runs the
+ * kernels the first one chose.  Malformed text returns ATM_ERR_INVALID_ARG and
+ * imports nothing.  Host-only; allocate nothing on the device. */
+atm_status atm_tune_cache_export(char *buf, size_t cap, size_t *len);
+atm_status atm_tune_cache_import(const char *text);
+
 /* Message of the calling thread's last error ("" if none). */
 const char *atm_last_error(void);
 

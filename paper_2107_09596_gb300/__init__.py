@@ -86,7 +86,7 @@ EXPORTS = ["atm_workspace_size", "atm_create", "atm_set_initial_condition",
            "atm_nn_param_count", "atm_nn_workspace_size", "atm_nn_apply", "atm_nn_loss_grad",
            "atm_train_learned_coarse", "atm_set_learned_coarse", "atm_batch_solve", "atm_last_error",
            "atm_get_sweep_config", "atm_set_rhs", "atm_get_newton_stats", "atm_measure_fp64_rate",
-           "atm_destroy"]
+           "atm_tune_cache_export", "atm_tune_cache_import", "atm_destroy"]
 
 _lib = None
 
@@ -136,6 +136,8 @@ def load(build_if_missing: bool = True):
     L.atm_set_learned_coarse.argtypes = [vp, vp]
     L.atm_batch_solve.argtypes = [ctypes.POINTER(vp), i, vp, ctypes.POINTER(Result)]
     L.atm_measure_fp64_rate.argtypes = [vp, ctypes.POINTER(d)]
+    L.atm_tune_cache_export.argtypes = [ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
+    L.atm_tune_cache_import.argtypes = [ctypes.c_char_p]
     L.atm_last_error.restype = ctypes.c_char_p
     L.atm_destroy.argtypes = [vp]
     for name in EXPORTS:
@@ -205,6 +207,20 @@ def measure_fp64_rate(stream=None) -> float:
     v = ctypes.c_double()
     _check(load().atm_measure_fp64_rate(ctypes.c_void_p(st.cuda_stream), ctypes.byref(v)))
     return v.value
+
+
+def tune_cache_export() -> str:
+    """The autotuner's kernel choices of this process, as text."""
+    n = ctypes.c_size_t()
+    _check(load().atm_tune_cache_export(None, 0, ctypes.byref(n)))
+    buf = ctypes.create_string_buffer(n.value)
+    _check(load().atm_tune_cache_export(buf, n.value, ctypes.byref(n)))
+    return buf.value.decode()
+
+
+def tune_cache_import(text: str) -> None:
+    """Add kernel choices exported by tune_cache_export (this or another process)."""
+    _check(load().atm_tune_cache_import(text.encode()))
 
 
 def _ptr(x) -> int:

@@ -1,6 +1,8 @@
 // atm_api.cu -- the extern "C" entry points declared in include/atm.h.
 // Argument marshalling and validation only; every step of the sweep runs in
 // the kernels of atm_kernels.cuh, driven by the plan in atm_host.cuh.
+#include <cstdlib>
+
 #include "atm_host.cuh"
 
 struct atm_handle {
@@ -324,6 +326,60 @@ atm_status atm_measure_fp64_rate(void *cuda_stream, double *tflops)
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     *tflops = 2.0 * 8.0 * iters * (double)blocks * threads / (best * 1e-3) / 1e12;
+    return ATM_OK;
+}
+
+atm_status atm_tune_cache_export(char *buf, size_t cap, size_t *len)
+{
+    atm::last_error().clear();
+    if (!len) return atm::fail(ATM_ERR_INVALID_ARG, "null len");
+    std::string out;
+    {
+        std::lock_guard<std::mutex> lk(atm::tune_cache().mu);
+        for (const auto &kv : atm::tune_cache().choice) {
+            out += kv.first;
+            out += '\t';
+            for (size_t i = 0; i < kv.second.size(); ++i) {
+                if (i) out += ',';
+                out += std::to_string(kv.second[i]);
+            }
+            out += '\n';
+        }
+    }
+    *len = out.size() + 1;
+    if (!buf) return ATM_OK;
+    if (cap < out.size() + 1) return atm::fail(ATM_ERR_INVALID_ARG, "buffer of %zu bytes, %zu needed", cap, out.size() + 1);
+    std::memcpy(buf, out.c_str(), out.size() + 1);
+    return ATM_OK;
+}
+
+atm_status atm_tune_cache_import(const char *text)
+{
+    atm::last_error().clear();
+    if (!text) return atm::fail(ATM_ERR_INVALID_ARG, "null text");
+    std::map<std::string, std::vector<int>> add;
+    const char *p = text;
+    while (*p) {
+        const char *nl = std::strchr(p, '\n');
+        const std::string line(p, nl ? (size_t)(nl - p) : std::strlen(p));
+        p = nl ? nl + 1 : p + line.size();
+        if (line.empty()) continue;
+        const size_t tab = line.find('\t');
+        if (tab == std::string::npos || tab == 0) return atm::fail(ATM_ERR_INVALID_ARG, "malformed line: %s", line.c_str());
+        std::vector<int> v;
+        size_t q = tab + 1;
+        while (q < line.size()) {
+            char *end = nullptr;
+            const long x = std::strtol(line.c_str() + q, &end, 10);
+            if (end == line.c_str() + q) return atm::fail(ATM_ERR_INVALID_ARG, "malformed value in: %s", line.c_str());
+            v.push_back((int)x);
+            q = (size_t)(end - line.c_str());
+            if (q < line.size() && line[q] == ',') ++q;
+        }
+        add[line.substr(0, tab)] = v;
+    }
+    std::lock_guard<std::mutex> lk(atm::tune_cache().mu);
+    for (auto &kv : add) atm::tune_cache().choice[kv.first] = kv.second;
     return ATM_OK;
 }
 

@@ -1906,7 +1906,18 @@ struct Plan : PlanBase {
         {
             std::lock_guard<std::mutex> lk(tune_cache().mu);
             auto it = tune_cache().choice.find(tkey);
-            if (it != tune_cache().choice.end() && (int)it->second.size() == 3 * L + 1) {
+            // an entry (possibly imported) is used only when every index names a
+            // shape this plan has
+            bool valid = it != tune_cache().choice.end() && (int)it->second.size() == 3 * L + 1 &&
+                         it->second[0] >= 0;
+            for (int l = 0; valid && l < L; ++l) {
+                const std::vector<int> &v = it->second;
+                valid = v[1 + l] >= -1 && v[1 + l] < (int)lv[l].fused.size() && v[1 + L + l] >= -1 &&
+                        v[1 + L + l] < (int)lv[l].chains.size() && v[1 + 2 * L + l] >= -1 &&
+                        v[1 + 2 * L + l] < (int)lv[l].df.size() &&
+                        (lv[l].df.empty() || v[1 + 2 * L + l] >= 0) && (lv[l].chains.empty() || v[1 + L + l] >= 0);
+            }
+            if (valid) {
                 chunk = it->second[0];
                 for (int l = 0; l < L; ++l) lv[l].fz = it->second[1 + l];
                 for (int l = 0; l < L; ++l) lv[l].chz = it->second[1 + L + l];

@@ -100,3 +100,17 @@ def test_gray_scott_workspace_and_validation(atm):
     # any grid size from 8 to 512 is allowed
     atm.workspace_size(atm.make_problem(atm.GRAY_SCOTT, 40, 24, lx=2.5, ly=1.5, dt=0.01, nt_points=65),
                        atm.make_solver(atm.MGRIT, m=(8,), k=1))
+
+
+def test_tune_cache_round_trip_and_malformed_text(atm):
+    """The autotuner's choices as text (no device work): an imported line is
+    exported again; malformed text is rejected and imports nothing."""
+    before = atm.tune_cache_export()
+    atm.tune_cache_import("testkey d0 T4\t0,1,-1,2\n")
+    out = atm.tune_cache_export()
+    assert "testkey d0 T4\t0,1,-1,2\n" in out
+    for bad in ("no tab here\n", "\t1,2\n", "k\t1,x\n"):
+        with pytest.raises(atm.AtmError):
+            atm.tune_cache_import(bad)
+    assert atm.tune_cache_export() == out
+    assert set(before.splitlines()) <= set(out.splitlines())
