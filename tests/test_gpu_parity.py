@@ -51,6 +51,21 @@ PROP_CASES = {
 }
 
 
+def fp32_bar(kw, level):
+    """FP32 bar of one application (FP32 rounding of ~20 operations per value,
+    amplified by the line solve's condition number 1 + 4a, a = f D / dx^2):
+    max(3e-6, 2.5e-7 (1 + 4a)); 3e-6 up to 256^2, 1.3e-5 on the 1024^2 fine level."""
+    D = kw["dt"]
+    for j in range(level):
+        D *= kw["m"][j]
+    if kw["kind"] == "heat1d":
+        a = D / (kw.get("lx", 1.0) / (kw["nx"] + 1)) ** 2
+    else:
+        f = 0.5 if level == 0 and kw.get("fine_prop", atm.PROP_PR_ADI) == atm.PROP_PR_ADI else 1.0
+        a = f * D / min(kw.get("lx", 1.0) / kw["nx"], kw.get("ly", 1.0) / kw["ny"]) ** 2
+    return max(3e-6, 2.5e-7 * (1 + 4 * a))
+
+
 @pytest.mark.parametrize("prec", [atm.FP64, atm.FP32])
 @pytest.mark.parametrize("case", sorted(PROP_CASES))
 def test_propagator_matches_oracle(torch, case, prec):
@@ -63,7 +78,7 @@ def test_propagator_matches_oracle(torch, case, prec):
     for level in range(len(kw["m"]) + 1):
         want = oracle.apply_prop(oc, level, x)
         got = s.apply_propagator(level, dev(torch, x)).cpu().numpy()
-        tol = 1e-13 if prec == atm.FP64 else 3e-6
+        tol = 1e-13 if prec == atm.FP64 else fp32_bar(kw, level)
         for j in range(nstates):
             assert rel_l2(got[j], want[j]) <= tol, (level, j, rel_l2(got[j], want[j]))
 
