@@ -704,7 +704,7 @@ def main():
         res = step()
         launches += res["launches"]
         iters.append(res["iterations"])
-        fallbacks.append((res["fallback"], res["fallback_iterations"]))
+        fallbacks.append((res["fallback"], res["fallback_iterations"], res["fallback_residual"]))
     e1.record(solver.stream)
     torch.cuda.synchronize(device)
     clk = clocks.stop()
@@ -848,8 +848,9 @@ def main():
                 "gpu_launches": int(launches),
                 "coarse": args.coarse,
                 "learned": None if learned_info is None else dict(
-                    learned_info, fallback_in_timed_steps=sum(f for f, _ in fallbacks),
-                    cycles_with_network_before_fallback=[i for _, i in fallbacks]),
+                    learned_info, fallback_in_timed_steps=sum(f for f, _, _ in fallbacks),
+                    cycles_with_network_before_fallback=[i for _, i, _ in fallbacks],
+                    residual_ending_the_network_attempt=[r for _, _, r in fallbacks]),
                 "kernels_per_level": [solver.sweep_config(l) for l in range(len(w["m"]) + 1)]
                 if args.algorithm != "seq" else [solver.sweep_config(0)],
                 "roofline": roof, "roofline_other": roof_other, "cpu_baseline": cpu, "err_vs_oracle": err,

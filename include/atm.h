@@ -202,6 +202,7 @@ typedef struct {
     double time_ms;            /* device time of the solve (CUDA events) */
     int fallback;              /* 1 if a learned coarse propagator was replaced by the classical one */
     int fallback_iterations;   /* cycles run with the learned propagator before the fallback */
+    double fallback_residual;  /* the residual that ended the learned propagator's attempt (0: none) */
 } atm_result;
 
 typedef struct atm_handle atm_handle;

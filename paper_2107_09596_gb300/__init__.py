@@ -75,7 +75,7 @@ class Result(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int),
                 ("initial_residual", ctypes.c_double), ("final_residual", ctypes.c_double),
                 ("time_ms", ctypes.c_double), ("fallback", ctypes.c_int),
-                ("fallback_iterations", ctypes.c_int)]
+                ("fallback_iterations", ctypes.c_int), ("fallback_residual", ctypes.c_double)]
 
 
 EXPORTS = ["atm_workspace_size", "atm_create", "atm_set_initial_condition",
@@ -314,7 +314,8 @@ class Solver:
         return {"status": STATUS[st], "iterations": r.iterations, "converged": bool(r.converged),
                 "initial_residual": r.initial_residual, "final_residual": r.final_residual,
                 "time_ms": r.time_ms, "launches": load().atm_last_launch_count(self.handle),
-                "fallback": bool(r.fallback), "fallback_iterations": r.fallback_iterations}
+                "fallback": bool(r.fallback), "fallback_iterations": r.fallback_iterations,
+                "fallback_residual": r.fallback_residual}
 
     def residual_history(self, cap=4096) -> np.ndarray:
         buf = np.zeros(cap)

@@ -2113,6 +2113,7 @@ struct Plan : PlanBase {
         launches += l1;
         second.fallback = 1;
         second.fallback_iterations = first.iterations;
+        second.fallback_residual = first.final_residual;
         second.time_ms += first.time_ms;
         if (res) *res = second;
         return s2;
