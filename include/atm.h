@@ -400,6 +400,9 @@ atm_status atm_train_learned_coarse(float *d_params, float *d_adam, const float 
  * mostly zero states): the network's output for the zero state is a constant
  * field (circular convolutions of a constant are constant), computed once here
  * by the inference kernels.  The caller's parameters are not changed.
+ * For Allen-Cahn the learned level's output is projected onto [-1, 1], the
+ * interval the equation keeps invariant (maximum principle) and that the
+ * classical coarse propagator respects.
  * Fallback: such a handle keeps the classical split-BE ADI propagator for
  * level 1 too.  Every atm_solve starts with the network; when a cycle gives a
  * non-finite residual or one above 1e3 times the smallest so far, it restores

@@ -1866,6 +1866,10 @@ struct Plan : PlanBase {
         if (any_learned) {
             nn::carve_packed(nn_packed, &net);
             net.params = nn_params;
+            // Allen-Cahn keeps [-1, 1] invariant (maximum principle), as the
+            // classical coarse propagator (exact reaction flow, backward Euler)
+            // does: the learned one is projected onto it
+            net.clamp = pb.kind == ATM_ALLEN_CAHN ? 1.f : 0.f;
             ATM_TRY(nn::prepare<T>());
             ATM_CK(cudaMemsetAsync(nn_err, 0, sizeof(int), st));
         }
@@ -2462,7 +2466,9 @@ struct Plan : PlanBase {
             ATM_CK(cudaMemsetAsync(snapshot, 0, 2 * nst * sizeof(T), st));
             Job<T> j = job(snapshot, snapshot + nst);
             ATM_CK(cudaMemcpyAsync(d_dyn, &j, sizeof(Job<T>), cudaMemcpyHostToDevice, st));
-            ATM_TRY(nn::infer_jobs<T>(net, d_dyn, 1, 0, nullptr, pb.ny, pb.nx, nn_scratch, 1, nn_err, st, nullptr));
+            nn::Net raw = net;
+            raw.clamp = 0.f;
+            ATM_TRY(nn::infer_jobs<T>(raw, d_dyn, 1, 0, nullptr, pb.ny, pb.nx, nn_scratch, 1, nn_err, st, nullptr));
             T c = 0;
             ATM_CK(cudaMemcpyAsync(&c, snapshot + nst, sizeof(T), cudaMemcpyDeviceToHost, st));
             float b = 0;

@@ -144,6 +144,7 @@ atm_status infer_jobs(const Net &net, const Job<T> *d_jobs, int njobs, int neg, 
         a.w = net.fwd[kLayers - 1];
         a.bias = bias_of(net.params, kLayers - 1);
         a.neg = neg;
+        a.clampv = net.clamp;
         a.partials = partials ? partials + (size_t)j0 * tiles : nullptr;
         a.skip = skip ? skip + (size_t)j0 * P : nullptr;
         ATM_TRY((launch_conv<T, IN_BF16, 16, EPI_LAST>(a, nj, st)));

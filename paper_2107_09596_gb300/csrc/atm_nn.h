@@ -16,6 +16,7 @@ namespace nn {
 // (biases are read from here) and the packed BF16 operands.
 struct Net {
     const float *params = nullptr;
+    float clamp = 0.f;   // > 0: outputs projected onto [-clamp, clamp] (inference on a handle's jobs)
     __nv_bfloat16 *fwd[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     __nv_bfloat16 *bwd[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
 };

@@ -102,6 +102,7 @@ struct ConvArgs {
     int neg;
     double *partials;                // EPI_LAST with jobs and residuals: per-CTA sums of r^2
     int *err;                        // set to 1 when an MMA wait times out
+    float clampv;                    // EPI_LAST with jobs, > 0: Psi_NN projected onto [-clampv, clampv]
 };
 
 // Gather of one pixel's A row into the operand tile.
@@ -268,7 +269,8 @@ __global__ void __launch_bounds__(kTile) conv_umma_kernel(const __grid_constant_
         const size_t q = (size_t)p;
         if (a.jobs) {
             const Job<T> jb = a.jobs[img];
-            const T phi = (a.skip ? a.skip[(size_t)img * a.H * a.W + q] : jb.in[q]) + (T)z;
+            T phi = (a.skip ? a.skip[(size_t)img * a.H * a.W + q] : jb.in[q]) + (T)z;
+            if (a.clampv > 0.f) phi = fmin(fmax(phi, (T)-a.clampv), (T)a.clampv);
             double r2 = 0.0;
             if (jb.sub) apply_epilogue<T, true>(jb, q, phi, a.neg, r2);
             else apply_epilogue<T, false>(jb, q, phi, a.neg, r2);

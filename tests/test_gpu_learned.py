@@ -316,7 +316,7 @@ def test_installed_network_maps_zero_to_zero(torch):
     shifted by the network's constant output for the zero state.  States away
     from zero move by that constant only: Psi_NN(u) - Psi_NN(0) equals the
     standalone network's u + N(u) - N(0)."""
-    oc, gp, gs = pair(kind="ac", nx=64, ny=64, dt=1e-4, nt=257, m=(16, 4), k=3, nu=1,
+    oc, gp, gs = pair(kind="heat2d", nx=64, ny=64, dt=1e-4, nt=257, m=(16, 4), k=3, nu=1,
                       coarse_prop=atm.PROP_LEARNED)
     params = make_params(7)
     p = torch.as_tensor(flat(params), dtype=torch.float32, device="cuda:0")
@@ -334,3 +334,16 @@ def test_installed_network_maps_zero_to_zero(torch):
     # and the caller's parameters are unchanged
     assert np.array_equal(p.cpu().numpy(), flat(params).astype(np.float32))
     s.close()
+    # Allen-Cahn: the learned level's output is projected onto [-1, 1], where
+    # the network's own output stays inside it is unchanged
+    _, gpa, gsa = pair(kind="ac", nx=64, ny=64, dt=1e-4, nt=257, m=(16, 4), k=3, nu=1,
+                       coarse_prop=atm.PROP_LEARNED)
+    a = atm.Solver(gpa, gsa)
+    a.set_learned_coarse(p)
+    big = 3.0 * u
+    got = a.apply_propagator(1, torch.as_tensor(big, device="cuda:0")).cpu().numpy()
+    raw = net.apply(p, torch.as_tensor(big, dtype=torch.float32)).cpu().numpy().astype(np.float64) - c
+    assert np.abs(got).max() <= 1.0
+    inside = np.abs(raw) < 0.999
+    assert inside.any() and np.allclose(got[inside], raw[inside], atol=1e-3)
+    a.close()
