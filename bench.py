@@ -410,6 +410,47 @@ def run_gray_scott(args):
     solver.close()
 
 
+def run_nn_probe(args):
+    """Inference of the learned coarse propagator alone (the tensor-core
+    convolutions of Psi_NN, five layers) on 32 states of the workload's grid,
+    timed with CUDA events on the network's stream, against the measured bf16
+    tensor peak.  Algorithmic work per pixel: 2 * 9 * (1*32 + 3*32*32 + 32*1)
+    = 56,448 flop (the kernels pad the first layer's K and the last layer's N
+    to 16, which is not counted)."""
+    import torch
+    import paper_2107_09596_gb300 as atm
+    atm._build.build()
+    w = WORKLOADS[args.workload]
+    n, states = w["n"], 32
+    net = atm.LearnedCoarse()
+    flat = np.concatenate([np.concatenate([wt.ravel(), b.ravel()]) for (wt, b) in I.conv_net_init(7)])
+    params = torch.as_tensor(flat, dtype=torch.float32, device="cuda:0")
+    x = torch.as_tensor(I.uniform_field((states, n, n), 1, -1.0, 1.0), dtype=torch.float32, device="cuda:0")
+    for _ in range(max(args.warmup, 1)):
+        net.apply(params, x)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = max(args.steps, 1)
+    e0.record(net.stream)
+    for _ in range(reps):
+        net.apply(params, x)
+    e1.record(net.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    flop = 2 * 9 * (1 * 32 + 3 * 32 * 32 + 32 * 1) * n * n * states
+    mp = load_json(os.path.join(ROOT, "MEASURED_PEAKS.json"), {}) or {}
+    peak = mp.get("bf16_tflops", 1900.0)
+    ach = flop / (ms / 1e3) / 1e12
+    print(json.dumps({"probe": "learned coarse propagator inference (conv_umma_kernel x 5 layers)",
+                      "states": states, "grid": [n, n], "ms_per_apply": ms,
+                      "roofline": {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                                   "frac": ach / peak,
+                                   "peak_source": ("measured cuBLAS bf16 burst (MEASURED_PEAKS.json)"
+                                                   if "bf16_tflops" in mp else "fallback"),
+                                   "algorithmic": "56,448 flop per pixel (five 3x3 layers, 1-32-32-32-32-1)"}}),
+          flush=True)
+
+
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -630,6 +671,9 @@ def main():
     ap.add_argument("--nested", action="store_true", help="nested iteration: start from the coarse hierarchy")
     ap.add_argument("--fcycle", action="store_true", help="F-cycles instead of V-cycles")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--nn-probe", action="store_true",
+                    help="time the learned propagator's tensor-core inference alone (32 states of the workload's "
+                         "grid) and print its roofline")
     ap.add_argument("--tune-cache-out", default=None,
                     help="write the autotuner's kernel choices of this run to this file")
     ap.add_argument("--tune-cache-in", default=None,
@@ -648,6 +692,9 @@ def main():
             run_gs_probe(args)
         else:
             run_gray_scott(args)
+        return
+    if args.nn_probe:
+        run_nn_probe(args)
         return
     w = dict(WORKLOADS[args.workload])
     if args.max_iter is not None:
