@@ -157,9 +157,10 @@ def batch_descs(atm, count=64, seed=0, precision="fp32r", storage="cpoint"):
     """The batched workload: `count` problems drawn by atm_inputs.batch_problem_draws
     (kind in {heat2d, Allen-Cahn}, n in {64..512}, nt in {1025, 4097, 16385},
     m in {8, 16}); AT-MGRIT FCF with two coarsenings when the coarse grid allows,
-    k = ceil(N_c / 4); dt = 1e-4, eps = 0.02.  fp32r (FP32 propagation, FP64
-    residual): stop at an RMS C-point residual of 1e-10 per value; fp32: at an
-    RMS residual of 1e-6 (the FP32 floor is near 1e-7)."""
+    k = ceil(N_c / 4); dt = 1e-4, eps = 0.02.  fp32r / fp32rf (FP32 propagation,
+    FP64 residual in FP64 or float-float) and fp64: stop at an RMS C-point
+    residual of 1e-10 per value; fp32: at an RMS residual of 1e-6 (the FP32 floor
+    is near 1e-7)."""
     out = []
     for d in I.batch_problem_draws(count, seed):
         kind = atm.ALLEN_CAHN if d["kind"] == "allen_cahn" else atm.HEAT2D
@@ -169,11 +170,12 @@ def batch_descs(atm, count=64, seed=0, precision="fp32r", storage="cpoint"):
         ms = (m, m) if (nc - 1) // m + 1 >= 3 else (m,)
         nco = ((nc - 1) // m + 1) if len(ms) == 2 else nc
         k = max(2, (nco + 3) // 4)
-        rms = 1e-10 if precision == "fp32r" else 1e-6
+        rms = 1e-6 if precision == "fp32" else 1e-10
         pts = nc if storage == "cpoint" else nt
+        prec = {"fp32r": atm.FP32_REFINED, "fp32rf": atm.FP32_REFINED_FF, "fp64": atm.FP64,
+                "fp32": atm.FP32}[precision]
         desc = atm.make_solver(atm.AT_MGRIT, m=ms, k=k, nu=1, tol=rms * np.sqrt(pts * n * n),
-                               max_iter=40, precision=atm.FP32_REFINED if precision == "fp32r" else atm.FP32,
-                               use_graph=2, cpoint_only=storage == "cpoint")
+                               max_iter=40, precision=prec, use_graph=2, cpoint_only=storage == "cpoint")
         out.append((d, prob, desc))
     return out
 
@@ -185,7 +187,8 @@ def run_batch(args):
     import paper_2107_09596_gb300 as atm
     device = torch.device("cuda", 0)
     atm._build.build()
-    descs = batch_descs(atm, precision="fp32r" if args.precision == "fp32r" else "fp32", storage=args.storage)
+    bprec = args.precision if args.precision in ("fp32r", "fp32rf", "fp32") else "fp32rf"
+    descs = batch_descs(atm, precision=bprec, storage=args.storage)
     budget = 240e9
     groups, cur, used = [], [], 0
     for item in descs:
@@ -198,7 +201,7 @@ def run_batch(args):
     groups.append(cur)
     total_steps = sum(d["nt"] - 1 for d, _, _ in descs)
     t_batch = t_single = 0.0
-    iters_b, iters_s, statuses = [], [], []
+    iters_b, iters_s, statuses, failed = [], [], [], []
     for g in groups:
         solvers = [atm.Solver(p, s, device=device) for _, p, s in g]
         for (d, _, _), sv in zip(g, solvers):
@@ -222,21 +225,45 @@ def run_batch(args):
         t_batch += time.perf_counter() - t
         iters_b += [r["iterations"] for r in res]
         statuses += [r["converged"] for r in res]
+        for (d, p, s), sv, r in zip(g, solvers, res):
+            if not r["converged"]:
+                h = sv.residual_history()
+                failed.append({"kind": d["kind"], "n": d["n"], "nt": d["nt"], "m": list(s.m[:s.levels - 1]),
+                               "k": s.k, "cycles": r["iterations"], "tol": s.tol,
+                               "residual_history": [float(x) for x in h[:8]] + ([float(h[-1])] if len(h) > 8 else [])})
         for sv in solvers:
             sv.close()
         del solvers
         torch.cuda.empty_cache()
+    # the plain FP64 form of the same problems to the same tolerances, one at a time
+    t_fp64, conv64 = None, None
+    if args.batch_fp64:
+        t_fp64, conv64 = 0.0, 0
+        for d, p, s in batch_descs(atm, precision="fp64", storage=args.storage):
+            sv = atm.Solver(p, s, device=device)
+            sv.set_initial_condition(torch.as_tensor(I.uniform_field((d["n"], d["n"]), d["seed"]),
+                                                     dtype=torch.float64, device=device))
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            r = sv.solve()
+            torch.cuda.synchronize()
+            t_fp64 += time.perf_counter() - t
+            conv64 += int(r["converged"])
+            sv.close()
+            torch.cuda.empty_cache()
     value = total_steps / t_batch
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 0,
             "ms_per_step": t_batch * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32+f64" if args.precision == "fp32r" else "f32", "data": "synthetic",
+            "dtype": {"fp32r": "f32+f64", "fp32rf": "f32+f32x2", "fp32": "f32"}[bprec], "data": "synthetic",
             "config": {"workload": "batch64", "problems": len(descs), "groups": len(groups),
-                       "precision": args.precision, "storage": args.storage,
+                       "precision": bprec, "storage": args.storage,
                        "memory_budget_gb_per_group": budget / 1e9, "l2": "inputs larger than L2"},
             "one_at_a_time": {"value": total_steps / t_single, "ms": t_single * 1e3},
             "batched_speedup": t_single / t_batch,
             "iterations_batched": iters_b, "iterations_one_at_a_time": iters_s,
-            "converged": int(sum(statuses))}
+            "converged": int(sum(statuses)), "not_converged": failed,
+            "plain_fp64_one_at_a_time": None if t_fp64 is None else {
+                "ms": t_fp64 * 1e3, "value": total_steps / t_fp64, "converged": conv64}}
     print(json.dumps(line), flush=True)
 
 
@@ -671,6 +698,8 @@ def main():
     ap.add_argument("--nested", action="store_true", help="nested iteration: start from the coarse hierarchy")
     ap.add_argument("--fcycle", action="store_true", help="F-cycles instead of V-cycles")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-fp64", action="store_true",
+                    help="batch64: also solve the problems in plain FP64, one at a time, to the same tolerances")
     ap.add_argument("--nn-probe", action="store_true",
                     help="time the learned propagator's tensor-core inference alone (32 states of the workload's "
                          "grid) and print its roofline")

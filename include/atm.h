@@ -334,8 +334,9 @@ atm_status atm_get_newton_stats(atm_handle *h, long long *out);
  * residual below its tol (or max_iter, divergence); the problems' loops are
  * independent branches, so the GPU runs them concurrently and each stops on
  * its own.  Handles may differ in problem, grid, levels, m, k and precision
- * (FP64, FP32); not supported: sequential stepping, the refined mode and the
- * learned propagator (ATM_ERR_UNSUPPORTED).  Each handle's iterate, residual
+ * (every precision; the refined modes' loop is the whole refinement loop); not
+ * supported: sequential stepping and the learned propagator
+ * (ATM_ERR_UNSUPPORTED).  Each handle's iterate, residual
  * history and outs[i] are filled as by atm_solve; the return value is the
  * first non-OK status of the problems.  Blocks until all are done. */
 atm_status atm_batch_solve(atm_handle *const *hs, int n, void *cuda_stream, atm_result *outs);
