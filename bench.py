@@ -468,7 +468,7 @@ def run_nn_probe(args):
     mp = load_json(os.path.join(ROOT, "MEASURED_PEAKS.json"), {}) or {}
     peak = mp.get("bf16_tflops", 1900.0)
     ach = flop / (ms / 1e3) / 1e12
-    print(json.dumps({"probe": "learned coarse propagator inference (conv_umma_kernel x 5 layers)",
+    print(json.dumps({"probe": "learned coarse propagator inference (five tcgen05 convolution layers)",
                       "states": states, "grid": [n, n], "ms_per_apply": ms,
                       "roofline": {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                                    "frac": ach / peak,

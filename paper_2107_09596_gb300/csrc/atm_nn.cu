@@ -24,21 +24,34 @@ size_t conv_smem()
     return (size_t)kTile * KTOT * 2 + (size_t)NOUT * KTOT * 2;
 }
 
+constexpr int kRowsRT = 4;   // image rows per CTA of conv_rows_kernel
+
 template <typename T, int SRC, int NOUT, int EPI>
 atm_status set_smem_attr()
 {
     ATM_CK(cudaFuncSetAttribute((const void *)conv_umma_kernel<T, SRC, NOUT, EPI>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)conv_smem<T, SRC, NOUT, EPI>()));
+    if constexpr (SRC == IN_BF16)
+        ATM_CK(cudaFuncSetAttribute((const void *)conv_rows_kernel<T, NOUT, EPI, kRowsRT>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, rows_smem_bytes(kRowsRT, NOUT)));
     return ATM_OK;
 }
 
 // Shared-memory attributes are set by prepare()/prepare_training() before
 // any launch (and before any stream capture).
+// A 32-channel input on rows that are whole 128-pixel segments goes to the
+// row-segment kernel (input staged once per CTA); the single-channel first
+// layer and narrower grids to the per-tile gather kernel.  Both give the same
+// values (the same products summed in the same order).
 template <typename T, int SRC, int NOUT, int EPI>
 atm_status launch_conv(const ConvArgs<T> &a, int nimg, cudaStream_t st)
 {
     const int tiles = a.H * a.W / kTile;
-    conv_umma_kernel<T, SRC, NOUT, EPI><<<dim3(tiles, nimg), kTile, conv_smem<T, SRC, NOUT, EPI>(), st>>>(a);
+    if (SRC == IN_BF16 && a.W % kTile == 0 && a.H % kRowsRT == 0)
+        conv_rows_kernel<T, NOUT, EPI, kRowsRT>
+            <<<dim3(a.W / kTile * (a.H / kRowsRT), nimg), kRowsNT, rows_smem_bytes(kRowsRT, NOUT), st>>>(a);
+    else
+        conv_umma_kernel<T, SRC, NOUT, EPI><<<dim3(tiles, nimg), kTile, conv_smem<T, SRC, NOUT, EPI>(), st>>>(a);
     return ATM_OK;
 }
 

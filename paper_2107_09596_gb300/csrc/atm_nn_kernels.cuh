@@ -140,6 +140,94 @@ __device__ __forceinline__ void gather_row(const ConvArgs<T> &a, unsigned char *
     }
 }
 
+// The NOUT accumulator columns of this thread's TMEM lane (32x32b shape: warp
+// w of a warpgroup reads lanes 32 (w % 4) ..), waited for, as FP32.
+template <int NOUT>
+__device__ __forceinline__ void tmem_ld_acc(uint32_t taddr, float (&acc)[NOUT])
+{
+    uint32_t v[NOUT];
+    if constexpr (NOUT == 32) {
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                     "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                     : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                       "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                       "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]),
+                       "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]),
+                       "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                     : "r"(taddr));
+    } else {
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                     : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                       "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                       "=r"(v[14]), "=r"(v[15])
+                     : "r"(taddr));
+    }
+    asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+    for (int n = 0; n < NOUT; ++n) acc[n] = __uint_as_float(v[n]);
+}
+
+// Epilogue of one output pixel p of image img from its NOUT accumulators:
+// bias + GELU (hidden layers), dz = acc * GELU'(z_prev) (backward data), or
+// Psi_NN(u) = u + z with the job epilogue (last layer).  Returns the pixel's
+// squared residual when the last layer's jobs carry one, else 0.
+template <typename T, int NOUT, int EPI>
+__device__ __forceinline__ double conv_epilogue(const ConvArgs<T> &a, float (&acc)[NOUT], int img, int p)
+{
+    double r2 = 0.0;
+    const size_t pix = (size_t)img * a.H * a.W + p;
+    if constexpr (EPI == EPI_HIDDEN || EPI == EPI_HIDDEN_INFER) {
+        __nv_bfloat162 hb[kCh / 2];
+#pragma unroll
+        for (int n = 0; n < kCh; n += 2) {
+            const float z0 = acc[n] + a.bias[n], z1 = acc[n + 1] + a.bias[n + 1];
+            if (EPI == EPI_HIDDEN) { acc[n] = z0; acc[n + 1] = z1; }
+            hb[n / 2] = __floats2bfloat162_rn(gelu_f(z0), gelu_f(z1));
+        }
+        uint4 *hdst = reinterpret_cast<uint4 *>(a.h_out + pix * kCh);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) hdst[j] = reinterpret_cast<uint4 *>(hb)[j];
+        if constexpr (EPI == EPI_HIDDEN) {
+            float4 *zdst = reinterpret_cast<float4 *>(a.z_out + pix * kCh);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) zdst[j] = make_float4(acc[4 * j], acc[4 * j + 1], acc[4 * j + 2], acc[4 * j + 3]);
+        }
+    } else if constexpr (EPI == EPI_BWD) {
+        const float4 *zp = reinterpret_cast<const float4 *>(a.z_prev + pix * kCh);
+        float dz[kCh];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const float4 z = zp[j];
+            dz[4 * j] = acc[4 * j] * gelu_grad_f(z.x);
+            dz[4 * j + 1] = acc[4 * j + 1] * gelu_grad_f(z.y);
+            dz[4 * j + 2] = acc[4 * j + 2] * gelu_grad_f(z.z);
+            dz[4 * j + 3] = acc[4 * j + 3] * gelu_grad_f(z.w);
+        }
+        float4 *ddst = reinterpret_cast<float4 *>(a.dz_out + pix * kCh);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) ddst[j] = make_float4(dz[4 * j], dz[4 * j + 1], dz[4 * j + 2], dz[4 * j + 3]);
+        __nv_bfloat162 hb[kCh / 2];
+#pragma unroll
+        for (int n = 0; n < kCh; n += 2) hb[n / 2] = __floats2bfloat162_rn(dz[n], dz[n + 1]);
+        uint4 *hdst = reinterpret_cast<uint4 *>(a.h_out + pix * kCh);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) hdst[j] = reinterpret_cast<uint4 *>(hb)[j];
+    } else {   // EPI_LAST: Psi_NN(u) = u + z
+        const float z = acc[0] + a.bias[0];
+        const size_t q = (size_t)p;
+        if (a.jobs) {
+            const Job<T> jb = a.jobs[img];
+            T phi = (a.skip ? a.skip[(size_t)img * a.H * a.W + q] : jb.in[q]) + (T)z;
+            if (a.clampv > 0.f) phi = fmin(fmax(phi, (T)-a.clampv), (T)a.clampv);
+            if (jb.sub) apply_epilogue<T, true>(jb, q, phi, a.neg, r2);
+            else apply_epilogue<T, false>(jb, q, phi, a.neg, r2);
+        } else {
+            a.out_f32[pix] = a.u_f32[pix] + z;
+        }
+    }
+    return r2;
+}
+
 // One 3x3 convolution layer over tiles of 128 pixels.  Grid: (H*W/128, images).
 template <typename T, int SRC, int NOUT, int EPI>
 __global__ void __launch_bounds__(kTile) conv_umma_kernel(const __grid_constant__ ConvArgs<T> a)
@@ -200,86 +288,162 @@ __global__ void __launch_bounds__(kTile) conv_umma_kernel(const __grid_constant_
     asm volatile("tcgen05.fence::after_thread_sync;");
     float acc[NOUT];
     if (done) {
-        uint32_t v[NOUT];
-        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
-        if constexpr (NOUT == 32) {
-            asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                         "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                         : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-                           "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-                           "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]),
-                           "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]),
-                           "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-                         : "r"(taddr));
-        } else {
-            asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                         : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-                           "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-                           "=r"(v[14]), "=r"(v[15])
-                         : "r"(taddr));
-        }
-        asm volatile("tcgen05.wait::ld.sync.aligned;");
-#pragma unroll
-        for (int n = 0; n < NOUT; ++n) acc[n] = __uint_as_float(v[n]);
+        tmem_ld_acc<NOUT>(tmem + ((uint32_t)(warp * 32) << 16), acc);
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem));
     if (!done) return;
 
-    const size_t pix = (size_t)img * a.H * a.W + p;
-    if constexpr (EPI == EPI_HIDDEN || EPI == EPI_HIDDEN_INFER) {
-        __nv_bfloat162 hb[kCh / 2];
-#pragma unroll
-        for (int n = 0; n < kCh; n += 2) {
-            const float z0 = acc[n] + a.bias[n], z1 = acc[n + 1] + a.bias[n + 1];
-            if (EPI == EPI_HIDDEN) { acc[n] = z0; acc[n + 1] = z1; }
-            hb[n / 2] = __floats2bfloat162_rn(gelu_f(z0), gelu_f(z1));
+    const double r2 = conv_epilogue<T, NOUT, EPI>(a, acc, img, p);
+    if constexpr (EPI == EPI_LAST) {
+        if (a.jobs && a.partials) {
+            const double s = block_sum(r2, red);
+            if (t == 0) a.partials[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = s;
         }
-        uint4 *hdst = reinterpret_cast<uint4 *>(a.h_out + pix * kCh);
-#pragma unroll
-        for (int j = 0; j < 4; ++j) hdst[j] = reinterpret_cast<uint4 *>(hb)[j];
-        if constexpr (EPI == EPI_HIDDEN) {
-            float4 *zdst = reinterpret_cast<float4 *>(a.z_out + pix * kCh);
-#pragma unroll
-            for (int j = 0; j < 8; ++j) zdst[j] = make_float4(acc[4 * j], acc[4 * j + 1], acc[4 * j + 2], acc[4 * j + 3]);
-        }
-    } else if constexpr (EPI == EPI_BWD) {
-        const float4 *zp = reinterpret_cast<const float4 *>(a.z_prev + pix * kCh);
-        float dz[kCh];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const float4 z = zp[j];
-            dz[4 * j] = acc[4 * j] * gelu_grad_f(z.x);
-            dz[4 * j + 1] = acc[4 * j + 1] * gelu_grad_f(z.y);
-            dz[4 * j + 2] = acc[4 * j + 2] * gelu_grad_f(z.z);
-            dz[4 * j + 3] = acc[4 * j + 3] * gelu_grad_f(z.w);
-        }
-        float4 *ddst = reinterpret_cast<float4 *>(a.dz_out + pix * kCh);
-#pragma unroll
-        for (int j = 0; j < 8; ++j) ddst[j] = make_float4(dz[4 * j], dz[4 * j + 1], dz[4 * j + 2], dz[4 * j + 3]);
-        __nv_bfloat162 hb[kCh / 2];
-#pragma unroll
-        for (int n = 0; n < kCh; n += 2) hb[n / 2] = __floats2bfloat162_rn(dz[n], dz[n + 1]);
-        uint4 *hdst = reinterpret_cast<uint4 *>(a.h_out + pix * kCh);
-#pragma unroll
-        for (int j = 0; j < 4; ++j) hdst[j] = reinterpret_cast<uint4 *>(hb)[j];
-    } else {   // EPI_LAST: Psi_NN(u) = u + z
-        const float z = acc[0] + a.bias[0];
-        const size_t q = (size_t)p;
-        if (a.jobs) {
-            const Job<T> jb = a.jobs[img];
-            T phi = (a.skip ? a.skip[(size_t)img * a.H * a.W + q] : jb.in[q]) + (T)z;
-            if (a.clampv > 0.f) phi = fmin(fmax(phi, (T)-a.clampv), (T)a.clampv);
-            double r2 = 0.0;
-            if (jb.sub) apply_epilogue<T, true>(jb, q, phi, a.neg, r2);
-            else apply_epilogue<T, false>(jb, q, phi, a.neg, r2);
-            if (a.partials) {
-                double s = block_sum(r2, red);
-                if (t == 0) a.partials[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = s;
+    }
+}
+
+
+// ---------------------------------------------------------------------------
+// 3x3 convolution of a 32-channel BF16 input by row segments, without an
+// im2col tile.  A CTA owns RT image rows y0 .. y0+RT-1 of a 128-pixel segment
+// x0 .. x0+127 (W a multiple of 128, H of RT).  It stages the RT + 2 input
+// rows of the segment plus one periodic halo pixel on each side, once, as
+// four planes of 8 channels: plane c8 holds [row][slot][8 BF16], slot s =
+// pixel x0 - 1 + s.  In that layout the 8-pixel x 8-channel core matrices of
+// every tap's operand are contiguous 128-byte blocks, consecutive pixel groups
+// 128 B apart and the two channel octets of a K step one plane apart; the A
+// operand of output row r, tap (dy, dx) and K step is a plain descriptor that
+// starts at slot 1 + dx of row r + 1 + dy (16-byte granularity, no alignment
+// beyond it).  So 18 MMAs per output row (9 taps x 2 K steps of 16
+// channels), accumulating into TMEM columns r * NOUT .., read the staged
+// rows directly, and the input is read from memory (RT + 2) / RT times
+// instead of nine.  The K order (tap-major, then channel) and the B operand
+// are those of conv_umma_kernel, so each output value is the same sum of the
+// same BF16 products in the same order.  256 threads: all stage by cp.async;
+// one issues the MMAs; warp w then reads TMEM lanes 32 (w % 4) .. of rows
+// w / 4, w / 4 + 2, ... for the epilogue.  Grid: (W / 128 * H / RT, images).
+// ---------------------------------------------------------------------------
+constexpr int kRowSlots = kTile + 2;
+constexpr int kRowsNT = 256;
+
+__host__ __device__ constexpr int rows_plane_bytes(int RT) { return (RT + 2) * kRowSlots * 16; }
+__host__ __device__ constexpr int rows_smem_bytes(int RT, int NOUT) { return 4 * rows_plane_bytes(RT) + NOUT * kChK * 2; }
+__host__ __device__ constexpr int tmem_cols(int n) { return n <= 32 ? 32 : n <= 64 ? 64 : n <= 128 ? 128 : n <= 256 ? 256 : 512; }
+
+// shared-memory matrix descriptor, K-major without swizzle: K-adjacent core
+// matrices lbo bytes apart, M/N-adjacent ones sbo bytes apart
+__device__ __forceinline__ uint64_t umma_desc_strided(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+
+__device__ __forceinline__ void cp_async16(void *sdst, const void *gsrc)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(sdst)), "l"(gsrc) : "memory");
+}
+
+template <typename T, int NOUT, int EPI, int RT>
+__global__ void __launch_bounds__(kRowsNT) conv_rows_kernel(const __grid_constant__ ConvArgs<T> a)
+{
+    constexpr int PLANE = rows_plane_bytes(RT);
+    constexpr int BBYTES = NOUT * kChK * 2;
+    constexpr int KSTEPS = kChK / 16;
+    constexpr int TCOLS = tmem_cols(RT * NOUT);
+    constexpr int PIECES = (RT + 2) * kRowSlots * 4;
+    static_assert(4 * PLANE % 16 == 0 && PLANE < (1 << 18), "plane stride must fit the descriptor");
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char *sIn = smem;
+    unsigned char *sB = smem + 4 * PLANE;
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tslot;
+    __shared__ double red[RT][4];
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int segs = a.W / kTile;
+    const int seg = blockIdx.x % segs, y0 = (blockIdx.x / segs) * RT, x0 = seg * kTile;
+    const int img = blockIdx.y;
+    const __nv_bfloat16 *src = a.in_bf16 + (size_t)img * a.H * a.W * kCh;
+
+    // stage: piece i = (row, slot, octet c8), 16 bytes; consecutive threads
+    // read consecutive 16-byte pieces of a pixel's 64 bytes
+    for (int i = t; i < PIECES; i += kRowsNT) {
+        const int c8 = i & 3, q = i >> 2;
+        const int row = q / kRowSlots, slot = q - row * kRowSlots;
+        int yy = y0 - 1 + row, xx = x0 - 1 + slot;
+        yy = yy < 0 ? yy + a.H : (yy >= a.H ? yy - a.H : yy);
+        xx = xx < 0 ? xx + a.W : (xx >= a.W ? xx - a.W : xx);
+        cp_async16(sIn + c8 * PLANE + q * 16, src + ((size_t)yy * a.W + xx) * kCh + c8 * 8);
+    }
+    for (int i = t; i < BBYTES / 16; i += kRowsNT)
+        cp_async16(sB + i * 16, reinterpret_cast<const unsigned char *>(a.w) + i * 16);
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+    if (t == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tslot)),
+                     "n"(TCOLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("fence.proxy.async.shared::cta;");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = tslot;
+    if (t == 0) {
+        const uint32_t a0 = smem_u32(sIn), b0 = smem_u32(sB);
+#pragma unroll 1
+        for (int r = 0; r < RT; ++r) {
+#pragma unroll 1
+            for (int s = 0; s < KSTEPS; ++s) {
+                const int tap = s >> 1, half = s & 1;
+                const int dy = a.sign * (tap / 3 - 1), dx = a.sign * (tap % 3 - 1);
+                const uint32_t aa = a0 + (uint32_t)(2 * half * PLANE) + (uint32_t)(((r + 1 + dy) * kRowSlots + 1 + dx) * 16);
+                const uint64_t ad = umma_desc_strided(aa, PLANE, 128);
+                const uint64_t bd = umma_desc(b0 + s * (NOUT * 32));
+                asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                             " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                             ::"r"(tmem + (uint32_t)(r * NOUT)), "l"(ad), "l"(bd), "r"(umma_idesc(kTile, NOUT)),
+                             "r"((uint32_t)(s > 0)));
             }
-        } else {
-            a.out_f32[pix] = a.u_f32[pix] + z;
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                     ::"r"(smem_u32(&mbar)));
+    }
+    uint32_t done = 0;
+    for (int it = 0; it < (1 << 24) && !done; ++it) {
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n"
+                     " selp.u32 %0, 1, 0, p;\n}\n" : "=r"(done) : "r"(smem_u32(&mbar)));
+    }
+    done = __syncthreads_and(done);   // one decision for the whole CTA
+    if (!done && t == 0 && a.err) atomicExch(a.err, 1);
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (done) {
+        const int quarter = warp & 3;
+#pragma unroll 1
+        for (int r = warp >> 2; r < RT; r += kRowsNT / 128) {
+            float acc[NOUT];
+            tmem_ld_acc<NOUT>(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(r * NOUT), acc);
+            const int p = (y0 + r) * a.W + x0 + quarter * 32 + lane;
+            double r2 = conv_epilogue<T, NOUT, EPI>(a, acc, img, p);
+            if constexpr (EPI == EPI_LAST) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) r2 += __shfl_down_sync(0xffffffffu, r2, o);
+                if (lane == 0) red[r][quarter] = r2;
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(TCOLS));
+    if constexpr (EPI == EPI_LAST) {
+        // one partial per 128-pixel tile, indexed and summed as conv_umma_kernel does
+        if (done && a.jobs && a.partials && t < RT) {
+            const double s = red[t][0] + red[t][1] + red[t][2] + red[t][3];
+            a.partials[(size_t)img * (a.H * segs) + (size_t)(y0 + t) * segs + seg] = s;
         }
     }
 }

@@ -104,6 +104,50 @@ def test_nn_gradients_match_oracle(torch):
         off += nw + nb
 
 
+@pytest.mark.parametrize("reps", [(2, 2), (2, 4)])
+def test_row_segment_convolution_equals_the_tile_kernel(torch, reps):
+    """Grids whose rows are whole 128-pixel segments take the row-segment
+    kernel for the four 32-channel-input layers; 64-wide grids take the
+    per-tile gather kernel.  A 64^2 field tiled periodically over 128^2 or
+    128 x 256 is the same periodic function, so the circular network's output
+    is the 64^2 output tiled; both kernels sum the same BF16 products in the
+    same order, so the tiling holds bit for bit."""
+    params = make_params(4)
+    u = I.uniform_field((2, 64, 64), 12, -1.0, 1.0)
+    net = atm.LearnedCoarse()
+    p = torch.as_tensor(flat(params), dtype=torch.float32, device="cuda:0")
+    small = net.apply(p, torch.as_tensor(u, dtype=torch.float32)).cpu().numpy()
+    big = net.apply(p, torch.as_tensor(np.tile(u, (1,) + reps), dtype=torch.float32)).cpu().numpy()
+    assert big.shape == (2, 64 * reps[0], 64 * reps[1])
+    assert np.array_equal(big, np.tile(small, (1,) + reps))
+
+
+def test_row_segment_forward_and_gradients_match_oracle(torch):
+    """The row-segment kernel (128 x 256: two segments per row) against the
+    oracle network with bfloat16-rounded operands, forward and gradients (the
+    training forward keeps pre-activations, the backward-data layers run the
+    same kernel with the negated gather)."""
+    params = make_params(5)
+    u = I.uniform_field((2, 128, 256), 13, -1.0, 1.0)
+    target = u + 0.3 * I.uniform_field((2, 128, 256), 14, -1.0, 1.0)
+    net = atm.LearnedCoarse()
+    p = torch.as_tensor(flat(params), dtype=torch.float32, device="cuda:0")
+    got = net.apply(p, torch.as_tensor(u, dtype=torch.float32)).cpu().numpy().astype(np.float64)
+    want, _, _ = emu_forward(params, u)
+    u32 = u.astype(np.float32).astype(np.float64)
+    assert rel_l2(got - u32, want - u) <= 1e-3, rel_l2(got - u32, want - u)
+    loss, g = net.loss_grad(p, torch.as_tensor(u, dtype=torch.float32), torch.as_tensor(target, dtype=torch.float32))
+    g = g.cpu().numpy().astype(np.float64)
+    wg = flat(emu_grads(params, u, target))
+    assert abs(loss - np.mean((want - target) ** 2)) <= 1e-3 * loss
+    off = 0
+    for (w, b) in params:
+        nw, nb = w.size, b.size
+        assert rel_l2(g[off:off + nw], wg[off:off + nw]) <= 2e-3, (off, rel_l2(g[off:off + nw], wg[off:off + nw]))
+        assert rel_l2(g[off + nw:off + nw + nb], wg[off + nw:off + nw + nb]) <= 2e-3
+        off += nw + nb
+
+
 def test_training_lowers_the_loss_on_propagator_pairs(torch):
     # pairs (u, Phi^16 u) of the Allen-Cahn fine propagator on 64^2
     oc = oracle.make_cfg(oracle.ALLEN_CAHN, 64, 64, dt=1e-4, nt=17, eps=0.02, m=(16,), k=2)
@@ -142,6 +186,24 @@ def test_solve_with_learned_coarse_reaches_the_sequential_solution(torch):
     assert r["converged"] and r["iterations"] <= 16, r
     seq = oracle.sequential(oc, u0)
     assert rel_l2(s.solution().cpu().numpy(), seq) <= 1e-9
+
+
+def test_solve_with_learned_coarse_on_row_segments(torch):
+    """As above on 128^2 with three levels, where the network's inner and
+    last layers (the last with the propagator epilogue and, for the level-1
+    residual, per-tile residual sums) run in the row-segment kernel."""
+    oc, gp, gs = pair(kind="heat2d", nx=128, ny=128, dt=2e-4, nt=257, m=(16, 4), k=3, nu=1, tol=1e-10,
+                      max_iter=40, coarse_prop=atm.PROP_LEARNED)
+    s = atm.Solver(gp, gs)
+    s.set_learned_coarse(torch.as_tensor(flat(onn.init_params(3)), dtype=torch.float32))
+    u0 = I.uniform_field((128, 128), 10)
+    s.set_initial_condition(torch.as_tensor(u0, device="cuda:0"))
+    r = s.solve()
+    assert r["converged"] and r["iterations"] <= 16, r
+    seq = oracle.sequential(oc, u0)
+    assert rel_l2(s.solution().cpu().numpy(), seq) <= 1e-9
+    h = s.residual_history()
+    assert len(h) == r["iterations"] + 1 and h[-1] <= 1e-10
 
 
 def test_trained_network_gain_over_classical_is_measured(torch):
