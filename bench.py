@@ -201,7 +201,7 @@ def run_batch(args):
     groups.append(cur)
     total_steps = sum(d["nt"] - 1 for d, _, _ in descs)
     t_batch = t_single = 0.0
-    iters_b, iters_s, statuses, failed = [], [], [], []
+    iters_b, iters_s, statuses, failed, ms_single = [], [], [], [], []
     for g in groups:
         solvers = [atm.Solver(p, s, device=device) for _, p, s in g]
         for (d, _, _), sv in zip(g, solvers):
@@ -212,7 +212,9 @@ def run_batch(args):
         t = time.perf_counter()
         for sv in solvers:
             sv.set_initial_guess(None)
+            t1 = time.perf_counter()
             r = sv.solve()
+            ms_single.append((time.perf_counter() - t1) * 1e3)
             iters_s.append(r["iterations"])
         torch.cuda.synchronize()
         t_single += time.perf_counter() - t
@@ -228,7 +230,8 @@ def run_batch(args):
         for (d, p, s), sv, r in zip(g, solvers, res):
             if not r["converged"]:
                 h = sv.residual_history()
-                failed.append({"kind": d["kind"], "n": d["n"], "nt": d["nt"], "m": list(s.m[:s.levels - 1]),
+                failed.append({"draw": descs.index((d, p, s)), "kind": d["kind"], "n": d["n"], "nt": d["nt"],
+                               "m": list(s.m[:s.levels - 1]),
                                "k": s.k, "cycles": r["iterations"], "tol": s.tol,
                                "residual_history": [float(x) for x in h[:8]] + ([float(h[-1])] if len(h) > 8 else [])})
         for sv in solvers:
@@ -258,7 +261,8 @@ def run_batch(args):
             "config": {"workload": "batch64", "problems": len(descs), "groups": len(groups),
                        "precision": bprec, "storage": args.storage,
                        "memory_budget_gb_per_group": budget / 1e9, "l2": "inputs larger than L2"},
-            "one_at_a_time": {"value": total_steps / t_single, "ms": t_single * 1e3},
+            "one_at_a_time": {"value": total_steps / t_single, "ms": t_single * 1e3,
+                              "ms_per_problem": [round(x, 2) for x in ms_single]},
             "batched_speedup": t_single / t_batch,
             "iterations_batched": iters_b, "iterations_one_at_a_time": iters_s,
             "converged": int(sum(statuses)), "not_converged": failed,
