@@ -145,10 +145,12 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def kernel_source_hash(fused=False):
-    """Hash of the timed kernel's source (the split sweep kernels, or the fused
-    kernel): stored ncu traffic is used only while it matches."""
-    name = "atm_fused.cuh" if fused else "atm_kernels.cuh"
+def kernel_source_hash(kind="split"):
+    """Hash of the timed kernel's source (the split sweep kernels, the fused
+    cluster kernels or the float-float kernel): stored ncu traffic is used only
+    while it matches."""
+    name = {"fused": "atm_fused.cuh", "persistent": "atm_fused.cuh", "float-float": "atm_df.cuh"}.get(kind,
+                                                                                                 "atm_kernels.cuh")
     with open(os.path.join(ROOT, "paper_2107_09596_gb300", "csrc", name), "rb") as fh:
         return hashlib.md5(fh.read()).hexdigest()[:12]
 
@@ -832,9 +834,9 @@ def main():
         jobs = 1
     traffic_db = load_json(os.path.join(ROOT, "profiles", "traffic.json"), {}) or {}
 
-    def stored_traffic(key, fused):
+    def stored_traffic(key, kind):
         tr = traffic_db.get(key)
-        return tr["bytes_per_launch"] if tr and tr.get("source_hash") == kernel_source_hash(fused) else None
+        return tr["bytes_per_launch"] if tr and tr.get("source_hash") == kernel_source_hash(kind) else None
 
     def kernel_name(sc, what):
         k = sc["kernel"]
@@ -856,9 +858,8 @@ def main():
         if cnt <= 0 or not tot > 0:
             return None
         avg = tot / cnt
-        fusedk = sc["kernel"] in ("fused", "persistent")
         base = {"kernel": kernel_name(sc, what), "avg_launch_ms": avg, "launches_timed": cnt,
-                "traffic": stored_traffic(traffic_key, fusedk),
+                "traffic": stored_traffic(traffic_key, sc["kernel"]),
                 "share_of_step": tot / args.steps * per_step_factor / ms}
         if fp64_pipe:
             fpv = (FLOPS_PER_VALUE[("row", "heat1d")] if w["kind"] == "heat1d" else
