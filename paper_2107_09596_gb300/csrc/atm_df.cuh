@@ -274,7 +274,15 @@ __global__ void __launch_bounds__(NT, MINB) df_sweep_kernel(const __grid_constan
     const int r0 = rank * R;
     const int px = (threadIdx.x * 4) % NX, prow = (threadIdx.x * 4) / NX, pxs = fz_swz(px);
 
-    // 1. load (FP64 -> float-float), react; tile row t = state row r0 - 1 + t
+    // 1. load (FP64 -> float-float), react; tile row t = state row r0 - 1 + t.
+    //    Three threads first prefetch the CTA's FP64 rows (and the halo rows) to
+    //    L2 in bulk, so that the register-staged loads after the first batch
+    //    find them there.
+    if (threadIdx.x == 0) fz_prefetch_l2(jb.in + (size_t)r0 * NX, (unsigned)(R * NX * sizeof(double)));
+    if (PR && threadIdx.x == 1)
+        fz_prefetch_l2(jb.in + (size_t)((r0 + NY - 1) & (NY - 1)) * NX, (unsigned)(NX * sizeof(double)));
+    if (PR && threadIdx.x == 2)
+        fz_prefetch_l2(jb.in + (size_t)((r0 + R) & (NY - 1)) * NX, (unsigned)(NX * sizeof(double)));
     {
         const int t_lo = PR ? 0 : 1, t_hi = PR ? R + 2 : R + 1;
         constexpr int U = 4;
