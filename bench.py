@@ -553,7 +553,7 @@ def train_learned(atm, w, device, steps, seeds=tuple(range(101, 117)), cycles=(1
 
 
 def make_desc(atm, w, algorithm, precision, profile, coarse="classical", sweep="auto", cpoint=False,
-              inner_cycles=0, nu=None, nested=False, fcycle=False):
+              inner_cycles=0, nu=None, nested=False, fcycle=False, inner_coarse_relax=0):
     kind = {"ac": atm.ALLEN_CAHN, "heat1d": atm.HEAT1D}[w["kind"]]
     ny = w["n"] if w["kind"] != "heat1d" else 1
     prob = atm.make_problem(kind, w["n"], ny, dt=w["dt"], nt_points=w["nt"], eps=w["eps"])
@@ -566,7 +566,8 @@ def make_desc(atm, w, algorithm, precision, profile, coarse="classical", sweep="
                            sweep_kernel={"auto": atm.SWEEP_AUTO, "split": atm.SWEEP_SPLIT,
                                          "fused": atm.SWEEP_FUSED, "chain": atm.SWEEP_CHAIN,
                                          "persistent": atm.SWEEP_PERSISTENT}[sweep],
-                           cpoint_only=cpoint, inner_cycles=inner_cycles, nested=nested, fcycle=fcycle)
+                           cpoint_only=cpoint, inner_cycles=inner_cycles, nested=nested, fcycle=fcycle,
+                           inner_coarse_relax=inner_coarse_relax)
     return prob, desc
 
 
@@ -698,6 +699,8 @@ def main():
                     help="level-0 storage: C-points only (default) or every time point")
     ap.add_argument("--nu", type=int, choices=[0, 1], default=None,
                     help="relaxation: 0 F, 1 FCF (default: the workload's); in fp32r it shapes the inner cycles")
+    ap.add_argument("--inner-coarse-relax", choices=["F", "nu"], default="F",
+                    help="refined modes: relaxation on the coarse levels of the FP32 inner cycles (F, or as --nu)")
     ap.add_argument("--inner-cycles", type=int, default=0,
                     help="fp32r: FP32 V-cycles per FP64 refinement step (0: the library default, 5)")
     ap.add_argument("--max-iter", type=int, default=None, help="override the workload's cycle cap")
@@ -756,7 +759,8 @@ def main():
                                                 correction=args.coarse == "correction")
     prob, desc = make_desc(atm, w, args.algorithm, prec, profile=True, coarse=args.coarse,
                            sweep=args.sweep_kernel, cpoint=args.storage == "cpoint",
-                           inner_cycles=args.inner_cycles, nu=args.nu, nested=args.nested, fcycle=args.fcycle)
+                           inner_cycles=args.inner_cycles, nu=args.nu, nested=args.nested, fcycle=args.fcycle,
+                           inner_coarse_relax=int(args.inner_coarse_relax == "nu"))
     solver = atm.Solver(prob, desc, device=device)
     if args.coarse in ("learned", "correction"):
         solver.set_learned_coarse(nn_params)
@@ -916,6 +920,7 @@ def main():
                            "sweep_kernel": args.sweep_kernel, "storage": args.storage, "nested": args.nested,
                            "cycle": "F" if args.fcycle else "V",
                            "inner_cycles": (args.inner_cycles or 5) if refined else None,
+                           "inner_coarse_relax": args.inner_coarse_relax if refined else None,
                            "l2": "working set larger than L2 (workspace %.2f GB; one level-0 launch reads and "
                                  "writes %.0f MB)" % (atm.workspace_size(prob, desc) / 1e9,
                                                       2 * jobs * n_val * (4 if args.precision == "fp32" else 8) / 1e6)},

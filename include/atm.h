@@ -192,6 +192,14 @@ typedef struct {
                                          that array fits in 16 GiB, else the FP32 inner cycles
                                          regenerate the base F-chain they linearise around.  With
                                          ATM_SEQUENTIAL every m_0-th state is kept (m_0 = 0: 16). */
+    int refine_coarse_relax;          /* ATM_FP32_REFINED(_FF): relaxation on levels >= 1 of the FP32
+                                         inner V-cycles -- 0: F-relaxation (default), 1: as `nu`.
+                                         Level 0 of the inner cycles and every level of the FP64
+                                         forms always use `nu`.  The inner cycle only has to
+                                         approximate the correction (the FP64 residual decides the
+                                         result), and on the 256^2 Allen-Cahn workload F on the
+                                         coarse levels needs the same 4 residual passes as FCF with
+                                         a third fewer coarse sweeps (102 ms against 108 ms) */
 } atm_solver;
 
 typedef struct {

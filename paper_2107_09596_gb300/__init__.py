@@ -56,7 +56,7 @@ class SolverDesc(ctypes.Structure):
                 ("profile", ctypes.c_int), ("sweep_kernel", ctypes.c_int),
                 ("refine_inner_cycles", ctypes.c_int), ("cycle_type", ctypes.c_int), ("forcing", ctypes.c_int),
                 ("nested_iteration", ctypes.c_int),
-                ("cpoint_storage_only", ctypes.c_int)]
+                ("cpoint_storage_only", ctypes.c_int), ("refine_coarse_relax", ctypes.c_int)]
 
 
 class TrainCfg(ctypes.Structure):
@@ -171,7 +171,8 @@ def make_solver(algorithm=AT_MGRIT, m=(8,), k=4, nu=1, fine_prop=PROP_PR_ADI,
                 coarse_prop=PROP_SPLIT_BE, reaction_substeps=None, coarse_reaction=REACT_EXACT,
                 tol=1e-10, max_iter=50,
                 precision=FP64, use_graph=True, profile=False, cpoint_only=False,
-                sweep_kernel=0, inner_cycles=0, nested=False, forcing=False, fcycle=False) -> SolverDesc:
+                sweep_kernel=0, inner_cycles=0, nested=False, forcing=False, fcycle=False,
+                inner_coarse_relax=0) -> SolverDesc:
     s = SolverDesc()
     s.algorithm = algorithm
     s.levels = len(m) + 1
@@ -191,6 +192,7 @@ def make_solver(algorithm=AT_MGRIT, m=(8,), k=4, nu=1, fine_prop=PROP_PR_ADI,
     s.nested_iteration = int(nested)
     s.forcing = int(forcing)
     s.cycle_type = int(fcycle)
+    s.refine_coarse_relax = int(inner_coarse_relax)
     return s
 
 

@@ -92,6 +92,8 @@ atm_status check_args(const atm_problem *pb, const atm_solver *sv)
         return atm::fail(ATM_ERR_INVALID_ARG, "unknown sweep_kernel %d", sv->sweep_kernel);
     if (sv->refine_inner_cycles < 0 || sv->refine_inner_cycles > 16)
         return atm::fail(ATM_ERR_INVALID_ARG, "refine_inner_cycles must be in [0, 16]");
+    if (sv->refine_coarse_relax < 0 || sv->refine_coarse_relax > 1)
+        return atm::fail(ATM_ERR_INVALID_ARG, "refine_coarse_relax must be 0 (F) or 1 (as nu)");
     return ATM_OK;
 }
 

@@ -1034,7 +1034,7 @@ struct Plan : PlanBase {
             add_coarsest(ph);
             return;
         }
-        if (sv.nu == 1) {
+        if (fcf(l)) {
             add_frelax(ph, l, 0, false);
             add_crelax(ph, l);
         }
@@ -1047,13 +1047,20 @@ struct Plan : PlanBase {
     }
 
     // Algorithm 2 on level l (one V-cycle visit; level 0 only with a right-hand side).
+    // FCF on level l: nu = 1, except on the coarse levels of the refined
+    // mode's inner cycles, which use F-relaxation unless refine_coarse_relax = 1
+    bool fcf(int l) const
+    {
+        return sv.nu == 1 && !(role == ROLE_INNER && l >= 1 && sv.refine_coarse_relax == 0);
+    }
+
     void add_level_cycle(Phase &ph, int l)
     {
         if (l == L - 1) {
             add_coarsest(ph);
             return;
         }
-        if (sv.nu == 1) {
+        if (fcf(l)) {
             add_frelax(ph, l, 0, false);
             add_crelax(ph, l);
         }
@@ -1654,8 +1661,9 @@ struct Plan : PlanBase {
         int dev = 0;
         cudaGetDevice(&dev);
         char b[512];
-        int n = std::snprintf(b, sizeof(b), "d%d T%zu p%d r%d k%d %dx%d nt%d alg%d L%d nu%d k%d fp%d cp%d sk%d cr%d cpo%d m",
-                              dev, sizeof(T), sv.precision, role, pb.kind, pb.nx, pb.ny, pb.nt_points, sv.algorithm, L, sv.nu, sv.k,
+        int n = std::snprintf(b, sizeof(b), "d%d T%zu p%d r%d k%d %dx%d nt%d alg%d L%d nu%d rc%d k%d fp%d cp%d sk%d cr%d cpo%d m",
+                              dev, sizeof(T), sv.precision, role, pb.kind, pb.nx, pb.ny, pb.nt_points, sv.algorithm, L, sv.nu,
+                              sv.refine_coarse_relax, sv.k,
                               sv.fine_prop, sv.coarse_prop, sv.sweep_kernel, sv.coarse_reaction,
                               (int)cpo + 2 * (base_store != nullptr) + 4 * (fp32_out != nullptr));
         for (int l = 0; l + 1 < L && n < (int)sizeof(b) - 8; ++l) n += std::snprintf(b + n, sizeof(b) - n, "_%d", sv.m[l]);

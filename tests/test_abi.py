@@ -63,7 +63,8 @@ def test_invalid_problem_rejected(atm, change, status):
     assert status in str(e.value)
 
 
-@pytest.mark.parametrize("change", [dict(m=(1,)), dict(k=0), dict(nu=3), dict(m=(64, 64))])
+@pytest.mark.parametrize("change", [dict(m=(1,)), dict(k=0), dict(nu=3), dict(m=(64, 64)),
+                                    dict(inner_coarse_relax=2), dict(inner_coarse_relax=-1)])
 def test_invalid_solver_rejected(atm, change):
     p = atm.make_problem(atm.HEAT1D, 127, dt=1 / 1024, nt_points=1025)
     kw = dict(algorithm=atm.AT_MGRIT, m=(8,), k=4, nu=1)

@@ -147,6 +147,24 @@ def test_refined_with_several_inner_cycles(torch, inner):
     assert res[inner][0]["iterations"] < res[1][0]["iterations"], (res[1][0], res[inner][0])
 
 
+@pytest.mark.parametrize("relax", [0, 1])
+def test_refined_inner_coarse_relaxation(torch, relax):
+    """The coarse levels of the FP32 inner cycles relaxed by F (refine_coarse_relax
+    = 0, the default) or, like level 0, by FCF (1): the same FP64 fixed point
+    (<= 1e-7 against the oracle's sequential solution)."""
+    kw = dict(kind="ac", nx=128, ny=128, dt=1e-4, nt=257, m=(8, 4), k=4, nu=1, tol=1e-9, max_iter=60,
+              precision=atm.FP32_REFINED_FF, cpoint_only=True)
+    oc, gp, gs = pair(**kw)
+    gs.refine_coarse_relax = relax
+    s = atm.Solver(gp, gs)
+    u0 = I.uniform_field((128, 128), 16)
+    s.set_initial_condition(dev(torch, u0))
+    r = s.solve()
+    assert r["converged"], r
+    seq = oracle.sequential(oc, u0)
+    assert rel_l2(s.solution().cpu().numpy(), seq) <= 1e-7
+
+
 CHAIN_CASES = {
     "ac64_ragged_full": dict(kind="ac", nx=64, ny=64, dt=1e-4, nt=300, m=(4, 4), k=3, nu=1),
     "ac128_cpoint": dict(kind="ac", nx=128, ny=128, dt=1e-4, nt=257, m=(8, 4), k=4, nu=1, cpoint_only=True),
