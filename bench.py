@@ -289,11 +289,12 @@ GS_METRIC = "Gray-Scott time-to-solution at space-time residual 1e-7 and fine st
 def gs_vector_bytes(st, n2):
     """Bytes of whole-vector reads and writes (2 n^2 values) done by the Newton
     kernel as written, from its counters.  FP64 passes: per step 7, per Newton
-    iteration -5, per line-search trial 6, per GMRES cycle 10, per GMRES
-    iteration 2.  FP32 passes (Krylov basis, preconditioner): per GMRES cycle
-    17, per GMRES iteration 20, per basis vector orthogonalised against 4."""
-    f64 = 7 * st["steps"] - 5 * st["newton"] + 6 * st["trials"] + 10 * st["cycles"] + 2 * st["gmres"]
-    f32 = 17 * st["cycles"] + 20 * st["gmres"] + 4 * st["basis"]
+    iteration -4 (including the read of the iterate for its FP32 copy), per
+    line-search trial 6, per GMRES cycle 9.  FP32 passes (Krylov basis,
+    preconditioner, the iterate's FP32 copy): per Newton iteration 1, per GMRES
+    cycle 18, per GMRES iteration 22, per basis vector orthogonalised against 4."""
+    f64 = 7 * st["steps"] - 4 * st["newton"] + 6 * st["trials"] + 9 * st["cycles"]
+    f32 = st["newton"] + 18 * st["cycles"] + 22 * st["gmres"] + 4 * st["basis"]
     return (8 * f64 + 4 * f32) * n2
 
 

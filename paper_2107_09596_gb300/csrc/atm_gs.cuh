@@ -75,12 +75,12 @@ struct GsArgs {
 constexpr int kGsStats = 8;
 
 // Bytes of one CTA's scratch slice: five FP64 vectors (W, G, d, trial W,
-// trial G) and restart + 2 FP32 vectors (Z and the Krylov basis), each of
-// 2 nx ny values.
+// trial G) and restart + 3 FP32 vectors (Z, the FP32 copy of W that GMRES
+// reads, and the Krylov basis), each of 2 nx ny values.
 inline size_t gs_cta_bytes(int nx, int ny, int restart)
 {
     const size_t n2 = 2 * (size_t)nx * ny;
-    return 5 * n2 * sizeof(double) + (size_t)(restart + 2) * n2 * sizeof(float);
+    return 5 * n2 * sizeof(double) + (size_t)(restart + 3) * n2 * sizeof(float);
 }
 
 // CTA-wide sum in a fixed order; every thread receives the total.
@@ -226,9 +226,10 @@ __device__ __forceinline__ void gs_apply_M64(const GsArgs &a, const double *W, c
     }
 }
 
-// The same operator in FP32 on FP32 vectors (GMRES; no synchronisation).
+// The same operator in FP32 on FP32 vectors (GMRES; no synchronisation);
+// Wf = fp32(W), made once per Newton system.
 template <int NT>
-__device__ __forceinline__ void gs_apply_M32(const GsArgs &a, const double *W, const float *z, float *out)
+__device__ __forceinline__ void gs_apply_M32(const GsArgs &a, const float *Wf, const float *z, float *out)
 {
     const int nx = a.nx, ny = a.ny, n = nx * ny;
     const float D = (float)a.D, feed = (float)a.feed, kf = (float)(a.kill + a.feed);
@@ -237,7 +238,7 @@ __device__ __forceinline__ void gs_apply_M32(const GsArgs &a, const double *W, c
         int xm, xp, ym, yp;
         w.nbrs(nx, ny, n, xm, xp, ym, yp);
         const int p = w.p;
-        const float u = (float)W[p], v = (float)W[n + p];
+        const float u = Wf[p], v = Wf[n + p];
         const float zu = z[p], zv = z[n + p];
         const float lu = exu * (z[xm] + z[xp] - 2.0f * zu) + eyu * (z[ym] + z[yp] - 2.0f * zu);
         const float lv = exv * (z[n + xm] + z[n + xp] - 2.0f * zv) + eyv * (z[n + ym] + z[n + yp] - 2.0f * zv);
@@ -257,9 +258,9 @@ __device__ __forceinline__ GsLine32 gs_line32(const GsLine &c)
     return r;
 }
 
-// z = P^-1 x in FP32 (x != z); ends synchronised.
+// z = P^-1 x in FP32 (x != z; Wf = fp32(W)); ends synchronised.
 template <int NT>
-__device__ __forceinline__ void gs_precond(const GsArgs &a, const double *W, const float *x, float *z)
+__device__ __forceinline__ void gs_precond(const GsArgs &a, const float *Wf, const float *x, float *z)
 {
     const int nx = a.nx, ny = a.ny, n = nx * ny;
     for (int t = threadIdx.x; t < 2 * ny; t += NT) {
@@ -271,7 +272,7 @@ __device__ __forceinline__ void gs_precond(const GsArgs &a, const double *W, con
     const float D = (float)a.D, feed = (float)a.feed, kf = (float)(a.kill + a.feed);
 #pragma unroll 4
     for (int p = threadIdx.x; p < n; p += NT) {
-        const float u = (float)W[p], v = (float)W[n + p];
+        const float u = Wf[p], v = Wf[n + p];
         const float a11 = 1.0f + D * (v * v + feed), a12 = 2.0f * D * u * v;
         const float a21 = -D * v * v, a22 = 1.0f - D * (2.0f * u * v - kf);
         const float det = a11 * a22 - a12 * a21;
@@ -301,16 +302,21 @@ struct GsSmem {
 
 // d ~= M(W)^-1 G by right-preconditioned restarted GMRES from d = 0, to
 // relative residual eta (||G||_2 = beta0) or max_inner iterations; the
-// Krylov basis V and Z are FP32, d is FP64 (T a free FP64 vector).  Returns
-// the iterations taken.
+// Krylov basis V and Z are FP32, d is FP64 (T a free FP64 vector).  The FP32
+// operator and preconditioner read Wf = fp32(W), converted once here rather
+// than in every application (the same values: each converted W[p] once).
+// Returns the iterations taken.
 template <int NT>
 __device__ __forceinline__ int gs_gmres(const GsArgs &a, const double *W, const double *G, double beta0, double *d,
-                                        double *T, float *Z, float *V, GsSmem &sm, unsigned long long &basis,
-                                        unsigned long long &cycles)
+                                        double *T, float *Z, float *Wf, float *V, GsSmem &sm,
+                                        unsigned long long &basis, unsigned long long &cycles)
 {
     const int n2 = 2 * a.nx * a.ny, kr = a.restart;
     const double target = a.eta * beta0;
-    for (int p = threadIdx.x; p < n2; p += NT) d[p] = 0.0;
+    for (int p = threadIdx.x; p < n2; p += NT) {
+        d[p] = 0.0;
+        Wf[p] = (float)W[p];
+    }
     int total = 0;
     bool first = true;
     while (true) {
@@ -346,8 +352,8 @@ __device__ __forceinline__ int gs_gmres(const GsArgs &a, const double *W, const 
         while (j < kr) {
             const float *Vj = V + (size_t)j * n2;
             float *Vn = V + (size_t)(j + 1) * n2;
-            gs_precond<NT>(a, W, Vj, Z);
-            gs_apply_M32<NT>(a, W, Z, Vn);
+            gs_precond<NT>(a, Wf, Vj, Z);
+            gs_apply_M32<NT>(a, Wf, Z, Vn);
             __syncthreads();
             // modified Gram-Schmidt; the update by V_i and the product with
             // V_{i+1} (or the squared norm) share one pass
@@ -425,7 +431,7 @@ __device__ __forceinline__ int gs_gmres(const GsArgs &a, const double *W, const 
             S[p] = s;
         }
         __syncthreads();
-        gs_precond<NT>(a, W, S, Z);
+        gs_precond<NT>(a, Wf, S, Z);
         for (int p = threadIdx.x; p < n2; p += NT) d[p] += (double)Z[p];
         __syncthreads();
         if (done || res <= target) break;
@@ -445,7 +451,8 @@ __global__ void __launch_bounds__(NT, 2) gs_newton_kernel(GsArgs a)
     double *W = reinterpret_cast<double *>(slice);
     double *G = W + n2, *d = G + n2, *Wt = d + n2, *Gt = Wt + n2;
     float *Z = reinterpret_cast<float *>(Gt + n2);
-    float *V = Z + n2;
+    float *Wf = Z + n2;
+    float *V = Wf + n2;
     for (int job = blockIdx.x; job < a.njobs; job += gridDim.x) {
         const Job<double> jb = a.jobs[job];
         const double *win = jb.in;
@@ -456,7 +463,7 @@ __global__ void __launch_bounds__(NT, 2) gs_newton_kernel(GsArgs a)
         int it = 0, inner = 0;
         unsigned long long basis = 0, cycles = 0, trials = 0;
         while (f > stop && it < a.max_newton) {
-            inner += gs_gmres<NT>(a, W, G, f, d, Wt, Z, V, sm, basis, cycles);
+            inner += gs_gmres<NT>(a, W, G, f, d, Wt, Z, Wf, V, sm, basis, cycles);
             double lam = 1.0, ft = f;
             for (int h = 0; h < 11; ++h) {
                 for (int p = threadIdx.x; p < n2; p += NT) Wt[p] = fma(-lam, d[p], W[p]);
