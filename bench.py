@@ -897,6 +897,23 @@ def main():
         cands = [r for r in [roofline(2, solver.sweep_config(0), "level-0 propagator", fp64p, 2 * sb,
                                       f"{2 * sb} bytes per value (input, output)",
                                       f"{args.workload}:{args.precision}:{args.storage}", 1.0)] if r]
+    if not cands and w["kind"] == "heat1d" and args.sweep_kernel == "persistent":
+        # the whole solve is one cooperative launch: its FP64 line-solve work
+        # over the solve's time (propagator applications counted from the cycle)
+        N0, m, k = w["nt"], w["m"][0], w["k"]
+        NC = (N0 - 1) // m + 1
+        nf = N0 - NC                                   # F-points
+        coarse = NC - 1 if args.algorithm == "mgrit" else sum(min(p, k - 1) for p in range(NC))
+        nu = w["nu"] if args.nu is None else args.nu
+        it = int(np.median(iters))
+        apps = nf + (NC - 1) + it * (nu * (NC - 1 + nf) + 2 * (NC - 1) + coarse + nf + (NC - 1))
+        fpv = FLOPS_PER_VALUE[("row", "heat1d")]
+        ach = fpv * n_val * apps / (ms / 1e3) / 1e12
+        cands = [{"kernel": "persist1d_kernel (the whole solve, one cooperative launch)", "avg_launch_ms": ms,
+                  "launches_timed": args.steps, "traffic": None, "share_of_step": 1.0, "bound": "alu",
+                  "achieved": ach, "peak": pk["fp64_tflops"], "unit": "TFLOP/s", "frac": ach / pk["fp64_tflops"],
+                  "peak_source": pk["fp64_src"],
+                  "algorithmic": f"{fpv} flop/value x {n_val} values x {apps} propagator applications per solve"}]
     if not cands:
         raise RuntimeError("kernel profile recorded no launches")
     cands.sort(key=lambda r: -r["share_of_step"])

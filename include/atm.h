@@ -162,7 +162,13 @@ typedef struct {
                                          walk the states of a launch, the next state's input
                                          arriving in a second shared-memory tile while the current
                                          one is solved).  ATM_SWEEP_AUTO times the split, fused
-                                         and persistent kernels at create time */
+                                         and persistent kernels at create time.  For the 1D heat
+                                         problem ATM_SWEEP_PERSISTENT runs the whole solve as one
+                                         cooperative launch (one warp per C-interval or local grid,
+                                         grid barriers between the stages of Alg. 2, the stopping
+                                         test on the device): FP64, two levels, full storage,
+                                         V-cycles, no right-hand side (ATM_ERR_UNSUPPORTED
+                                         otherwise) */
     int refine_inner_cycles;          /* ATM_FP32_REFINED: FP32 V-cycles on the correction per FP64
                                          residual, 1..16 (0: 5).  More cycles trade FP64 residual
                                          passes for FP32 cycles while the inner iteration still

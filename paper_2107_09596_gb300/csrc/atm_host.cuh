@@ -17,6 +17,7 @@
 #include "atm_common.cuh"
 #include "atm_kernels.cuh"
 #include "atm_gs.cuh"
+#include "atm_persist1d.cuh"
 #include "atm_fused.h"
 #include "atm_df.h"
 #include "atm_nn.h"
@@ -485,6 +486,9 @@ struct Plan : PlanBase {
     void *nn_packed = nullptr;
     void *nn_scratch = nullptr;
     int *nn_err = nullptr;
+    bool p1 = false;                     // 1D heat, ATM_SWEEP_PERSISTENT: the solve is one cooperative launch
+    double *p1_part = nullptr;           // its per-C-point residual sums
+    int *p1_go = nullptr;                // its loop decision
     T *snapshot = nullptr;               // iterate at the start of a solve (learned fallback)
     bool learned_cfg = false;            // created with a learned level
     cudaGraphExec_t gA_nn = nullptr, gIter_nn = nullptr, gA_cl = nullptr, gIter_cl = nullptr;
@@ -1242,6 +1246,15 @@ struct Plan : PlanBase {
         norm_cur = take<double>(1);
         loop_hist = take<double>((size_t)(sv.max_iter > 0 ? sv.max_iter : 0) + 2);
         loop_state = take<double>(4);
+        p1 = is1d && sv.sweep_kernel == ATM_SWEEP_PERSISTENT && role == ROLE_NORMAL;
+        if (p1) {
+            if (sizeof(T) != sizeof(double) || L != 2 || cpo || sv.forcing || sv.nested_iteration || sv.cycle_type != 0)
+                return fail(ATM_ERR_UNSUPPORTED,
+                            "the persistent 1D solve needs FP64, two levels, full storage, V-cycles, no right-hand "
+                            "side and no nested iteration");
+            p1_part = take<double>((size_t)lv[0].NC);
+            p1_go = take<int>(1);
+        }
         any_learned = !is1d && L > 1 &&
                       (sv.coarse_prop == ATM_PROP_LEARNED || sv.coarse_prop == ATM_PROP_LEARNED_CORRECTION);
         hybrid = any_learned && sv.coarse_prop == ATM_PROP_LEARNED_CORRECTION;
@@ -2131,8 +2144,75 @@ struct Plan : PlanBase {
         return s2;
     }
 
+    // The whole solve as one cooperative launch (1D heat, two levels): the
+    // kernel keeps the device-side loop's history and state, read back as a
+    // graph loop's are.
+    atm_status solve_p1(atm_result *res)
+    {
+        if constexpr (sizeof(T) != sizeof(double)) {
+            return fail(ATM_ERR_UNSUPPORTED, "the persistent 1D solve runs in FP64");
+        } else {
+            P1Args a;
+            std::memset(&a, 0, sizeof(a));
+            a.nx = pb.nx;
+            a.N0 = lv[0].N;
+            a.m = sv.m[0];
+            a.N1 = lv[1].N;
+            a.k = sv.algorithm == ATM_AT_MGRIT ? sv.k : 0;
+            a.nu = sv.nu;
+            a.max_iter = sv.max_iter;
+            a.tol = sv.tol;
+            a.u0 = lv[0].u;
+            a.u1 = lv[1].u;
+            a.v1 = lv[1].v;
+            a.r1 = lv[1].r;
+            a.g1 = lv[1].g;
+            a.part = p1_part;
+            a.hist = loop_hist;
+            a.state = loop_state;
+            a.go = p1_go;
+            for (int l = 0; l < 2; ++l) {
+                a.rx0[l] = lv[l].args.rx0;
+                a.cx[l] = lv[l].args.cx;
+            }
+            int C = 1;
+            while (32 * C < pb.nx) C *= 2;
+            const void *fn = C == 1    ? (const void *)persist1d_kernel<1>
+                             : C == 2  ? (const void *)persist1d_kernel<2>
+                             : C == 4  ? (const void *)persist1d_kernel<4>
+                             : C == 8  ? (const void *)persist1d_kernel<8>
+                             : C == 16 ? (const void *)persist1d_kernel<16>
+                             : C == 32 ? (const void *)persist1d_kernel<32>
+                                       : (const void *)persist1d_kernel<64>;
+            int dev = 0, sms = 0, per_sm = 0, coop = 0;
+            ATM_CK(cudaGetDevice(&dev));
+            ATM_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+            ATM_CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+            const size_t smem = 2 * (size_t)pb.nx * sizeof(double);   // both levels' Dirichlet vectors
+            ATM_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, smem));
+            if (!coop || per_sm < 1) return fail(ATM_ERR_UNSUPPORTED, "no cooperative launch on this device");
+            // one warp per C-interval, all CTAs resident (the barriers need it)
+            int grid = (lv[1].N + 7) / 8;
+            if (grid > per_sm * sms) grid = per_sm * sms;
+            void *args[] = {(void *)&a};
+            ATM_CK(cudaEventRecord(ev0, st));
+            ATM_CK(cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(256), args, smem, st));
+            ATM_CK(cudaEventRecord(ev1, st));
+            ATM_CK(cudaEventSynchronize(ev1));
+            float ms = 0;
+            ATM_CK(cudaEventElapsedTime(&ms, ev0, ev1));
+            atm_result R;
+            const atm_status s = loop_result(&R);
+            launches = 1;
+            R.time_ms = ms;
+            if (res) *res = R;
+            return s;
+        }
+    }
+
     atm_status solve_once(atm_result *res)
     {
+        if (p1) return solve_p1(res);
         if (gLoop) {
             ATM_CK(cudaEventRecord(ev0, st));
             ATM_CK(cudaGraphLaunch(gLoop, st));

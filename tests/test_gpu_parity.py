@@ -181,6 +181,53 @@ def test_solve_iterates_match_oracle(torch, case):
         np.testing.assert_allclose(gh, hist, rtol=1e-9, atol=1e-13 * hist[0])
 
 
+PERSIST_1D_CASES = ["cfg1_at_fcf", "cfg1_at_k5", "cfg1_mgrit", "heat1d_f_ragged", "heat1d_k1"]
+
+
+@pytest.mark.parametrize("case", PERSIST_1D_CASES)
+def test_persistent_1d_solve_matches_oracle(torch, case):
+    """The two-level 1D solve as one cooperative launch (ATM_SWEEP_PERSISTENT):
+    iterates after j = 1, 2, 5 cycles and the residual history against the
+    oracle's Algorithm 2, and the iterate against the launch-per-stage plan."""
+    kw = dict(SOLVE_CASES[case])
+    nt = kw["nt"]
+    u0 = I.heat1d_initial_condition(kw["nx"], 0)
+    for j in (1, 2, 5):
+        oc, gp, gs = pair(max_iter=j, tol=0.0, sweep_kernel=atm.SWEEP_PERSISTENT, **kw)
+        _, _, gl = pair(max_iter=j, tol=0.0, **kw)
+        out = []
+        for desc in (gs, gl):
+            s = atm.Solver(gp, desc)
+            guess = I.random_guess(nt, s.state_shape, 2, -0.3, 0.3)
+            guess[0] = u0
+            s.set_initial_condition(dev(torch, u0))
+            s.set_initial_guess(dev(torch, guess))
+            res = s.solve()
+            assert res["iterations"] == j
+            out.append((s.solution().cpu().numpy(), s.residual_history()))
+            s.close()
+        uo = guess.copy()
+        it, hist = oracle.solve(oc, uo, j, 0.0)
+        assert rel_l2(out[0][0], uo) <= 1e-12, (j, rel_l2(out[0][0], uo))
+        assert rel_l2(out[0][0], out[1][0]) <= 1e-14, (j, rel_l2(out[0][0], out[1][0]))
+        np.testing.assert_allclose(out[0][1], hist, rtol=1e-9, atol=1e-13 * hist[0])
+
+
+def test_persistent_1d_solve_converges_and_rejects_other_shapes(torch):
+    oc, gp, gs = pair(kind="heat1d", nx=127, dt=1 / 1024, nt=1025, m=(8,), k=4, nu=1, tol=1e-10, max_iter=60,
+                      sweep_kernel=atm.SWEEP_PERSISTENT)
+    s = atm.Solver(gp, gs)
+    u0 = I.heat1d_initial_condition(127, 0)
+    s.set_initial_condition(dev(torch, u0))
+    r = s.solve()
+    assert r["converged"], r
+    assert rel_l2(s.solution().cpu().numpy(), oracle.sequential(oc, u0)) <= 1e-9
+    _, gp3, gs3 = pair(kind="heat1d", nx=31, dt=1 / 256, nt=257, m=(2, 4), k=4, nu=1,
+                       sweep_kernel=atm.SWEEP_PERSISTENT)
+    with pytest.raises(atm.AtmError, match="persistent 1D"):
+        atm.Solver(gp3, gs3)
+
+
 def test_converged_solution_is_sequential_and_graph_is_bitwise(torch):
     oc, gp, gs = pair(kind="ac", nx=64, ny=64, dt=1e-4, nt=257, m=(4, 4), k=4, nu=1, tol=1e-10,
                       max_iter=60, use_graph=True)
