@@ -2,8 +2,8 @@
 // problem (Sec. 2, Alg. 2; backward Euler per step) in one cooperative launch.
 //
 // A state here is one line of nx <= 2048 values, so every propagator
-// application is one warp's line solve of a microsecond or two, and a solve
-// that launches a kernel per stage spends its time in launch latency.  This
+// application is one warp's line solve of a few microseconds, and a solve
+// that launches a kernel per stage spends much of its time in launch latency.  This
 // kernel keeps one grid resident for the whole solve and walks the stages of
 // the cycle with a grid-wide barrier between dependent stages:
 //
@@ -29,8 +29,9 @@
 // A cycle's leading F-relaxation is the previous cycle's closing one (the
 // F-points follow from the C-points), so it runs once, before the first
 // residual.  The arithmetic of each application is the row kernel's (the same
-// scaling and line solve), so iterates equal those of the launch-per-stage
-// plan.  The only waits are grid barriers of a cooperative launch.
+// scaling and line solve), so iterates agree with those of the
+// launch-per-stage plan.  The only waits are grid barriers of a cooperative
+// launch.
 #pragma once
 
 #include <cooperative_groups.h>
