@@ -213,6 +213,24 @@ def test_persistent_1d_solve_matches_oracle(torch, case):
         np.testing.assert_allclose(out[0][1], hist, rtol=1e-9, atol=1e-13 * hist[0])
 
 
+@pytest.mark.parametrize("nx", [5, 700, 2048])
+def test_persistent_1d_line_lengths(torch, nx):
+    """Lines of 1, 32 and 64 values per lane (nx up to the 2048 limit): the
+    iterate after two cycles of the cooperative solve against the oracle."""
+    kw = dict(kind="heat1d", nx=nx, dt=1e-5, nt=129, m=(8,), k=3, nu=1)
+    oc, gp, gs = pair(max_iter=2, tol=0.0, sweep_kernel=atm.SWEEP_PERSISTENT, **kw)
+    s = atm.Solver(gp, gs)
+    u0 = I.heat1d_initial_condition(nx, 0)
+    guess = I.random_guess(129, s.state_shape, 4, -0.3, 0.3)
+    guess[0] = u0
+    s.set_initial_condition(dev(torch, u0))
+    s.set_initial_guess(dev(torch, guess))
+    s.solve()
+    uo = guess.copy()
+    oracle.solve(oc, uo, 2, 0.0)
+    assert rel_l2(s.solution().cpu().numpy(), uo) <= 1e-12
+
+
 def test_persistent_1d_solve_converges_and_rejects_other_shapes(torch):
     oc, gp, gs = pair(kind="heat1d", nx=127, dt=1 / 1024, nt=1025, m=(8,), k=4, nu=1, tol=1e-10, max_iter=60,
                       sweep_kernel=atm.SWEEP_PERSISTENT)
