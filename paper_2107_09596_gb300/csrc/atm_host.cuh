@@ -2189,14 +2189,18 @@ struct Plan : PlanBase {
             ATM_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
             ATM_CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
             const size_t smem = 2 * (size_t)pb.nx * sizeof(double);   // both levels' Dirichlet vectors
-            ATM_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, smem));
+            // two warps per CTA: the line solves are chains of dependent FP64
+            // operations, and spreading the warps over the SMs gives each a
+            // larger share of an SM's FP64 pipe
+            constexpr int kThreads = 64;
+            ATM_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem));
             if (!coop || per_sm < 1) return fail(ATM_ERR_UNSUPPORTED, "no cooperative launch on this device");
             // one warp per C-interval, all CTAs resident (the barriers need it)
-            int grid = (lv[1].N + 7) / 8;
+            int grid = (lv[1].N + kThreads / 32 - 1) / (kThreads / 32);
             if (grid > per_sm * sms) grid = per_sm * sms;
             void *args[] = {(void *)&a};
             ATM_CK(cudaEventRecord(ev0, st));
-            ATM_CK(cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(256), args, smem, st));
+            ATM_CK(cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kThreads), args, smem, st));
             ATM_CK(cudaEventRecord(ev1, st));
             ATM_CK(cudaEventSynchronize(ev1));
             float ms = 0;
