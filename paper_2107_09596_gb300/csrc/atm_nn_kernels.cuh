@@ -72,7 +72,24 @@ __host__ __device__ constexpr uint32_t umma_idesc(int M, int N)
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-__device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+// GELU(z) = z Phi(z), Phi the standard normal distribution function, with
+// erfc from the rational approximation 7.1.26 of Abramowitz and Stegun,
+// Handbook of Mathematical Functions (|error in erf| <= 1.5e-7 for x >= 0):
+//   erfc(x) ~ t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) exp(-x^2),  t = 1 / (1 + p x).
+// Phi(z) = erfc(|z| / sqrt 2) / 2 for z < 0 and 1 - erfc(|z| / sqrt 2) / 2
+// otherwise, so that the negative tail keeps its relative accuracy.  The
+// error is far below the BF16 rounding of the stored activation.
+__device__ __forceinline__ float gelu_f(float z)
+{
+    const float x = fabsf(z) * 0.70710678118654752f;
+    const float t = __fdividef(1.0f, fmaf(0.3275911f, x, 1.0f));
+    float q = fmaf(1.061405429f, t, -1.453152027f);
+    q = fmaf(q, t, 1.421413741f);
+    q = fmaf(q, t, -0.284496736f);
+    q = fmaf(q, t, 0.254829592f);
+    const float half_erfc = 0.5f * q * t * __expf(-x * x);
+    return z * (z < 0.f ? half_erfc : 1.0f - half_erfc);
+}
 
 __device__ __forceinline__ float gelu_grad_f(float z)
 {
